@@ -1,0 +1,174 @@
+"""CPU oracle of the BBE race simulator's Monte Carlo win-probability path.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg are the only callers.  Nothing on the product path imports this package,
+and it imports nothing from the product package except the seeded input generators.
+
+The arithmetic lives in ``bbe_oracle.c`` (plain C, binary32, no fused operations except
+the written ``fmaf`` calls); this module compiles it with gcc and wraps it with ctypes.
+``surrogate_ref.py`` holds the float64 reference of the surrogate network.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bbe_oracle.c")
+_HDR = os.path.join(_HERE, "bbe_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libbbe_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIST_NORMAL, DIST_UNIFORM, DIST_TWO_POINT = 0, 1, 2
+MAX_STEPS_DEFAULT = 1 << 20
+STEP_LIMIT = -5
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wextra"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (contraction off, no fast-math). Returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_SO) or max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_SO)
+    if stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Race(C.Structure):
+    _fields_ = [("n", C.c_int), ("L", C.c_float), ("d0", C.c_void_p), ("mu", C.c_void_p), ("sigma", C.c_void_p),
+                ("rho", C.c_void_p), ("P", C.c_void_p), ("theta", C.c_void_p), ("prev0", C.c_void_p),
+                ("dist", C.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            vp, i64, u32, u64, f32 = C.c_void_p, C.c_int64, C.c_uint32, C.c_uint64, C.c_float
+            L.bbe_oracle_philox4x32_10.argtypes = [vp, vp, vp]
+            L.bbe_oracle_log.argtypes = [f32]
+            L.bbe_oracle_log.restype = f32
+            L.bbe_oracle_z.argtypes = [C.c_int, u64, u32, u32, u32, u32]
+            L.bbe_oracle_z.restype = f32
+            L.bbe_oracle_rollout.argtypes = [C.POINTER(_Race), u64, u32, u32, i64, vp, vp, i64]
+            L.bbe_oracle_rollout.restype = C.c_int
+            L.bbe_oracle_race_counts.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, i64, vp, vp]
+            L.bbe_oracle_race_counts.restype = C.c_int
+            L.bbe_oracle_win_probs.argtypes = [C.c_int, vp, i64, vp, vp]
+            L.bbe_oracle_log_batch.argtypes = [vp, vp, i64]
+            L.bbe_oracle_sincos2pi_batch.argtypes = [vp, vp, vp, i64]
+            L.bbe_oracle_z_batch.argtypes = [C.c_int, u64, u32, u32, i64, u32, u32, vp]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().bbe_oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def log_f32(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    lib().bbe_oracle_log_batch(_ptr(x), _ptr(y), x.size)
+    return y
+
+
+def sincos2pi(m24):
+    m = np.ascontiguousarray(m24, np.uint32)
+    s = np.empty(m.shape, np.float32)
+    c = np.empty(m.shape, np.float32)
+    lib().bbe_oracle_sincos2pi_batch(_ptr(m), _ptr(s), _ptr(c), m.size)
+    return s, c
+
+
+def z(dist: int, seed: int, r: int, k: int, t: int, c: int) -> float:
+    return float(lib().bbe_oracle_z(dist, seed, r, k, t, c))
+
+
+def z_block(dist: int, seed: int, r: int, k0: int, nk: int, nt: int, c: int) -> np.ndarray:
+    """z for rollouts k0..k0+nk-1 and steps 0..nt-1 of competitor c of race r: [nk, nt]."""
+    out = np.empty((nk, nt), np.float32)
+    lib().bbe_oracle_z_batch(dist, seed, r, k0, nk, nt, c, _ptr(out))
+    return out
+
+
+class _RaceArgs:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, race: dict):
+        f = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+        self.arrays = [f(race[k]) for k in ("d0", "mu", "sigma", "rho", "P", "theta", "prev0")]
+        d0, mu, sigma, rho, P, theta, prev0 = self.arrays
+        self.s = _Race(int(race["n"]), float(race["L"]), _ptr(d0), _ptr(mu), _ptr(sigma), _ptr(rho), _ptr(P),
+                       _ptr(theta), _ptr(prev0), int(race.get("dist", DIST_NORMAL)))
+
+
+def rollout(race: dict, seed: int, r: int, k: int, max_steps: int = MAX_STEPS_DEFAULT, traj_cap: int = 0):
+    """One dry-run: (winner, steps, trajectory [steps, n] or None)."""
+    a = _RaceArgs(race)
+    steps = np.zeros(1, np.int64)
+    traj = np.zeros((max(traj_cap, 0), race["n"]), np.float32) if traj_cap > 0 else None
+    w = lib().bbe_oracle_rollout(C.byref(a.s), seed, r, k, max_steps, _ptr(steps), _ptr(traj), traj_cap)
+    st = int(steps[0])
+    return w, st, (traj[: min(st, traj_cap)] if traj is not None else None)
+
+
+def race_counts(race: dict, seed: int, r: int | None = None, R: int | None = None, k_begin: int = 0,
+                max_steps: int = MAX_STEPS_DEFAULT):
+    """Win counts of one race over rollouts k_begin .. k_begin+R-1: (counts int32 [n], steps_total, status)."""
+    a = _RaceArgs(race)
+    r = race["race_id"] if r is None else r
+    R = race["R"] if R is None else R
+    counts = np.zeros(race["n"], np.int32)
+    steps = np.zeros(1, np.int64)
+    st = lib().bbe_oracle_race_counts(C.byref(a.s), seed, r, k_begin, R, max_steps, _ptr(counts), _ptr(steps))
+    return counts, int(steps[0]), int(st)
+
+
+def batch_counts(batch, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT):
+    """Win counts for the given races of a RaceBatch (all by default), one race per task on
+    a thread pool (ctypes releases the GIL).  Returns (counts int32 [sum n over the given
+    races, concatenated in the order given], steps int64 [len(races)], status)."""
+    races = list(range(batch.n_races)) if races is None else [int(x) for x in races]
+    threads = threads or os.cpu_count() or 1
+
+    def one(r):
+        return race_counts(batch.race(r), batch.seed, max_steps=max_steps)
+
+    if threads <= 1 or len(races) <= 1:
+        res = [one(r) for r in races]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(one, races))
+    counts = np.concatenate([x[0] for x in res]) if res else np.zeros(0, np.int32)
+    steps = np.array([x[1] for x in res], np.int64)
+    status = min([x[2] for x in res], default=0)
+    return counts, steps, status
+
+
+def win_probs(counts, R: int):
+    counts = np.ascontiguousarray(counts, np.int32)
+    p = np.empty(counts.size, np.float32)
+    o = np.empty(counts.size, np.float32)
+    lib().bbe_oracle_win_probs(counts.size, _ptr(counts), R, _ptr(p), _ptr(o))
+    return p, o
