@@ -1,0 +1,388 @@
+"""Benchmark: Monte Carlo race rollouts -> win counts -> win probabilities, on GB300.
+
+A step is one pass of the whole path over one batch: bbe_rollout_batch (every race's
+rollouts, winners counted) and bbe_win_probs (probabilities and odds).  The default
+workload is 4096 mid-race snapshots x 20 competitors x 10,000 rollouts (track 5000, positions
+U(0, 0.9 L), mean step U(15,17), spread U(0.5,1.5), responsiveness U(0,1), seed 0).  The metric is
+competitor-steps per second: one competitor advanced by one step of Eq. 1, summed over all
+rollouts until each rollout's first finisher.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload uniform|uneven|single]
+                  [--impl gb300|reference] [--no-cpu-baseline] [--no-e2e]
+
+Under torchrun (N > 1) every rank runs its own batch of the same shape with a distinct
+range of race ids (weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2108_02419_gb300 import workloads as W  # noqa: E402
+
+METRIC = "competitor-steps/s & win-prob vectors/s, MC vs surrogate (≤0.01 max-abs err), 1 GB300"
+UNIT = "competitor-steps/s"
+
+# Algorithmic 32-bit operations per competitor-step of the rollout contract:
+#   Philox4x32-10 per 4 steps: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor) + 9 x 2 key adds = 98 -> 24.5
+#   Box-Muller per 2 steps: u1 (4), log (20), radius (2), sin/cos (22), 2 products      = 50 -> 25
+#   Eq. 1: responsiveness (2), i+ lookup and blocking test (6), step (3 or 1), floor (2),
+#          advance (1), finish test (1), bookkeeping (1)                                   = 16.5
+ALG_OPS_PER_COMPETITOR_STEP = 66.0
+SMS = 152
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "single"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--races", type=int, default=0, help="use only the first N races (profiling of a small case)")
+    return ap.parse_args()
+
+
+def make_workload(name: str, rank: int = 0, races: int = 0) -> W.RaceBatch:
+    if name == "uniform":
+        rb = W.uniform_batch(seed=0)
+    elif name == "uneven":
+        rb = W.uneven_batch(seed=0)
+    else:
+        rb = W.single_race_start(seed=0)
+    if races and races < rb.n_races:
+        rb = rb.slice(0, races)
+    # weak scaling: rank r simulates its own races, ids offset past the other ranks'
+    rb.race_id0 = rank * rb.n_races
+    return rb
+
+
+def workload_config(name: str, rb: W.RaceBatch) -> dict:
+    sizes = rb.sizes()
+    cfg = {
+        "uniform": {"workload": "uniform mid-race snapshots", "races": rb.n_races, "competitors": int(sizes[0]),
+                    "track_len": 5000, "rollouts_per_race": int(rb.rollouts[0]),
+                    "positions": "U(0, 0.9 L)"},
+        "uneven": {"workload": "uneven snapshots, one persistent launch", "races": rb.n_races,
+                   "competitors": "U{2..24}", "track_len": 5000, "remaining": "U(100, 5000)",
+                   "rollouts_per_race": "floor(10^U(3,5))"},
+        "single": {"workload": "single race from the start line", "races": 1, "competitors": int(sizes[0]),
+                   "track_len": 2000, "rollouts_per_race": int(rb.rollouts[0])},
+    }[name]
+    cfg.update({"params": "mu U(15,17), sigma U(0.5,1.5), rho U(0,1), P 1, theta 1", "seed": 0,
+                "dist": "normal (Box-Muller)", "total_rollouts": int(rb.rollouts.sum()),
+                "competitors_total": rb.n_total})
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def competitor_steps(rb: W.RaceBatch, steps_total: np.ndarray) -> int:
+    return int((rb.sizes() * steps_total.astype(np.int64)).sum())
+
+
+# ---------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(rb: W.RaceBatch, seconds: float, threads: int):
+    """Time the CPU oracle (as it stands) on a leading sample of the workload's races, sized
+    to about `seconds` of CPU time on `threads` threads.  Returns (comp-steps/s, description)."""
+    import oracle
+
+    oracle.build()
+    # calibrate on one chunk of race 0
+    probe = min(int(rb.rollouts[0]), 500)
+    t0 = time.perf_counter()
+    _, st, _ = oracle.race_counts(rb.race(0), rb.seed, R=probe)
+    per_rollout_s = (time.perf_counter() - t0) / probe
+    rollouts_target = max(1, int(seconds * threads / max(per_rollout_s, 1e-9)))
+    races, tot = [], 0
+    for r in range(rb.n_races):
+        races.append(r)
+        tot += int(rb.rollouts[r])
+        if tot >= rollouts_target:
+            break
+    t0 = time.perf_counter()
+    _, steps, _ = oracle.batch_counts(rb, races=races, threads=threads)
+    dt = time.perf_counter() - t0
+    cs = int((rb.sizes()[races] * steps).sum())
+    desc = f"races 0..{races[-1]} of the workload ({len(races)} races, {tot} rollouts, {cs} competitor-steps), {dt:.1f} s"
+    return cs / dt, desc, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    rb = make_workload(args.workload, 0, args.races)
+    threads = os.cpu_count() or 1
+    # size one step to ~1.5 s of CPU work on all cores
+    probe = min(int(rb.rollouts[0]), 400)
+    t0 = time.perf_counter()
+    oracle.race_counts(rb.race(0), rb.seed, R=probe)
+    per_rollout = (time.perf_counter() - t0) / probe
+    target = max(1, int(1.5 * threads / max(per_rollout, 1e-9)))
+    races, tot = [], 0
+    for r in range(rb.n_races):
+        races.append(r)
+        tot += int(rb.rollouts[r])
+        if tot >= target:
+            break
+    units, times = 0, []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, steps, _ = oracle.batch_counts(rb, races=races, threads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            units = int((rb.sizes()[races] * steps).sum())
+    total = sum(times)
+    value = units * len(times) / total
+    sample = f"races 0..{races[-1]} ({len(races)} races, {tot} rollouts, {units} competitor-steps) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args.workload, rb),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU leg
+
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rb = make_workload(args.workload, rank, args.races)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    batch = bbe.Batch(rb, stream=stream)
+    counts = torch.empty(rb.n_total, dtype=torch.int32, device=dev)
+    steps_t = torch.empty(rb.n_races, dtype=torch.int64, device=dev)
+    probs = torch.empty(rb.n_total, dtype=torch.float32, device=dev)
+    odds = torch.empty_like(probs)
+    if args.autotune:
+        batch.autotune(counts, budget_ms=5000.0, stream=stream)
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
+
+    def one_step():
+        batch.rollout(counts, steps_t, stream=stream)
+        batch.win_probs(counts, probs, odds, stream=stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    stream.synchronize()
+    batch.status(stream)
+    units_per_step = competitor_steps(rb, steps_t.cpu().numpy())
+    rollouts_per_step = int(rb.rollouts.sum())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        l2_flush.fill_(i)  # flush L2 between timed steps (outside the events)
+        ev[i][0].record(stream)
+        batch.rollout(counts, steps_t, stream=stream)
+        ev[i][1].record(stream)
+        batch.win_probs(counts, probs, odds, stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    roll_ms = [a.elapsed_time(b) for a, b, c in ev]
+    batch.status(stream)
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    if dist:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = units_per_step * world * args.steps / t_max
+
+    # end to end through the public API: pinned host inputs -> bbe_race_init (H2D) ->
+    # rollouts -> probabilities -> D2H of probabilities and counts
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host = {k: pin(getattr(rb, k)) for k in ("race_off", "L", "rollouts", "d0", "mu", "sigma", "rho", "P", "theta")}
+        h_probs = torch.empty(rb.n_total, dtype=torch.float32).pin_memory()
+        h_counts = torch.empty(rb.n_total, dtype=torch.int32).pin_memory()
+        h2d = sum(int(t.numel() * t.element_size()) for t in host.values())
+        d2h = int(h_probs.numel() * 4 + h_counts.numel() * 4)
+        e_times = []
+        for i in range(2 + max(1, min(args.steps, 5))):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            h = bbe.bbe_race_init(rb.n_races, host["race_off"], host["L"], host["rollouts"], host["d0"], host["mu"],
+                                  host["sigma"], host["rho"], host["P"], host["theta"], None, rb.seed, rb.dist,
+                                  rb.race_id0, stream)
+            bbe.bbe_rollout_batch(h, counts, None, stream)
+            bbe.bbe_win_probs(h, counts, probs, odds, stream)
+            h_probs.copy_(probs, non_blocking=True)
+            h_counts.copy_(counts, non_blocking=True)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            bbe.bbe_destroy_batch(h)
+            if i >= 2:
+                e_times.append(dt)
+        e_local = statistics.median(e_times)
+        if dist:
+            tt = torch.tensor([e_local], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_local = float(tt.item())
+        e2e = {"value": units_per_step * world / e_local, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e_local}
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * LANES_PER_SM * sm_max * 1e6  # lane-operations per second at the maximum SM clock
+    roll_s = statistics.mean(roll_ms) / 1e3
+    achieved = ALG_OPS_PER_COMPETITOR_STEP * units_per_step / roll_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "rollout_kernel", "ops_per_competitor_step": ALG_OPS_PER_COMPETITOR_STEP,
+                "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (maximum SM clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, desc, _ = oracle_sample(rb, args.cpu_seconds, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    cfg = workload_config(args.workload, rb)
+    cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch.cfg(),
+                "rollouts_per_step_per_gpu": rollouts_per_step, "competitor_steps_per_step_per_gpu": units_per_step,
+                "parallelism": f"races x{world} (weak)"})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "win_prob_vectors_per_s": rb.n_races * world * args.steps / t_max,
+            "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 2 * args.steps}
+    batch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as D
+
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        D.init_process_group(backend)
+        dist = D
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * bbe.h -- C ABI of the GB300 (sm_103a) Monte Carlo race-rollout library.
+ *
+ * The library estimates, for many race states at once, each competitor's probability of
+ * winning the race and the matching decimal odds, by re-running the race from its current
+ * state many times: these are the dry-runs of the paper's rational-predictor bettors
+ * (Section 3), whose outcomes are counted into frequencies, and the repeated seeded runs
+ * that estimate the outcome distribution (Section 6).  One step of a race follows Eq. 1:
+ *
+ *   d_c(t+1) = d_c(t) + S_c(t),
+ *   S_c = R_c * P_c * delta(v_c)          if Delta_c > theta_c (no one close in front)
+ *       = R_c * min(S_c(t-1), S_i+(t-1))  otherwise (blocked by the nearest i+ in front)
+ *
+ * with these readings where the paper leaves the law open:
+ *   delta(v_c) = mu_c + sigma_c * z, z ~ N(0,1) (or uniform / two-point, see bbe_dist);
+ *   R_c        = 1 + 0.2 (2 rho_c - 1) (d_c / L - 1/2), rho_c in [0,1];
+ *   S_c        >= 1e-3 (Section 3: S_c > 0 at all times);
+ *   a rollout ends at the first step in which some competitor reaches d >= L; the
+ *   winner is the finisher that crossed earliest within that step, i.e. the least
+ *   (L - d_c) / S_c, ties to the lowest competitor index.
+ * All arithmetic is IEEE binary32 with round-to-nearest-even in a fixed operation order,
+ * and the random numbers come from a counter-based Philox4x32-10 stream keyed by
+ * (seed) and (rollout k, step t / 4, competitor c, race id r), so the integer win counts
+ * are a deterministic function of (state, seed, rollout budget): any partition of the
+ * races or rollouts gives the same counts.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BBE_OK or a negative bbe_status; on error nothing was launched and
+ *     bbe_last_error() returns a thread-local message.
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Calls that
+ *     launch work are asynchronous on that stream unless stated otherwise.
+ *   - Buffers passed in are owned by the caller and must stay valid until the work that
+ *     uses them has completed; handles (bbe_batch) are owned by the library and freed
+ *     with their destroy call.
+ *   - Faults found on the device (a rollout that reaches the step limit) are recorded in
+ *     a per-batch status word and returned by bbe_batch_status().
+ */
+#ifndef BBE_H
+#define BBE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BBE_API __attribute__((visibility("default")))
+#else
+#define BBE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BBE_OK = 0,
+    BBE_ERR_ARG = -1,         /* null pointer, bad size, non-monotone offsets, NaN/Inf, out-of-range parameter */
+    BBE_ERR_UNSUPPORTED = -2, /* a race with fewer than 1 or more than BBE_MAX_COMPETITORS competitors */
+    BBE_ERR_FINISHED = -3,    /* a competitor already at or past the finish line (d >= L) */
+    BBE_ERR_CUDA = -4,        /* a CUDA runtime call failed (message in bbe_last_error) */
+    BBE_ERR_STEP_LIMIT = -5,  /* some rollout reached max_steps without a finisher; it counts for nobody */
+    BBE_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up */
+    BBE_ERR_RANGE = -7        /* a value outside the range the call supports */
+} bbe_status;
+
+/* Distribution of z in delta(v_c) = mu_c + sigma_c * z.  Section 3 leaves the step
+ * generator open (its example is uniform); NORMAL is the default reading. */
+typedef enum {
+    BBE_DIST_NORMAL = 0,   /* z ~ N(0, 1) by the Box-Muller transform */
+    BBE_DIST_UNIFORM = 1,  /* z ~ U(-sqrt 3, sqrt 3): mean 0, variance 1 */
+    BBE_DIST_TWO_POINT = 2 /* z = -1 or +1 with probability 1/2 each */
+} bbe_dist;
+
+#define BBE_MAX_COMPETITORS 32
+#define BBE_THETA_DEFAULT 1.0f
+#define BBE_MAX_STEPS_DEFAULT (1 << 20)
+
+typedef struct bbe_batch bbe_batch; /* opaque, library-owned */
+
+/* Launch shape of the rollout kernel.  Zero fields mean "library default". */
+typedef struct {
+    int32_t warps_per_block;    /* 1..32 */
+    int32_t blocks_per_sm;      /* 1..32; grid = SMs x blocks_per_sm (persistent) */
+    int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 */
+    int32_t max_steps;          /* step limit per rollout, 1..2^30 */
+} bbe_launch_cfg;
+
+/* bbe_race_init -- validate a batch of race states and stage it on the current device.
+ *
+ * Section 3 defines a race r by its track length L_r and, per competitor c, its position
+ * d_c, its step distribution v_c (here mu_c, sigma_c), its responsiveness R_c (here the
+ * parameter rho_c), its preference coefficient P_c in [0,1] and its blocking threshold
+ * theta_c; S_c(t-1) is the competitor's previous step.
+ *
+ *   out         receives the new handle (set to NULL on error).
+ *   n_races     number of races, >= 1.
+ *   race_off    int32[n_races + 1], CSR offsets over competitors: race r owns competitors
+ *               race_off[r] .. race_off[r+1]-1; race_off[0] = 0; 1 <= size <= 32.
+ *   track_len   float[n_races], L_r > 0.
+ *   rollouts    int64[n_races], rollout budget R_r, 1 .. 2^31-1.
+ *   pos         float[sum n], d_c, 0 <= d_c < L_r.
+ *   mu, sigma   float[sum n], mean step mu_c > 0 and spread sigma_c >= 0.
+ *   resp        float[sum n], responsiveness parameter rho_c in [0, 1].
+ *   pref        float[sum n] or NULL (all 1): P_c in (0, 1].
+ *   theta       float[sum n] or NULL (all BBE_THETA_DEFAULT): theta_c >= 0.
+ *   prev_step   float[sum n] or NULL (mu_c * P_c): S_c(t-1) > 0 for the first step.
+ *   seed        64-bit Philox key.
+ *   dist        the distribution of z.
+ *   race_id0    id of race 0 in the random stream; race r uses id race_id0 + r, so a batch
+ *               split into pieces reproduces the counts of the whole.
+ *   cuda_stream stream for the staging copies; the call synchronises it before returning.
+ * Every array may live in host or device memory (copied with cudaMemcpyDefault); the
+ * library keeps its own device copy, so the caller may free them after the call.
+ * Errors: BBE_ERR_ARG, BBE_ERR_UNSUPPORTED, BBE_ERR_FINISHED, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
+                         const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
+                         const float *resp, const float *pref, const float *theta, const float *prev_step,
+                         uint64_t seed, bbe_dist dist, uint32_t race_id0, void *cuda_stream);
+
+/* bbe_rollout_batch -- run every race's R_r rollouts and count the winners (Section 3
+ * dry-runs; Section 6 repeated runs).  One persistent kernel launch (replayed from a CUDA
+ * graph) processes all races.
+ *   win_counts  device int32[sum n], overwritten: win_counts[race_off[r] + c] = number of
+ *               rollouts of race r that competitor c won.  Sum over a race = R_r unless a
+ *               rollout hit the step limit.
+ *   steps_total device int64[n_races] or NULL, overwritten: total steps over race r's
+ *               rollouts (the finishing step included); competitor-steps = n_r x this.
+ * Asynchronous on cuda_stream.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA; device faults via
+ * bbe_batch_status. */
+BBE_API bbe_status bbe_rollout_batch(bbe_batch *batch, int32_t *win_counts, int64_t *steps_total, void *cuda_stream);
+
+/* bbe_win_probs -- frequentist win probabilities p_c = count_c / R_r and decimal odds
+ * 1 / p_c (decimal odds are the total returned per unit stake; +Inf when p_c = 0).
+ *   win_counts device int32[sum n] from bbe_rollout_batch.
+ *   probs      device float[sum n]; odds device float[sum n] or NULL.
+ * Asynchronous on cuda_stream.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_win_probs(const bbe_batch *batch, const int32_t *win_counts, float *probs, float *odds,
+                         void *cuda_stream);
+
+/* bbe_batch_status -- synchronise cuda_stream and return the batch's device status from
+ * the last bbe_rollout_batch: BBE_OK, BBE_ERR_STEP_LIMIT, or BBE_ERR_CUDA if the stream
+ * reported an error. */
+BBE_API bbe_status bbe_batch_status(bbe_batch *batch, void *cuda_stream);
+
+/* bbe_batch_set_cfg / bbe_batch_get_cfg -- launch shape used by bbe_rollout_batch.
+ * Setting rebuilds the work list.  Errors: BBE_ERR_ARG for out-of-range fields. */
+BBE_API bbe_status bbe_batch_set_cfg(bbe_batch *batch, const bbe_launch_cfg *cfg);
+BBE_API bbe_status bbe_batch_get_cfg(const bbe_batch *batch, bbe_launch_cfg *cfg);
+
+/* bbe_batch_autotune -- time candidate launch shapes on this batch and keep the fastest.
+ * Runs the batch's rollouts once per candidate (bounded by `budget_ms` of GPU time per
+ * candidate: candidates are timed on a leading subset of the work list), writing into
+ * win_counts (device int32[sum n]) as scratch.  Synchronous.  Errors: BBE_ERR_ARG,
+ * BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_batch_autotune(bbe_batch *batch, int32_t *win_counts, double budget_ms, void *cuda_stream);
+
+/* bbe_batch_info -- sizes of a staged batch (any output pointer may be NULL). */
+BBE_API bbe_status bbe_batch_info(const bbe_batch *batch, int32_t *n_races, int64_t *n_competitors,
+                          int64_t *total_rollouts, int32_t *max_competitors);
+
+/* bbe_destroy_batch -- free a handle (NULL is ignored).  Synchronises the device work
+ * that uses it first. */
+BBE_API void bbe_destroy_batch(bbe_batch *batch);
+
+/* bbe_last_error -- thread-local message of the last failed call on this thread. */
+BBE_API const char *bbe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBE_H */

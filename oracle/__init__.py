@@ -145,24 +145,38 @@ def race_counts(race: dict, seed: int, r: int | None = None, R: int | None = Non
     return counts, int(steps[0]), int(st)
 
 
-def batch_counts(batch, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT):
-    """Win counts for the given races of a RaceBatch (all by default), one race per task on
-    a thread pool (ctypes releases the GIL).  Returns (counts int32 [sum n over the given
-    races, concatenated in the order given], steps int64 [len(races)], status)."""
+def batch_counts(batch, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,
+                 rollout_chunk: int = 2500):
+    """Win counts for the given races of a RaceBatch (all by default).  Each race's rollouts
+    are split into chunks of ``rollout_chunk`` and the chunks run on a thread pool (ctypes
+    releases the GIL); the counter-based stream makes the split exact.  Returns
+    (counts int32 [sum n over the given races, concatenated in the order given],
+    steps int64 [len(races)], status)."""
     races = list(range(batch.n_races)) if races is None else [int(x) for x in races]
     threads = threads or os.cpu_count() or 1
+    tasks = []
+    for i, r in enumerate(races):
+        R = int(batch.rollouts[r])
+        for k0 in range(0, R, rollout_chunk):
+            tasks.append((i, r, k0, min(rollout_chunk, R - k0)))
 
-    def one(r):
-        return race_counts(batch.race(r), batch.seed, max_steps=max_steps)
+    def one(task):
+        i, r, k0, cnt = task
+        return race_counts(batch.race(r), batch.seed, R=cnt, k_begin=k0, max_steps=max_steps)
 
-    if threads <= 1 or len(races) <= 1:
-        res = [one(r) for r in races]
+    if threads <= 1 or len(tasks) <= 1:
+        res = [one(t) for t in tasks]
     else:
         with ThreadPoolExecutor(threads) as ex:
-            res = list(ex.map(one, races))
-    counts = np.concatenate([x[0] for x in res]) if res else np.zeros(0, np.int32)
-    steps = np.array([x[1] for x in res], np.int64)
-    status = min([x[2] for x in res], default=0)
+            res = list(ex.map(one, tasks))
+    per_race = [np.zeros(int(batch.race_off[r + 1] - batch.race_off[r]), np.int64) for r in races]
+    steps = np.zeros(len(races), np.int64)
+    status = 0
+    for (i, r, k0, cnt), (c, st, s) in zip(tasks, res):
+        per_race[i] += c
+        steps[i] += st
+        status = min(status, s)
+    counts = np.concatenate(per_race).astype(np.int32) if per_race else np.zeros(0, np.int32)
     return counts, steps, status
 
 

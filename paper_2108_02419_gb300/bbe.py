@@ -1,0 +1,231 @@
+"""Python binding of the C ABI in include/bbe.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but
+convert arguments (torch tensors, numpy arrays, raw pointers, streams) and raise
+``BbeError`` on a non-zero status.  All simulation work runs in the CUDA library; there
+is no fallback: if ``libbbe.so`` has not been built, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbbe.so")
+
+BBE_OK = 0
+STATUS_NAMES = {0: "BBE_OK", -1: "BBE_ERR_ARG", -2: "BBE_ERR_UNSUPPORTED", -3: "BBE_ERR_FINISHED",
+                -4: "BBE_ERR_CUDA", -5: "BBE_ERR_STEP_LIMIT", -6: "BBE_ERR_TIMEOUT", -7: "BBE_ERR_RANGE"}
+BBE_DIST_NORMAL, BBE_DIST_UNIFORM, BBE_DIST_TWO_POINT = 0, 1, 2
+BBE_MAX_COMPETITORS = 32
+BBE_MAX_STEPS_DEFAULT = 1 << 20
+
+
+class BbeError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        self.status = status
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+class bbe_launch_cfg(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("rollouts_per_lane", C.c_int32),
+                ("max_steps", C.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbbe.so.  Raises if the library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2108_02419_gb300.build.build() "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+        sig = {
+            "bbe_race_init": [C.POINTER(vp), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, C.c_int, u32, vp],
+            "bbe_rollout_batch": [vp, vp, vp, vp],
+            "bbe_win_probs": [vp, vp, vp, vp, vp],
+            "bbe_batch_status": [vp, vp],
+            "bbe_batch_set_cfg": [vp, C.POINTER(bbe_launch_cfg)],
+            "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
+            "bbe_batch_autotune": [vp, vp, C.c_double, vp],
+            "bbe_batch_info": [vp, vp, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.bbe_destroy_batch.argtypes = [vp]
+        L.bbe_destroy_batch.restype = None
+        L.bbe_last_error.argtypes = []
+        L.bbe_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, func: str):
+    if status != BBE_OK:
+        raise BbeError(status, func, lib().bbe_last_error().decode(errors="replace"))
+
+
+def _ptr(x, dtype=None):
+    """Raw address of a torch tensor / numpy array (contiguous, of the given dtype), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if dtype is not None and x.dtype != np.dtype(dtype):
+            raise TypeError(f"expected numpy {dtype}, got {x.dtype}")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    import torch
+
+    if isinstance(x, torch.Tensor):
+        if dtype is not None and x.dtype != getattr(torch, np.dtype(dtype).name):
+            raise TypeError(f"expected torch {np.dtype(dtype).name}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def bbe_race_init(n_races, race_off, track_len, rollouts, pos, mu, sigma, resp, pref=None, theta=None, prev_step=None,
+                  seed=0, dist=BBE_DIST_NORMAL, race_id0=0, stream=None) -> int:
+    """Stage a batch of race states; returns the opaque handle (an int)."""
+    h = C.c_void_p()
+    st = lib().bbe_race_init(C.byref(h), int(n_races), _ptr(race_off, np.int32), _ptr(track_len, np.float32),
+                             _ptr(rollouts, np.int64), _ptr(pos, np.float32), _ptr(mu, np.float32),
+                             _ptr(sigma, np.float32), _ptr(resp, np.float32), _ptr(pref, np.float32),
+                             _ptr(theta, np.float32), _ptr(prev_step, np.float32), int(seed) & (2**64 - 1), int(dist),
+                             int(race_id0) & 0xFFFFFFFF, _stream(stream))
+    _check(st, "bbe_race_init")
+    return h.value
+
+
+def bbe_rollout_batch(batch: int, win_counts, steps_total=None, stream=None) -> None:
+    _check(lib().bbe_rollout_batch(batch, _ptr(win_counts, np.int32), _ptr(steps_total, np.int64), _stream(stream)),
+           "bbe_rollout_batch")
+
+
+def bbe_win_probs(batch: int, win_counts, probs, odds=None, stream=None) -> None:
+    _check(lib().bbe_win_probs(batch, _ptr(win_counts, np.int32), _ptr(probs, np.float32), _ptr(odds, np.float32),
+                               _stream(stream)), "bbe_win_probs")
+
+
+def bbe_batch_status(batch: int, stream=None) -> None:
+    _check(lib().bbe_batch_status(batch, _stream(stream)), "bbe_batch_status")
+
+
+def bbe_batch_set_cfg(batch: int, warps_per_block=0, blocks_per_sm=0, rollouts_per_lane=0, max_steps=0) -> None:
+    cfg = bbe_launch_cfg(warps_per_block, blocks_per_sm, rollouts_per_lane, max_steps)
+    _check(lib().bbe_batch_set_cfg(batch, C.byref(cfg)), "bbe_batch_set_cfg")
+
+
+def bbe_batch_get_cfg(batch: int) -> dict:
+    cfg = bbe_launch_cfg()
+    _check(lib().bbe_batch_get_cfg(batch, C.byref(cfg)), "bbe_batch_get_cfg")
+    return cfg.as_dict()
+
+
+def bbe_batch_autotune(batch: int, win_counts, budget_ms: float = 2000.0, stream=None) -> dict:
+    _check(lib().bbe_batch_autotune(batch, _ptr(win_counts, np.int32), float(budget_ms), _stream(stream)),
+           "bbe_batch_autotune")
+    return bbe_batch_get_cfg(batch)
+
+
+def bbe_batch_info(batch: int) -> dict:
+    nr, nc, tr, mx = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().bbe_batch_info(batch, C.byref(nr), C.byref(nc), C.byref(tr), C.byref(mx)), "bbe_batch_info")
+    return dict(n_races=nr.value, n_competitors=nc.value, total_rollouts=tr.value, max_competitors=mx.value)
+
+
+def bbe_destroy_batch(batch: int) -> None:
+    if batch:
+        lib().bbe_destroy_batch(batch)
+
+
+def bbe_last_error() -> str:
+    return lib().bbe_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Batch:
+    """Owns one staged batch handle; arrays are taken from a ``workloads.RaceBatch``-like
+    object (numpy, host memory: bbe_race_init copies them to the device itself)."""
+
+    def __init__(self, rb, stream=None):
+        self.rb = rb
+        self.handle = bbe_race_init(rb.n_races, rb.race_off, rb.L, rb.rollouts, rb.d0, rb.mu, rb.sigma, rb.rho, rb.P,
+                                    rb.theta, rb.prev0, rb.seed, rb.dist, rb.race_id0, stream)
+
+    def new_outputs(self, device="cuda"):
+        import torch
+
+        counts = torch.empty(self.rb.n_total, dtype=torch.int32, device=device)
+        steps = torch.empty(self.rb.n_races, dtype=torch.int64, device=device)
+        return counts, steps
+
+    def rollout(self, counts=None, steps=None, stream=None):
+        if counts is None:
+            counts, steps = self.new_outputs()
+        bbe_rollout_batch(self.handle, counts, steps, stream)
+        return counts, steps
+
+    def win_probs(self, counts, probs=None, odds=None, stream=None):
+        import torch
+
+        if probs is None:
+            probs = torch.empty(self.rb.n_total, dtype=torch.float32, device=counts.device)
+            odds = torch.empty_like(probs)
+        bbe_win_probs(self.handle, counts, probs, odds, stream)
+        return probs, odds
+
+    def status(self, stream=None):
+        bbe_batch_status(self.handle, stream)
+
+    def set_cfg(self, **kw):
+        bbe_batch_set_cfg(self.handle, **kw)
+
+    def cfg(self):
+        return bbe_batch_get_cfg(self.handle)
+
+    def autotune(self, counts, budget_ms=2000.0, stream=None):
+        return bbe_batch_autotune(self.handle, counts, budget_ms, stream)
+
+    def close(self):
+        if self.handle:
+            bbe_destroy_batch(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

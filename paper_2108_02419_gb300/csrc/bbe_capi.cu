@@ -1,0 +1,549 @@
+// bbe_capi.cu -- the C ABI declared in include/bbe.h: validation and staging of race
+// batches, the persistent launch (replayed from an instantiated CUDA graph), the launch
+// autotuner and the win-probability finaliser.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "bbe_internal.h"
+
+namespace bbe {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace bbe
+
+using bbe::set_error;
+
+struct bbe_batch {
+    int device = 0;
+    int num_sms = 0;
+    int32_t n_races = 0;
+    int32_t n_total = 0;
+    int32_t max_n = 0;
+    uint64_t seed = 0;
+    int32_t dist = 0;
+    uint32_t race_id0 = 0;
+
+    // host copies (kept for scheduling and cost estimates)
+    std::vector<int32_t> h_off;
+    std::vector<float> h_L;
+    std::vector<int64_t> h_R;
+    std::vector<float> h_d0, h_mu;
+
+    // library-owned device memory
+    void *arena = nullptr;
+    bbe::DevBatch dev{};
+    bbe::WorkItem *d_items = nullptr;
+    int32_t n_items = 0;
+    int32_t *d_queue = nullptr;
+    int32_t *d_status = nullptr;
+
+    bbe_launch_cfg cfg{};
+
+    // graph cache
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int32_t *g_counts = nullptr;
+    int64_t *g_steps = nullptr;
+};
+
+namespace {
+
+#define BBE_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));                 \
+            return BBE_ERR_CUDA;                                                            \
+        }                                                                                   \
+    } while (0)
+
+constexpr int32_t kDefaultWarpsPerBlock = 8;
+constexpr int32_t kDefaultBlocksPerSm = 8;
+constexpr int32_t kDefaultRolloutsPerLane = 32;
+
+bool finite(float x) { return std::isfinite(x); }
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bbe_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s, const char *what)
+{
+    if (bytes == 0) return BBE_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) {
+        set_error(std::string("copy of ") + what + ": " + cudaGetErrorString(e));
+        return BBE_ERR_CUDA;
+    }
+    return BBE_OK;
+}
+
+void free_graph(bbe_batch *b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_counts = nullptr;
+    b->g_steps = nullptr;
+}
+
+// Expected steps of one rollout: the leader's remaining distance over the largest mean
+// step (used only to order the work queue, longest items first).
+double est_steps(const bbe_batch *b, int r)
+{
+    const int a = b->h_off[r], e = b->h_off[r + 1];
+    float lead = 0.0f, vmax = 0.0f;
+    for (int i = a; i < e; ++i) {
+        lead = std::max(lead, b->h_d0[i]);
+        vmax = std::max(vmax, b->h_mu[i]);
+    }
+    return 1.0 + double(b->h_L[r] - lead) / double(std::max(vmax, 1e-3f));
+}
+
+bbe_status build_items(bbe_batch *b)
+{
+    std::vector<bbe::WorkItem> items;
+    std::vector<double> cost;
+    const int64_t per_lane = b->cfg.rollouts_per_lane;
+    for (int r = 0; r < b->n_races; ++r) {
+        const int n = b->h_off[r + 1] - b->h_off[r];
+        const int nseg = 32 / n;
+        const int64_t chunk = per_lane * nseg;
+        const double st = est_steps(b, r);
+        for (int64_t k = 0; k < b->h_R[r]; k += chunk) {
+            const int64_t cnt = std::min<int64_t>(chunk, b->h_R[r] - k);
+            items.push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
+            cost.push_back(double((cnt + nseg - 1) / nseg) * st);
+        }
+    }
+    if (items.size() > size_t(INT32_MAX)) {
+        set_error("work list too long; raise rollouts_per_lane");
+        return BBE_ERR_RANGE;
+    }
+    std::vector<int32_t> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    std::vector<bbe::WorkItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->n_items = int32_t(sorted.size());
+    BBE_CUDA_TRY(cudaMalloc(&b->d_items, std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem)));
+    BBE_CUDA_TRY(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice));
+    free_graph(b);
+    return BBE_OK;
+}
+
+bbe_status check_cfg(const bbe_launch_cfg &c)
+{
+    if (c.warps_per_block < 1 || c.warps_per_block > 32 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
+        c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30)) {
+        set_error("launch configuration out of range");
+        return BBE_ERR_ARG;
+    }
+    return BBE_OK;
+}
+
+bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *steps)
+{
+    bbe::RolloutLaunch l{};
+    l.b = b->dev;
+    l.items = b->d_items;
+    l.n_items = b->n_items;
+    l.queue = b->d_queue;
+    l.counts = counts;
+    l.steps = reinterpret_cast<unsigned long long *>(steps);
+    l.status = b->d_status;
+    l.max_steps = b->cfg.max_steps;
+    l.block = 32 * b->cfg.warps_per_block;
+    l.grid = std::max(1, b->num_sms * b->cfg.blocks_per_sm);
+    return l;
+}
+
+// The launch sequence of one rollout pass: reset queue, status and outputs, then the
+// persistent kernel.
+cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, size_t(b->n_total) * sizeof(int32_t), s);
+    if (e == cudaSuccess && steps) e = cudaMemsetAsync(steps, 0, size_t(b->n_races) * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps), s);
+    return e;
+}
+
+bbe_status ensure_graph(bbe_batch *b, int32_t *counts, int64_t *steps)
+{
+    if (b->gexec && b->g_counts == counts && b->g_steps == steps) return BBE_OK;
+    free_graph(b);
+    if (!b->capture_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    BBE_CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_pass(b, counts, steps, b->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error(std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BBE_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+        return BBE_ERR_CUDA;
+    }
+    b->g_counts = counts;
+    b->g_steps = steps;
+    return BBE_OK;
+}
+
+template <typename T>
+T *carve(char *&p, size_t count)
+{
+    T *out = reinterpret_cast<T *>(p);
+    p += (count * sizeof(T) + 255) / 256 * 256;
+    return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bbe_last_error(void) { return bbe::g_last_error.c_str(); }
+
+bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
+                         const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
+                         const float *resp, const float *pref, const float *theta, const float *prev_step,
+                         uint64_t seed, bbe_dist dist, uint32_t race_id0, void *cuda_stream)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return BBE_ERR_ARG;
+    }
+    *out = nullptr;
+    if (n_races < 1 || !race_off || !track_len || !rollouts || !pos || !mu || !sigma || !resp) {
+        set_error("n_races < 1 or a required array is NULL");
+        return BBE_ERR_ARG;
+    }
+    if (int(dist) < 0 || int(dist) > 2) {
+        set_error("unknown distribution");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    std::vector<int32_t> off(size_t(n_races) + 1);
+    bbe_status st = copy_in(off.data(), race_off, off.size() * sizeof(int32_t), s, "race_off");
+    if (st) return st;
+    BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (off[0] != 0) {
+        set_error("race_off[0] != 0");
+        return BBE_ERR_ARG;
+    }
+    int32_t max_n = 0;
+    for (int r = 0; r < n_races; ++r) {
+        const int64_t n = int64_t(off[r + 1]) - off[r];
+        if (n < 0) {
+            set_error("race_off is not monotone at race " + std::to_string(r));
+            return BBE_ERR_ARG;
+        }
+        if (n < 1 || n > BBE_MAX_COMPETITORS) {
+            set_error("race " + std::to_string(r) + " has " + std::to_string(n) + " competitors (supported: 1..32)");
+            return BBE_ERR_UNSUPPORTED;
+        }
+        max_n = std::max<int32_t>(max_n, int32_t(n));
+    }
+    const int32_t nt = off[n_races];
+
+    auto b = new bbe_batch();
+    b->n_races = n_races;
+    b->n_total = nt;
+    b->max_n = max_n;
+    b->seed = seed;
+    b->dist = int32_t(dist);
+    b->race_id0 = race_id0;
+    b->h_off = off;
+    b->h_L.resize(n_races);
+    b->h_R.resize(n_races);
+    b->h_d0.resize(nt);
+    b->h_mu.resize(nt);
+    std::vector<float> h_sigma(nt), h_rho(nt), h_P(nt, 1.0f), h_theta(nt, BBE_THETA_DEFAULT), h_prev;
+    auto fail = [&](bbe_status code) {
+        delete b;
+        return code;
+    };
+    if ((st = copy_in(b->h_L.data(), track_len, n_races * sizeof(float), s, "track_len")) ||
+        (st = copy_in(b->h_R.data(), rollouts, n_races * sizeof(int64_t), s, "rollouts")) ||
+        (st = copy_in(b->h_d0.data(), pos, nt * sizeof(float), s, "pos")) ||
+        (st = copy_in(b->h_mu.data(), mu, nt * sizeof(float), s, "mu")) ||
+        (st = copy_in(h_sigma.data(), sigma, nt * sizeof(float), s, "sigma")) ||
+        (st = copy_in(h_rho.data(), resp, nt * sizeof(float), s, "resp")) ||
+        (pref && (st = copy_in(h_P.data(), pref, nt * sizeof(float), s, "pref"))) ||
+        (theta && (st = copy_in(h_theta.data(), theta, nt * sizeof(float), s, "theta"))))
+        return fail(st);
+    if (prev_step) {
+        h_prev.resize(nt);
+        if ((st = copy_in(h_prev.data(), prev_step, nt * sizeof(float), s, "prev_step"))) return fail(st);
+    }
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("staging copies: ") + cudaGetErrorString(e));
+            return fail(BBE_ERR_CUDA);
+        }
+    }
+    // validation (Section 3: S > 0, P in [0,1], positions on the track)
+    for (int r = 0; r < n_races; ++r) {
+        const float L = b->h_L[r];
+        if (!finite(L) || !(L > 0.0f)) {
+            set_error("track_len of race " + std::to_string(r) + " is not a positive finite number");
+            return fail(BBE_ERR_ARG);
+        }
+        if (b->h_R[r] < 1 || b->h_R[r] > INT32_MAX) {
+            set_error("rollouts of race " + std::to_string(r) + " outside 1..2^31-1");
+            return fail(BBE_ERR_ARG);
+        }
+        for (int i = off[r]; i < off[r + 1]; ++i) {
+            const float d = b->h_d0[i];
+            auto where = [&]() { return " (race " + std::to_string(r) + ", competitor " + std::to_string(i - off[r]) + ")"; };
+            if (!finite(d) || d < 0.0f) {
+                set_error("position must be finite and >= 0" + where());
+                return fail(BBE_ERR_ARG);
+            }
+            if (d >= L) {
+                set_error("competitor already finished (d >= L)" + where());
+                return fail(BBE_ERR_FINISHED);
+            }
+            if (!finite(b->h_mu[i]) || !(b->h_mu[i] > 0.0f) || !finite(h_sigma[i]) || !(h_sigma[i] >= 0.0f)) {
+                set_error("need finite mu > 0 and sigma >= 0" + where());
+                return fail(BBE_ERR_ARG);
+            }
+            if (!(h_rho[i] >= 0.0f && h_rho[i] <= 1.0f)) {
+                set_error("responsiveness rho outside [0, 1]" + where());
+                return fail(BBE_ERR_ARG);
+            }
+            if (!(h_P[i] > 0.0f && h_P[i] <= 1.0f)) {
+                set_error("preference P outside (0, 1]" + where());
+                return fail(BBE_ERR_ARG);
+            }
+            if (!finite(h_theta[i]) || !(h_theta[i] >= 0.0f)) {
+                set_error("theta must be finite and >= 0" + where());
+                return fail(BBE_ERR_ARG);
+            }
+            if (prev_step && (!finite(h_prev[i]) || !(h_prev[i] > 0.0f))) {
+                set_error("prev_step must be finite and > 0" + where());
+                return fail(BBE_ERR_ARG);
+            }
+        }
+    }
+    std::vector<int32_t> comp_race(nt);
+    for (int r = 0; r < n_races; ++r)
+        for (int i = off[r]; i < off[r + 1]; ++i) comp_race[i] = r;
+
+    // one device arena for the staged batch
+    size_t bytes = 0;
+    auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
+    add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4);
+    for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
+    add(4); add(4);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("device allocation: ") + cudaGetErrorString(e));
+        return fail(BBE_ERR_CUDA);
+    }
+    char *p = static_cast<char *>(b->arena);
+    int32_t *d_off = carve<int32_t>(p, n_races + 1);
+    float *d_L = carve<float>(p, n_races);
+    int64_t *d_R = carve<int64_t>(p, n_races);
+    int32_t *d_cr = carve<int32_t>(p, nt);
+    float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
+    float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
+    float *d_prev = carve<float>(p, nt);
+    b->d_queue = carve<int32_t>(p, 1);
+    b->d_status = carve<int32_t>(p, 1);
+    struct {
+        void *dst;
+        const void *src;
+        size_t n;
+    } ups[] = {{d_off, off.data(), off.size() * 4},       {d_L, b->h_L.data(), size_t(n_races) * 4},
+               {d_R, b->h_R.data(), size_t(n_races) * 8}, {d_cr, comp_race.data(), size_t(nt) * 4},
+               {d_d0, b->h_d0.data(), size_t(nt) * 4},   {d_mu, b->h_mu.data(), size_t(nt) * 4},
+               {d_sigma, h_sigma.data(), size_t(nt) * 4}, {d_rho, h_rho.data(), size_t(nt) * 4},
+               {d_P, h_P.data(), size_t(nt) * 4},         {d_theta, h_theta.data(), size_t(nt) * 4}};
+    for (auto &u : ups) {
+        if ((st = copy_in(u.dst, u.src, u.n, s, "staged batch"))) return fail(st);
+    }
+    if (prev_step && (st = copy_in(d_prev, h_prev.data(), size_t(nt) * 4, s, "prev_step"))) return fail(st);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error(std::string("staging upload: ") + cudaGetErrorString(e));
+        return fail(BBE_ERR_CUDA);
+    }
+    b->dev = bbe::DevBatch{d_off, d_L, d_R, d_cr, d_d0, d_mu, d_sigma, d_rho, d_P, d_theta,
+                           prev_step ? d_prev : nullptr, n_races, nt, race_id0, uint32_t(seed), uint32_t(seed >> 32),
+                           int32_t(dist)};
+    b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT};
+    if ((st = build_items(b))) return fail(st);
+    *out = b;
+    return BBE_OK;
+}
+
+bbe_status bbe_rollout_batch(bbe_batch *b, int32_t *win_counts, int64_t *steps_total, void *cuda_stream)
+{
+    if (!b || !win_counts) {
+        set_error("batch or win_counts is NULL");
+        return BBE_ERR_ARG;
+    }
+    bbe_status st = ensure_graph(b, win_counts, steps_total);
+    if (st) return st;
+    BBE_CUDA_TRY(cudaGraphLaunch(b->gexec, as_stream(cuda_stream)));
+    return BBE_OK;
+}
+
+bbe_status bbe_win_probs(const bbe_batch *b, const int32_t *win_counts, float *probs, float *odds, void *cuda_stream)
+{
+    if (!b || !win_counts || !probs) {
+        set_error("batch, win_counts or probs is NULL");
+        return BBE_ERR_ARG;
+    }
+    BBE_CUDA_TRY(bbe::launch_win_probs(b->dev, win_counts, probs, odds, as_stream(cuda_stream)));
+    return BBE_OK;
+}
+
+bbe_status bbe_batch_status(bbe_batch *b, void *cuda_stream)
+{
+    if (!b) {
+        set_error("batch is NULL");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    int32_t flags = 0;
+    BBE_CUDA_TRY(cudaMemcpyAsync(&flags, b->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags & bbe::kStatusStepLimit) {
+        set_error("a rollout reached max_steps without a finisher");
+        return BBE_ERR_STEP_LIMIT;
+    }
+    return BBE_OK;
+}
+
+bbe_status bbe_batch_set_cfg(bbe_batch *b, const bbe_launch_cfg *cfg)
+{
+    if (!b || !cfg) {
+        set_error("batch or cfg is NULL");
+        return BBE_ERR_ARG;
+    }
+    bbe_launch_cfg c = *cfg;
+    if (c.warps_per_block == 0) c.warps_per_block = kDefaultWarpsPerBlock;
+    if (c.blocks_per_sm == 0) c.blocks_per_sm = kDefaultBlocksPerSm;
+    if (c.rollouts_per_lane == 0) c.rollouts_per_lane = kDefaultRolloutsPerLane;
+    if (c.max_steps == 0) c.max_steps = BBE_MAX_STEPS_DEFAULT;
+    bbe_status st = check_cfg(c);
+    if (st) return st;
+    const bool rebuild = c.rollouts_per_lane != b->cfg.rollouts_per_lane;
+    b->cfg = c;
+    free_graph(b);
+    return rebuild ? build_items(b) : BBE_OK;
+}
+
+bbe_status bbe_batch_get_cfg(const bbe_batch *b, bbe_launch_cfg *cfg)
+{
+    if (!b || !cfg) {
+        set_error("batch or cfg is NULL");
+        return BBE_ERR_ARG;
+    }
+    *cfg = b->cfg;
+    return BBE_OK;
+}
+
+bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_ms, void *cuda_stream)
+{
+    if (!b || !win_counts || !(budget_ms > 0.0)) {
+        set_error("batch or win_counts is NULL, or budget_ms <= 0");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    const bbe_launch_cfg start = b->cfg;
+    // candidates: resident warps per SM (occupancy) x block shape x work-item size
+    const int32_t shapes[][2] = {{8, 8}, {4, 16}, {16, 4}, {8, 4}, {32, 2}};
+    const int32_t per_lane[] = {8, 32, 128};
+    cudaEvent_t e0, e1;
+    BBE_CUDA_TRY(cudaEventCreate(&e0));
+    BBE_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = INFINITY;
+    bbe_launch_cfg best = start;
+    double spent = 0.0;
+    bbe_status st = BBE_OK;
+    for (int32_t pl : per_lane) {
+        for (auto &sh : shapes) {
+            bbe_launch_cfg c{sh[0], sh[1], pl, start.max_steps};
+            if ((st = bbe_batch_set_cfg(b, &c))) goto done;
+            // warm the item list, then time one full pass
+            cudaEventRecord(e0, s);
+            if (enqueue_pass(b, win_counts, nullptr, s) != cudaSuccess) {
+                set_error("autotune launch failed");
+                st = BBE_ERR_CUDA;
+                goto done;
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                set_error("autotune synchronise failed");
+                st = BBE_ERR_CUDA;
+                goto done;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            spent += ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+            if (spent > budget_ms) goto done;
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) {
+        bbe_batch_set_cfg(b, &start);
+        return st;
+    }
+    return bbe_batch_set_cfg(b, &best);
+}
+
+bbe_status bbe_batch_info(const bbe_batch *b, int32_t *n_races, int64_t *n_competitors, int64_t *total_rollouts,
+                          int32_t *max_competitors)
+{
+    if (!b) {
+        set_error("batch is NULL");
+        return BBE_ERR_ARG;
+    }
+    if (n_races) *n_races = b->n_races;
+    if (n_competitors) *n_competitors = b->n_total;
+    if (total_rollouts) *total_rollouts = std::accumulate(b->h_R.begin(), b->h_R.end(), int64_t(0));
+    if (max_competitors) *max_competitors = b->max_n;
+    return BBE_OK;
+}
+
+void bbe_destroy_batch(bbe_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_graph(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->arena) cudaFree(b->arena);
+    delete b;
+}
+
+}  // extern "C"
