@@ -70,8 +70,7 @@ def make_workload(name: str, rank: int = 0, races: int = 0) -> W.RaceBatch:
     if races and races < rb.n_races:
         rb = rb.slice(0, races)
     # weak scaling: rank r simulates its own races, ids offset past the other ranks'
-    rb.race_id0 = rank * rb.n_races
-    return rb
+    return W.for_rank(rb, rank)
 
 
 def workload_config(name: str, rb: W.RaceBatch) -> dict:

@@ -77,7 +77,7 @@ typedef struct bbe_batch bbe_batch; /* opaque, library-owned */
 
 /* Launch shape of the rollout kernel.  Zero fields mean "library default". */
 typedef struct {
-    int32_t warps_per_block;    /* 1..32 */
+    int32_t warps_per_block;    /* 1..16 */
     int32_t blocks_per_sm;      /* 1..32; grid = SMs x blocks_per_sm (persistent) */
     int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 */
     int32_t max_steps;          /* step limit per rollout, 1..2^30 */

@@ -49,6 +49,7 @@ struct bbe_batch {
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};
+    int32_t resident = 1;  // rollout-kernel blocks resident per SM for cfg (queried outside capture)
 
     // graph cache
     cudaStream_t capture_stream = nullptr;
@@ -145,7 +146,7 @@ bbe_status build_items(bbe_batch *b)
 
 bbe_status check_cfg(const bbe_launch_cfg &c)
 {
-    if (c.warps_per_block < 1 || c.warps_per_block > 32 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
+    if (c.warps_per_block < 1 || c.warps_per_block > 16 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
         c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30)) {
         set_error("launch configuration out of range");
         return BBE_ERR_ARG;
@@ -165,7 +166,8 @@ bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *ste
     l.status = b->d_status;
     l.max_steps = b->cfg.max_steps;
     l.block = 32 * b->cfg.warps_per_block;
-    l.grid = std::max(1, b->num_sms * b->cfg.blocks_per_sm);
+    // persistent grid: never more blocks than can be resident at once
+    l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident)));
     return l;
 }
 
@@ -393,6 +395,7 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
                            prev_step ? d_prev : nullptr, n_races, nt, race_id0, uint32_t(seed), uint32_t(seed >> 32),
                            int32_t(dist)};
     b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT};
+    b->resident = bbe::rollout_resident_blocks(b->dist, 32 * kDefaultWarpsPerBlock);
     if ((st = build_items(b))) return fail(st);
     *out = b;
     return BBE_OK;
@@ -452,6 +455,7 @@ bbe_status bbe_batch_set_cfg(bbe_batch *b, const bbe_launch_cfg *cfg)
     if (st) return st;
     const bool rebuild = c.rollouts_per_lane != b->cfg.rollouts_per_lane;
     b->cfg = c;
+    b->resident = bbe::rollout_resident_blocks(b->dist, 32 * c.warps_per_block);
     free_graph(b);
     return rebuild ? build_items(b) : BBE_OK;
 }
@@ -475,7 +479,7 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     cudaStream_t s = as_stream(cuda_stream);
     const bbe_launch_cfg start = b->cfg;
     // candidates: resident warps per SM (occupancy) x block shape x work-item size
-    const int32_t shapes[][2] = {{8, 8}, {4, 16}, {16, 4}, {8, 4}, {32, 2}};
+    const int32_t shapes[][2] = {{8, 8}, {4, 16}, {16, 4}, {8, 4}, {16, 2}};
     const int32_t per_lane[] = {8, 32, 128};
     cudaEvent_t e0, e1;
     BBE_CUDA_TRY(cudaEventCreate(&e0));

@@ -49,6 +49,8 @@ struct RolloutLaunch {
 constexpr int32_t kStatusStepLimit = 1;
 
 cudaError_t launch_rollout(const RolloutLaunch &l, cudaStream_t stream);
+// Blocks of `block` threads of the rollout kernel that fit on one SM at once.
+int rollout_resident_blocks(int dist, int block);
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
                              cudaStream_t stream);
 

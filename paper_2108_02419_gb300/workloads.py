@@ -165,3 +165,20 @@ def concat(batches) -> RaceBatch:
     prev0 = cat("prev0") if all(have) else None
     return _assemble(sizes, cat("L"), cat("rollouts"), cat("d0"), cat("mu"), cat("sigma"), cat("rho"), b0.seed,
                      "+".join(b.name for b in batches), b0.dist, cat("P"), cat("theta"), prev0)
+
+
+def for_rank(rb: RaceBatch, rank: int) -> RaceBatch:
+    """Weak scaling: rank r runs a batch of the same shape whose races take the stream ids
+    r * n_races .. (r+1) * n_races - 1, so no two ranks simulate the same race."""
+    out = rb.slice(0, rb.n_races)
+    out.race_id0 = rb.race_id0 + rank * rb.n_races
+    return out
+
+
+def shard(rb: RaceBatch, rank: int, world: int) -> RaceBatch:
+    """Strong scaling: a contiguous share of the races (ids kept), balanced by rollouts x competitors."""
+    work = np.cumsum(rb.rollouts * rb.sizes())
+    total = int(work[-1])
+    bounds = [0] + [int(np.searchsorted(work, total * q / world, side="left")) + 1 for q in range(1, world)] + [rb.n_races]
+    bounds = np.maximum.accumulate(np.minimum(bounds, rb.n_races))
+    return rb.slice(int(bounds[rank]), int(bounds[rank + 1]))

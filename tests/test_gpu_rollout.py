@@ -119,7 +119,7 @@ def test_launch_shape_does_not_change_counts(bbe):
     rb = W.uneven_batch(seed=8, n_races=60, r_lo_exp=1.5, r_hi_exp=3.0)
     ref = run_gpu(bbe, rb)
     for cfg in ({"warps_per_block": 1, "blocks_per_sm": 1, "rollouts_per_lane": 1},
-                {"warps_per_block": 32, "blocks_per_sm": 2, "rollouts_per_lane": 1000},
+                {"warps_per_block": 16, "blocks_per_sm": 2, "rollouts_per_lane": 1000},
                 {"warps_per_block": 4, "blocks_per_sm": 16, "rollouts_per_lane": 7}):
         got = run_gpu(bbe, rb, cfg)
         assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
