@@ -31,7 +31,7 @@ class BbeError(RuntimeError):
 
 class bbe_launch_cfg(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("rollouts_per_lane", C.c_int32),
-                ("max_steps", C.c_int32)]
+                ("max_steps", C.c_int32), ("slots_per_lane", C.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -136,8 +136,9 @@ def bbe_batch_status(batch: int, stream=None) -> None:
     _check(lib().bbe_batch_status(batch, _stream(stream)), "bbe_batch_status")
 
 
-def bbe_batch_set_cfg(batch: int, warps_per_block=0, blocks_per_sm=0, rollouts_per_lane=0, max_steps=0) -> None:
-    cfg = bbe_launch_cfg(warps_per_block, blocks_per_sm, rollouts_per_lane, max_steps)
+def bbe_batch_set_cfg(batch: int, warps_per_block=0, blocks_per_sm=0, rollouts_per_lane=0, max_steps=0,
+                      slots_per_lane=0) -> None:
+    cfg = bbe_launch_cfg(warps_per_block, blocks_per_sm, rollouts_per_lane, max_steps, slots_per_lane)
     _check(lib().bbe_batch_set_cfg(batch, C.byref(cfg)), "bbe_batch_set_cfg")
 
 

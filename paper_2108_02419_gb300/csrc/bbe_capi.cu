@@ -43,13 +43,15 @@ struct bbe_batch {
     // library-owned device memory
     void *arena = nullptr;
     bbe::DevBatch dev{};
-    bbe::WorkItem *d_items = nullptr;
-    int32_t n_items = 0;
-    int32_t *d_queue = nullptr;
+    bbe::WorkItem *d_items = nullptr;  // items of one-slot races, then of two-slot races
+    int32_t n_items_v[2] = {0, 0};     // item counts per slots-per-lane value (1, 2)
+    int32_t *d_queue = nullptr;        // two queue heads
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};
-    int32_t resident = 1;  // rollout-kernel blocks resident per SM for cfg (queried outside capture)
+    int32_t resident[2] = {1, 1};  // rollout-kernel blocks resident per SM, per slots-per-lane
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // graph cache
     cudaStream_t capture_stream = nullptr;
@@ -69,8 +71,8 @@ namespace {
         }                                                                                   \
     } while (0)
 
-constexpr int32_t kDefaultWarpsPerBlock = 8;
-constexpr int32_t kDefaultBlocksPerSm = 8;
+constexpr int32_t kDefaultWarpsPerBlock = 4;
+constexpr int32_t kDefaultBlocksPerSm = 16;
 constexpr int32_t kDefaultRolloutsPerLane = 32;
 
 bool finite(float x) { return std::isfinite(x); }
@@ -109,35 +111,49 @@ double est_steps(const bbe_batch *b, int r)
     return 1.0 + double(b->h_L[r] - lead) / double(std::max(vmax, 1e-3f));
 }
 
+// Competitors per lane for a race of n: two when that fills more of the warp's lanes.
+int slots_for(int n, int mode)
+{
+    if (mode == 1 || n < 2) return 1;
+    if (mode == 2) return 2;
+    const int used1 = n * (32 / n);
+    const int used2 = n * (32 / ((n + 1) / 2));  // of 64 slots
+    return 2 * used1 < used2 ? 2 : 1;
+}
+
 bbe_status build_items(bbe_batch *b)
 {
-    std::vector<bbe::WorkItem> items;
-    std::vector<double> cost;
+    std::vector<bbe::WorkItem> items[2];
+    std::vector<double> cost[2];
     const int64_t per_lane = b->cfg.rollouts_per_lane;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
-        const int nseg = 32 / n;
+        const int v = slots_for(n, b->cfg.slots_per_lane);
+        const int nseg = 32 / ((n + v - 1) / v);
         const int64_t chunk = per_lane * nseg;
         const double st = est_steps(b, r);
         for (int64_t k = 0; k < b->h_R[r]; k += chunk) {
             const int64_t cnt = std::min<int64_t>(chunk, b->h_R[r] - k);
-            items.push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
-            cost.push_back(double((cnt + nseg - 1) / nseg) * st);
+            items[v - 1].push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
+            cost[v - 1].push_back(double((cnt + nseg - 1) / nseg) * st);
         }
     }
-    if (items.size() > size_t(INT32_MAX)) {
+    if (items[0].size() + items[1].size() > size_t(INT32_MAX)) {
         set_error("work list too long; raise rollouts_per_lane");
         return BBE_ERR_RANGE;
     }
-    std::vector<int32_t> order(items.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
-    std::vector<bbe::WorkItem> sorted(items.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    std::vector<bbe::WorkItem> sorted;
+    sorted.reserve(items[0].size() + items[1].size());
+    for (int v = 0; v < 2; ++v) {
+        std::vector<int32_t> order(items[v].size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[v][x] > cost[v][y]; });
+        for (int32_t i : order) sorted.push_back(items[v][i]);
+        b->n_items_v[v] = int32_t(items[v].size());
+    }
 
     if (b->d_items) cudaFree(b->d_items);
     b->d_items = nullptr;
-    b->n_items = int32_t(sorted.size());
     BBE_CUDA_TRY(cudaMalloc(&b->d_items, std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem)));
     BBE_CUDA_TRY(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice));
     free_graph(b);
@@ -147,39 +163,52 @@ bbe_status build_items(bbe_batch *b)
 bbe_status check_cfg(const bbe_launch_cfg &c)
 {
     if (c.warps_per_block < 1 || c.warps_per_block > 16 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
-        c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30)) {
+        c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30) ||
+        c.slots_per_lane < 0 || c.slots_per_lane > 2) {
         set_error("launch configuration out of range");
         return BBE_ERR_ARG;
     }
     return BBE_OK;
 }
 
-bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *steps)
+bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *steps, int v)
 {
     bbe::RolloutLaunch l{};
     l.b = b->dev;
-    l.items = b->d_items;
-    l.n_items = b->n_items;
-    l.queue = b->d_queue;
+    l.items = b->d_items + (v == 2 ? b->n_items_v[0] : 0);
+    l.n_items = b->n_items_v[v - 1];
+    l.queue = b->d_queue + (v - 1);
     l.counts = counts;
     l.steps = reinterpret_cast<unsigned long long *>(steps);
     l.status = b->d_status;
     l.max_steps = b->cfg.max_steps;
     l.block = 32 * b->cfg.warps_per_block;
     // persistent grid: never more blocks than can be resident at once
-    l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident)));
+    l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident[v - 1])));
     return l;
 }
 
-// The launch sequence of one rollout pass: reset queue, status and outputs, then the
-// persistent kernel.
-cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cudaStream_t s)
+// The launch sequence of one rollout pass: reset queues, status and outputs, then the
+// persistent kernels (two-slot races first).  With a side stream the two kernels are
+// forked so that the second fills SMs as the first one's blocks retire.
+cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cudaStream_t s, cudaStream_t side)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, size_t(b->n_total) * sizeof(int32_t), s);
     if (e == cudaSuccess && steps) e = cudaMemsetAsync(steps, 0, size_t(b->n_races) * sizeof(int64_t), s);
-    if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps), s);
+    const bool both = b->n_items_v[0] > 0 && b->n_items_v[1] > 0;
+    if (e == cudaSuccess && both && side) {
+        e = cudaEventRecord(b->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_fork, 0);
+        if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps, 2), 2, s);
+        if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps, 1), 1, side);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
+        return e;
+    }
+    if (e == cudaSuccess && b->n_items_v[1] > 0) e = bbe::launch_rollout(make_launch(b, counts, steps, 2), 2, s);
+    if (e == cudaSuccess && b->n_items_v[0] > 0) e = bbe::launch_rollout(make_launch(b, counts, steps, 1), 1, s);
     return e;
 }
 
@@ -188,8 +217,11 @@ bbe_status ensure_graph(bbe_batch *b, int32_t *counts, int64_t *steps)
     if (b->gexec && b->g_counts == counts && b->g_steps == steps) return BBE_OK;
     free_graph(b);
     if (!b->capture_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    if (!b->side_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
+    if (!b->ev_fork) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    if (!b->ev_join) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
     BBE_CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_pass(b, counts, steps, b->capture_stream);
+    cudaError_t e = enqueue_pass(b, counts, steps, b->capture_stream, b->side_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -355,7 +387,7 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
     add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4);
     for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
-    add(4); add(4);
+    add(8); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
@@ -371,7 +403,7 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
     float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
     float *d_prev = carve<float>(p, nt);
-    b->d_queue = carve<int32_t>(p, 1);
+    b->d_queue = carve<int32_t>(p, 2);
     b->d_status = carve<int32_t>(p, 1);
     struct {
         void *dst;
@@ -394,8 +426,8 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     b->dev = bbe::DevBatch{d_off, d_L, d_R, d_cr, d_d0, d_mu, d_sigma, d_rho, d_P, d_theta,
                            prev_step ? d_prev : nullptr, n_races, nt, race_id0, uint32_t(seed), uint32_t(seed >> 32),
                            int32_t(dist)};
-    b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT};
-    b->resident = bbe::rollout_resident_blocks(b->dist, 32 * kDefaultWarpsPerBlock);
+    b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT, 0};
+    for (int v = 1; v <= 2; ++v) b->resident[v - 1] = bbe::rollout_resident_blocks(b->dist, v, 32 * kDefaultWarpsPerBlock);
     if ((st = build_items(b))) return fail(st);
     *out = b;
     return BBE_OK;
@@ -453,9 +485,9 @@ bbe_status bbe_batch_set_cfg(bbe_batch *b, const bbe_launch_cfg *cfg)
     if (c.max_steps == 0) c.max_steps = BBE_MAX_STEPS_DEFAULT;
     bbe_status st = check_cfg(c);
     if (st) return st;
-    const bool rebuild = c.rollouts_per_lane != b->cfg.rollouts_per_lane;
+    const bool rebuild = c.rollouts_per_lane != b->cfg.rollouts_per_lane || c.slots_per_lane != b->cfg.slots_per_lane;
     b->cfg = c;
-    b->resident = bbe::rollout_resident_blocks(b->dist, 32 * c.warps_per_block);
+    for (int v = 1; v <= 2; ++v) b->resident[v - 1] = bbe::rollout_resident_blocks(b->dist, v, 32 * c.warps_per_block);
     free_graph(b);
     return rebuild ? build_items(b) : BBE_OK;
 }
@@ -490,11 +522,11 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     bbe_status st = BBE_OK;
     for (int32_t pl : per_lane) {
         for (auto &sh : shapes) {
-            bbe_launch_cfg c{sh[0], sh[1], pl, start.max_steps};
+            bbe_launch_cfg c{sh[0], sh[1], pl, start.max_steps, start.slots_per_lane};
             if ((st = bbe_batch_set_cfg(b, &c))) goto done;
             // warm the item list, then time one full pass
             cudaEventRecord(e0, s);
-            if (enqueue_pass(b, win_counts, nullptr, s) != cudaSuccess) {
+            if (enqueue_pass(b, win_counts, nullptr, s, nullptr) != cudaSuccess) {
                 set_error("autotune launch failed");
                 st = BBE_ERR_CUDA;
                 goto done;
@@ -545,6 +577,9 @@ void bbe_destroy_batch(bbe_batch *b)
     cudaDeviceSynchronize();
     free_graph(b);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->side_stream) cudaStreamDestroy(b->side_stream);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->d_items) cudaFree(b->d_items);
     if (b->arena) cudaFree(b->arena);
     delete b;

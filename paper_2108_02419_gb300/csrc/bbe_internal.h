@@ -48,9 +48,10 @@ struct RolloutLaunch {
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;
 
-cudaError_t launch_rollout(const RolloutLaunch &l, cudaStream_t stream);
+// slots_per_lane: competitors held per lane (1 or 2).
+cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
 // Blocks of `block` threads of the rollout kernel that fit on one SM at once.
-int rollout_resident_blocks(int dist, int block);
+int rollout_resident_blocks(int dist, int slots_per_lane, int block);
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
                              cudaStream_t stream);
 

@@ -1,16 +1,19 @@
 // bbe_rollout.cu -- the Monte Carlo rollout kernel and the win-probability finaliser.
 //
-// One warp runs the rollouts of one race at a time with competitors in lanes: a race of
-// n competitors occupies a segment of n lanes, and a warp packs floor(32 / n) segments,
-// each running its own sequence of rollouts of the same race (Section 3 dry-runs).
-// Warps pull work items (race, rollout range) from a global queue: one persistent launch
-// covers races of any size mix.  The race's parameters are staged in shared memory per
-// warp.  Per step every lane evaluates Eq. 1 for the competitor it holds; lanes keep the
-// competitors in rank order, so the nearest competitor in front (i+) is one shuffle away;
-// finishing is detected with a ballot and the winner (least within-step crossing time,
-// lowest index on ties) found from the ballot mask, or by a shuffle reduction when
-// several cross in the same step.  Each lane counts the wins of the competitor that starts
-// every rollout in it; the counts are reduced once per work item.
+// One warp runs the rollouts of one race at a time.  A race of n competitors occupies a
+// segment of ceil(n / V) lanes, each lane holding V consecutive ranks (V = 1 or 2), and a
+// warp packs floor(32 / lanes) segments, each running its own sequence of rollouts of the
+// same race (Section 3 dry-runs).  Warps pull work items (race, rollout range) from a
+// global queue: one persistent launch per V covers races of any size mix.  The race's
+// parameters are staged in shared memory per warp.
+//
+// Per step every slot evaluates Eq. 1 for the competitor it holds.  Slots keep the
+// competitors in rank order (ascending position, then index), so the nearest competitor
+// strictly in front (i+) is the next slot: a register (same lane) or one shuffle (next
+// lane).  Finishing is detected with a ballot; the winner (least within-step crossing time,
+// lowest index on ties) comes from the ballot mask, or from a shuffle reduction when several
+// cross in the same step.  Each slot counts the wins of the competitor that starts every
+// rollout in it; the counts are reduced once per work item.
 //
 // The arithmetic is pinned to binary32 round-to-nearest with explicit intrinsics, and this
 // file is compiled with --fmad=false, so the counts are bit-identical to any
@@ -29,7 +32,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 // Per-warp staging of the current race: competitor parameters by competitor index, and the
-// competitor holding each rank (ascending position, then index) at the start of a rollout.
+// competitor holding each rank at the start of a rollout.
 struct WarpStage {
     float mu[32], sigma[32], P[32], theta[32], kr[32], d0[32], prev0[32];
     int init_c[32];
@@ -44,13 +47,73 @@ __device__ __forceinline__ Params load_params(const WarpStage &st, int c)
     return Params{st.mu[c], st.sigma[c], st.P[c], st.theta[c], st.kr[c]};
 }
 
-// Lanes of a segment hold the race's competitors in rank order: lane p holds the competitor
-// with the p-th smallest (position, index).  The nearest competitor strictly in front of the
-// one in lane p is then the one in lane p+1 (or, when positions are equal, the first later
-// lane with a larger position), found with one shuffle.  After each step the order is
-// restored by odd-even transposition (each competitor's state moves with it); overtakes are
-// rare, so this costs a ballot per step and a few shuffles per overtake.
+// (da, ca) comes after (db, cb) in rank order
+__device__ __forceinline__ bool key_gt(float da, int ca, float db, int cb)
+{
+    return da > db || (da == db && ca > cb);
+}
+
+// The state of one competitor that moves with it when ranks change.
+struct Slot {
+    int c;
+    float d, prev;
+    uint32_t w1, w2, w3;  // Philox words of the current 4-step block
+    float zs;             // sine half of the current Box-Muller pair
+    Params q;
+};
+
+__device__ __forceinline__ Slot shfl_slot(const Slot &s, int src)
+{
+    Slot o;
+    o.c = __shfl_sync(kFull, s.c, src);
+    o.d = __shfl_sync(kFull, s.d, src);
+    o.prev = __shfl_sync(kFull, s.prev, src);
+    o.w1 = __shfl_sync(kFull, s.w1, src);
+    o.w2 = __shfl_sync(kFull, s.w2, src);
+    o.w3 = __shfl_sync(kFull, s.w3, src);
+    o.zs = __shfl_sync(kFull, s.zs, src);
+    o.q = s.q;  // reloaded from shared memory by the caller when the competitor changes
+    return o;
+}
+
+// z for step t of competitor s.c in rollout k: one Philox block per 4 steps, one
+// Box-Muller pair per 2 steps; the rest of the block is cached in the slot.
 template <int DIST>
+__device__ __forceinline__ float draw_z(Slot &s, int t, uint32_t k, uint32_t rid, uint32_t key_lo, uint32_t key_hi)
+{
+    float z;
+    if (DIST == BBE_DIST_NORMAL) {
+        if ((t & 1) == 0) {
+            uint32_t wa = s.w2, wb = s.w3;
+            if ((t & 3) == 0) {
+                const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(s.c), rid, key_lo, key_hi);
+                wa = wd.w0;
+                wb = wd.w1;
+                s.w2 = wd.w2;
+                s.w3 = wd.w3;
+            }
+            box_muller(wa, wb, z, s.zs);
+        } else {
+            z = s.zs;
+        }
+    } else {
+        uint32_t wsel;
+        if ((t & 3) == 0) {
+            const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(s.c), rid, key_lo, key_hi);
+            wsel = wd.w0;
+            s.w1 = wd.w1;
+            s.w2 = wd.w2;
+            s.w3 = wd.w3;
+        } else {
+            const int qq = t & 3;
+            wsel = qq == 1 ? s.w1 : (qq == 2 ? s.w2 : s.w3);
+        }
+        z = DIST == BBE_DIST_UNIFORM ? uniform_z(wsel) : two_point_z(wsel);
+    }
+    return z;
+}
+
+template <int DIST, int V>
 __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
 {
     extern __shared__ WarpStage stage_all[];
@@ -66,13 +129,18 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         const int r = w.race;
         const int off = b.race_off[r];
         const int n = b.race_off[r + 1] - off;
-        const int nseg = 32 / n;
-        const int seg = lane / n;
-        const int p = lane - seg * n;  // rank slot within the segment
+        const int nl = (n + V - 1) / V;  // lanes per segment
+        const int nseg = 32 / nl;
+        const int seg = lane / nl;
+        const int ql = lane - seg * nl;  // lane within the segment
         const bool lane_used = seg < nseg;
-        const int segbase = seg * n;
-        const unsigned segmask = !lane_used ? 0u : (n == 32 ? kFull : (((1u << n) - 1u) << segbase));
-        const bool has_next = lane_used && p + 1 < n;
+        const int segbase = seg * nl;
+        const unsigned segmask = !lane_used ? 0u : (nl == 32 ? kFull : (((1u << nl) - 1u) << segbase));
+        const bool has_next_lane = lane_used && ql + 1 < nl;
+        const int rank0 = ql * V;
+        bool valid[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) valid[v] = lane_used && rank0 + v < n;
 
         // stage the race: lane j < n loads competitor j (coalesced) and ranks it
         __syncwarp();
@@ -100,131 +168,173 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         const float L = b.L[r];
         const float invL = __fdiv_rn(1.0f, L);
         const uint32_t rid = b.race_id0 + uint32_t(r);
-        const int home = lane_used ? st.init_c[p] : 0;  // this lane counts wins of `home`
         const int kend = w.k_begin + w.k_count;
         int k = w.k_begin + seg;
         bool active = lane_used && k < kend;
         int t = 0;
         unsigned gstep = 0;
-        int c = home;
-        float d = st.d0[c], prev = st.prev0[c];
-        Params q = load_params(st, c);
-        uint32_t w1 = 0u, w2 = 0u, w3 = 0u;  // Philox words of the current 4-step block
-        float zs = 0.0f;                    // sine half of the current Box-Muller pair
-        int wins = 0;
+        int home[V], wins[V];
+        Slot s[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            home[v] = valid[v] ? st.init_c[rank0 + v] : 0;
+            wins[v] = 0;
+            s[v].c = home[v];
+            s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
+            s[v].prev = st.prev0[home[v]];
+            s[v].w1 = s[v].w2 = s[v].w3 = 0u;
+            s[v].zs = 0.0f;
+            s[v].q = load_params(st, home[v]);
+        }
         long long steps = 0;
         bool hit_limit = false;
 
         while (__any_sync(kFull, active)) {
             const bool running = active && t >= 0;
             // delta(v_c): z for (race, rollout k, step t, competitor c)
-            float z = 0.0f;
-            if (running) {
-                if (DIST == BBE_DIST_NORMAL) {
-                    if ((t & 1) == 0) {
-                        uint32_t wa = w2, wb = w3;
-                        if ((t & 3) == 0) {
-                            const Words4 wd = philox4x32_10(uint32_t(k), uint32_t(t) >> 2, uint32_t(c), rid,
-                                                            b.seed_lo, b.seed_hi);
-                            wa = wd.w0;
-                            wb = wd.w1;
-                            w2 = wd.w2;
-                            w3 = wd.w3;
+            float z[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                z[v] = 0.0f;
+                if (running && valid[v]) z[v] = draw_z<DIST>(s[v], t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
+            }
+            // i+: the next rank (same lane, or slot 0 of the next lane)
+            float fd[V], fp[V];
+            bool hf[V];
+            {
+                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                const float np = __shfl_down_sync(kFull, s[0].prev, 1);
+#pragma unroll
+                for (int v = 0; v < V - 1; ++v) {
+                    fd[v] = s[v + 1].d;
+                    fp[v] = s[v + 1].prev;
+                    hf[v] = valid[v + 1];
+                }
+                fd[V - 1] = nd;
+                fp[V - 1] = np;
+                hf[V - 1] = valid[V - 1] && has_next_lane;
+            }
+            bool tie = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
+            if (__any_sync(kFull, running && tie)) {
+                // equal positions: the first later rank with a larger position
+#pragma unroll
+                for (int v = 0; v < V; ++v) hf[v] = false;
+                for (int j = 0; j < nl; ++j) {
+                    const int src = lane_used ? segbase + j : lane;
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        const float dj = __shfl_sync(kFull, s[u].d, src);
+                        const float pj = __shfl_sync(kFull, s[u].prev, src);
+                        const int rj = j * V + u;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            if (valid[v] && rj > rank0 + v && rj < n && !hf[v] && dj > s[v].d) {
+                                hf[v] = true;
+                                fd[v] = dj;
+                                fp[v] = pj;
+                            }
                         }
-                        box_muller(wa, wb, z, zs);
-                    } else {
-                        z = zs;
-                    }
-                } else {
-                    uint32_t wsel;
-                    if ((t & 3) == 0) {
-                        const Words4 wd = philox4x32_10(uint32_t(k), uint32_t(t) >> 2, uint32_t(c), rid,
-                                                        b.seed_lo, b.seed_hi);
-                        wsel = wd.w0;
-                        w1 = wd.w1;
-                        w2 = wd.w2;
-                        w3 = wd.w3;
-                    } else {
-                        const int qq = t & 3;
-                        wsel = qq == 1 ? w1 : (qq == 2 ? w2 : w3);
-                    }
-                    z = DIST == BBE_DIST_UNIFORM ? uniform_z(wsel) : two_point_z(wsel);
-                }
-            }
-            // responsiveness R_c
-            const float Rc = __fmaf_rn(q.kr, __fmaf_rn(d, invL, -0.5f), 1.0f);
-            // i+: the next rank; with equal positions, the first later rank strictly in front
-            float fd = __shfl_down_sync(kFull, d, 1);
-            float fp = __shfl_down_sync(kFull, prev, 1);
-            bool has_front = has_next;
-            if (__any_sync(kFull, running && has_next && fd == d)) {
-                has_front = false;
-                for (int i = 1; i < n; ++i) {
-                    const bool ok = lane_used && p + i < n;
-                    const int src = ok ? segbase + p + i : lane;
-                    const float di = __shfl_sync(kFull, d, src);
-                    const float pi = __shfl_sync(kFull, prev, src);
-                    if (ok && !has_front && di > d) {
-                        has_front = true;
-                        fd = di;
-                        fp = pi;
                     }
                 }
             }
-            // Eq. 1
-            const bool blocked = has_front && !(__fsub_rn(fd, d) > q.theta);
-            float S = blocked ? __fmul_rn(Rc, fminf(prev, fp))
-                              : __fmul_rn(__fmul_rn(Rc, q.P), __fmaf_rn(q.sigma, z, q.mu));
-            S = fmaxf(S, kStepFloor);
-            const float dn = __fadd_rn(d, S);
-
-            // finish: least within-step crossing time, ties to the lowest competitor index
+            // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
-            const bool fin = running && !aborted && dn >= L;
-            const unsigned fmask = __ballot_sync(kFull, fin);
-            const unsigned amask = __ballot_sync(kFull, aborted);
-            const unsigned my_f = fmask & segmask;
-            const bool seg_done = ((fmask | amask) & segmask) != 0u;
-            if (fmask != 0u) {
-                int wl = my_f ? (__ffs(my_f) - 1) : lane;
-                if (__any_sync(kFull, __popc(my_f) > 1)) {
-                    const float tau = fin ? __fdiv_rn(__fsub_rn(L, d), S) : INFINITY;
+            float S[V], dn[V];
+            bool fin[V], any_fin = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float Rc = __fmaf_rn(s[v].q.kr, __fmaf_rn(s[v].d, invL, -0.5f), 1.0f);
+                const bool blocked = hf[v] && !(__fsub_rn(fd[v], s[v].d) > s[v].q.theta);
+                float Sv = blocked ? __fmul_rn(Rc, fminf(s[v].prev, fp[v]))
+                                   : __fmul_rn(__fmul_rn(Rc, s[v].q.P), __fmaf_rn(s[v].q.sigma, z[v], s[v].q.mu));
+                Sv = fmaxf(Sv, kStepFloor);
+                S[v] = Sv;
+                dn[v] = __fadd_rn(s[v].d, Sv);
+                fin[v] = running && valid[v] && !aborted && dn[v] >= L;
+                any_fin |= fin[v];
+            }
+            // finish: least within-step crossing time, ties to the lowest competitor index
+            bool seg_fin = false, seg_done = false;
+            if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
+                const unsigned amask = __ballot_sync(kFull, aborted);
+                unsigned fm[V];
+                int nfin = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
+                    nfin += __popc(fm[v]);
+                }
+                seg_fin = nfin > 0;
+                seg_done = seg_fin || (amask & segmask) != 0u;
+                int wl = lane, wv = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (fm[v] != 0u) {
+                        wl = __ffs(fm[v]) - 1;
+                        wv = v;
+                    }
+                }
+                if (__any_sync(kFull, nfin > 1)) {
                     float best = INFINITY;
-                    int bestc = 1 << 30, bl = wl;
-                    for (int i = 0; i < n; ++i) {
-                        const int src = lane_used ? segbase + i : lane;
-                        const float ti = __shfl_sync(kFull, tau, src);
-                        const int ci = __shfl_sync(kFull, c, src);
-                        if (ti < best || (ti == best && ti < INFINITY && ci < bestc)) {
-                            best = ti;
-                            bestc = ci;
-                            bl = src;
+                    int bestc = 1 << 30, bl = wl, bv = wv;
+                    for (int j = 0; j < nl; ++j) {
+                        const int src = lane_used ? segbase + j : lane;
+#pragma unroll
+                        for (int u = 0; u < V; ++u) {
+                            const float tau = fin[u] ? __fdiv_rn(__fsub_rn(L, s[u].d), S[u]) : INFINITY;
+                            const float tj = __shfl_sync(kFull, tau, src);
+                            const int cj = __shfl_sync(kFull, s[u].c, src);
+                            if (tj < best || (tj == best && tj < INFINITY && cj < bestc)) {
+                                best = tj;
+                                bestc = cj;
+                                bl = src;
+                                bv = u;
+                            }
                         }
                     }
-                    if (my_f) wl = bl;
+                    if (nfin > 1) {
+                        wl = bl;
+                        wv = bv;
+                    }
                 }
-                const int cw = __shfl_sync(kFull, c, wl);
-                if (my_f != 0u && home == cw) ++wins;
+                int cw = __shfl_sync(kFull, s[0].c, wl);
+                if (V == 2) {
+                    const int cw1 = __shfl_sync(kFull, s[V - 1].c, wl);
+                    cw = wv ? cw1 : cw;
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
             }
 
             // advance, or start the segment's next rollout
             if (active) {
                 if (running) {
                     if (seg_done) {
-                        steps += my_f ? (t + 1) : t;
-                        hit_limit |= (my_f == 0u);
+                        steps += seg_fin ? (t + 1) : t;
+                        hit_limit |= !seg_fin;
                         k += nseg;
                         active = k < kend;
-                        // packed segments start rollouts on a common 4-step phase so
-                        // the warp draws Philox blocks together
+                        // packed segments start rollouts on a common 4-step phase so the
+                        // warp draws its Philox blocks together
                         t = nseg > 1 ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
-                        c = home;
-                        d = st.d0[c];
-                        prev = st.prev0[c];
-                        q = load_params(st, c);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            s[v].c = home[v];
+                            s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
+                            s[v].prev = st.prev0[home[v]];
+                            s[v].q = load_params(st, home[v]);
+                        }
                     } else {
-                        d = dn;
-                        prev = S;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            if (valid[v]) {
+                                s[v].d = dn[v];
+                                s[v].prev = S[v];
+                            }
+                        }
                         ++t;
                     }
                 } else {
@@ -233,43 +343,76 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             }
             ++gstep;
 
-            // restore rank order (odd-even transposition), moving each competitor's state
-            {
-                const float nd = __shfl_down_sync(kFull, d, 1);
-                const int nc = __shfl_down_sync(kFull, c, 1);
-                bool ooo = has_next && (nd < d || (nd == d && nc < c));
+            // restore rank order after overtakes (odd-even transposition)
+            if (V == 1) {
+                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                bool ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
                 while (__any_sync(kFull, ooo)) {
 #pragma unroll
                     for (int ph = 0; ph < 2; ++ph) {
-                        const bool lower = ((p - ph) & 1) == 0;
-                        const int pp = lower ? p + 1 : p - 1;
-                        const bool valid = lane_used && pp >= 0 && pp < n;
-                        const int pl = valid ? segbase + pp : lane;
-                        const float od = __shfl_sync(kFull, d, pl);
-                        const int oc = __shfl_sync(kFull, c, pl);
-                        const bool mine_greater = d > od || (d == od && c > oc);
-                        const bool swap = valid && (lower ? mine_greater : !mine_greater);
-                        const int src = swap ? pl : lane;
-                        c = __shfl_sync(kFull, c, src);
-                        d = __shfl_sync(kFull, d, src);
-                        prev = __shfl_sync(kFull, prev, src);
-                        w1 = __shfl_sync(kFull, w1, src);
-                        w2 = __shfl_sync(kFull, w2, src);
-                        w3 = __shfl_sync(kFull, w3, src);
-                        zs = __shfl_sync(kFull, zs, src);
-                        if (swap) q = load_params(st, c);
+                        const bool lower = ((ql - ph) & 1) == 0;
+                        const int pq = lower ? ql + 1 : ql - 1;
+                        const bool ok = lane_used && pq >= 0 && pq < nl;
+                        const int pl = ok ? segbase + pq : lane;
+                        const float od = __shfl_sync(kFull, s[0].d, pl);
+                        const int oc = __shfl_sync(kFull, s[0].c, pl);
+                        const bool mine_after = key_gt(s[0].d, s[0].c, od, oc);
+                        const bool swap = ok && (lower ? mine_after : !mine_after);
+                        const Slot o = shfl_slot(s[0], swap ? pl : lane);
+                        if (swap) {
+                            s[0] = o;
+                            s[0].q = load_params(st, o.c);
+                        }
                     }
-                    const float nd2 = __shfl_down_sync(kFull, d, 1);
-                    const int nc2 = __shfl_down_sync(kFull, c, 1);
-                    ooo = has_next && (nd2 < d || (nd2 == d && nc2 < c));
+                    const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
+                    ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd2, nc2);
+                }
+            } else {
+                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                bool ooo = (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) ||
+                           (has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc));
+                while (__any_sync(kFull, ooo)) {
+                    // pairs (slot 0, slot 1) within each lane
+                    if (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) {
+                        const Slot tmp = s[0];
+                        s[0] = s[V - 1];
+                        s[V - 1] = tmp;
+                    }
+                    // pairs (slot 1 of lane q, slot 0 of lane q + 1)
+                    const float xd = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int xc = __shfl_down_sync(kFull, s[0].c, 1);
+                    const float yd = __shfl_up_sync(kFull, s[V - 1].d, 1);
+                    const int yc = __shfl_up_sync(kFull, s[V - 1].c, 1);
+                    const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, xd, xc);
+                    const bool swap_lo = lane_used && ql > 0 && key_gt(yd, yc, s[0].d, s[0].c);
+                    const Slot from_next = shfl_slot(s[0], swap_hi ? lane + 1 : lane);
+                    const Slot from_prev = shfl_slot(s[V - 1], swap_lo ? lane - 1 : lane);
+                    if (swap_hi) {
+                        s[V - 1] = from_next;
+                        s[V - 1].q = load_params(st, from_next.c);
+                    }
+                    if (swap_lo) {
+                        s[0] = from_prev;
+                        s[0].q = load_params(st, from_prev.c);
+                    }
+                    const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
+                    ooo = (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) ||
+                          (has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2));
                 }
             }
         }
         // one reduction per work item: wins of each home competitor summed over segments
-        int total = 0;
-        for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins, s2 * n + (lane_used ? p : 0));
-        if (seg == 0 && total != 0) atomicAdd(&l.counts[off + home], total);
-        unsigned long long stp = (lane_used && p == 0) ? (unsigned long long)steps : 0ull;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            int total = 0;
+            for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
+            if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
+        }
+        unsigned long long stp = (lane_used && ql == 0) ? (unsigned long long)steps : 0ull;
         for (int o = 16; o > 0; o >>= 1) stp += __shfl_xor_sync(kFull, stp, o);
         if (lane == 0 && l.steps != nullptr) atomicAdd(&l.steps[r], stp);
         if (__any_sync(kFull, hit_limit) && lane == 0) atomicOr(l.status, kStatusStepLimit);
@@ -287,30 +430,48 @@ __global__ void win_probs_kernel(DevBatch b, const int32_t *__restrict__ counts,
     if (odds) odds[i] = __fdiv_rn(1.0f, p);
 }
 
-}  // namespace
-
-cudaError_t launch_rollout(const RolloutLaunch &l, cudaStream_t stream)
+template <int V>
+cudaError_t launch_v(const RolloutLaunch &l, cudaStream_t stream)
 {
     const size_t smem = size_t(l.block / 32) * sizeof(WarpStage);
     switch (l.b.dist) {
-    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL><<<l.grid, l.block, smem, stream>>>(l); break;
-    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM><<<l.grid, l.block, smem, stream>>>(l); break;
-    default: rollout_kernel<BBE_DIST_TWO_POINT><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL, V><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM, V><<<l.grid, l.block, smem, stream>>>(l); break;
+    default: rollout_kernel<BBE_DIST_TWO_POINT, V><<<l.grid, l.block, smem, stream>>>(l); break;
     }
     return cudaGetLastError();
 }
 
-int rollout_resident_blocks(int dist, int block)
+template <int V>
+int resident_v(int dist, int block)
 {
     const size_t smem = size_t(block / 32) * sizeof(WarpStage);
     int nb = 0;
     cudaError_t e;
     switch (dist) {
-    case BBE_DIST_NORMAL: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL>, block, smem); break;
-    case BBE_DIST_UNIFORM: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM>, block, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT>, block, smem); break;
+    case BBE_DIST_NORMAL:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL, V>, block, smem);
+        break;
+    case BBE_DIST_UNIFORM:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM, V>, block, smem);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT, V>, block, smem);
+        break;
     }
     return e == cudaSuccess ? nb : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
+{
+    return slots_per_lane == 2 ? launch_v<2>(l, stream) : launch_v<1>(l, stream);
+}
+
+int rollout_resident_blocks(int dist, int slots_per_lane, int block)
+{
+    return slots_per_lane == 2 ? resident_v<2>(dist, block) : resident_v<1>(dist, block);
 }
 
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
