@@ -162,6 +162,41 @@ BBE_API bbe_status bbe_batch_info(const bbe_batch *batch, int32_t *n_races, int6
  * that uses it first. */
 BBE_API void bbe_destroy_batch(bbe_batch *batch);
 
+/* bbe_rollout_noalloc -- the rollout pass of bbe_race_init + bbe_rollout_batch for callers
+ * that cannot allocate GPU memory.  The paper has no counterpart: it exists for code that
+ * may not call cudaMalloc where it needs win counts (inside a memory pool it does not own,
+ * in a latency-bound loop where an allocation could synchronise the device, or under an
+ * allocator that another framework holds).
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its work list,
+ * queue heads and status word live in one file-scope device array of 1,179,680 bytes
+ * (a 32-byte header, 2 x BBE_NOALLOC_MAX_RACES int32 per-race counts and
+ * BBE_NOALLOC_MAX_ITEMS 16-byte work items) that every GPU which loads the library holds
+ * until the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before any
+ * stream capture on the device.
+ *
+ * Arguments are those of bbe_race_init plus the outputs of bbe_rollout_batch, with these
+ * differences: every array must be device memory (host pointers are rejected), pref and
+ * theta are required, n_competitors = race_off[n_races] is the length of the per-competitor
+ * arrays, and the launch shape is the library default.  Counts and step totals are
+ * identical to bbe_rollout_batch's for the same inputs.
+ *
+ * Synchronous: the call synchronises cuda_stream after validating the batch on the device
+ * and again after the rollouts, and returns their status.  All calls share the array: calls
+ * that overlap on the GPU (from several host threads or streams) race and must be
+ * serialised by the caller; each call resets what it reads before use.
+ * Errors: BBE_ERR_RANGE (n_races outside 1..BBE_NOALLOC_MAX_RACES), BBE_ERR_ARG,
+ * BBE_ERR_UNSUPPORTED, BBE_ERR_FINISHED (as bbe_race_init), BBE_ERR_STEP_LIMIT, BBE_ERR_CUDA. */
+#define BBE_NOALLOC_MAX_RACES 16384
+#define BBE_NOALLOC_MAX_ITEMS 65536
+BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_competitors, const int32_t *race_off,
+                                       const float *track_len, const int64_t *rollouts, const float *pos,
+                                       const float *mu, const float *sigma, const float *resp, const float *pref,
+                                       const float *theta, const float *prev_step, uint64_t seed, bbe_dist dist,
+                                       uint32_t race_id0, int32_t *win_counts, int64_t *steps_total,
+                                       void *cuda_stream);
+
 /* bbe_last_error -- thread-local message of the last failed call on this thread. */
 BBE_API const char *bbe_last_error(void);
 

@@ -58,6 +58,7 @@ def lib():
             "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_autotune": [vp, vp, C.c_double, vp],
             "bbe_batch_info": [vp, vp, vp, vp, vp],
+            "bbe_rollout_noalloc": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, C.c_int, u32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -163,6 +164,18 @@ def bbe_batch_info(batch: int) -> dict:
 def bbe_destroy_batch(batch: int) -> None:
     if batch:
         lib().bbe_destroy_batch(batch)
+
+
+def bbe_rollout_noalloc(n_races, n_competitors, race_off, track_len, rollouts, pos, mu, sigma, resp, pref, theta,
+                        prev_step, seed, dist, race_id0, win_counts, steps_total=None, stream=None) -> None:
+    """Rollout pass that allocates no memory (device arrays only; see include/bbe.h)."""
+    _check(lib().bbe_rollout_noalloc(int(n_races), int(n_competitors), _ptr(race_off, np.int32),
+                                     _ptr(track_len, np.float32), _ptr(rollouts, np.int64), _ptr(pos, np.float32),
+                                     _ptr(mu, np.float32), _ptr(sigma, np.float32), _ptr(resp, np.float32),
+                                     _ptr(pref, np.float32), _ptr(theta, np.float32), _ptr(prev_step, np.float32),
+                                     int(seed) & (2**64 - 1), int(dist), int(race_id0) & 0xFFFFFFFF,
+                                     _ptr(win_counts, np.int32), _ptr(steps_total, np.int64), _stream(stream)),
+           "bbe_rollout_noalloc")
 
 
 def bbe_last_error() -> str:
