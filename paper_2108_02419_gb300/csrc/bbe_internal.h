@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bbe.h"
+#include "bbe.h"
 
 namespace bbe {
 

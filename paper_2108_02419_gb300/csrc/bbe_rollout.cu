@@ -31,21 +31,17 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Per-warp staging of the current race: competitor parameters by competitor index, and the
-// competitor holding each rank at the start of a rollout.
+// Per-warp staging of the current race, indexed by competitor: parameters, start state,
+// the competitor holding each rank at the start of a rollout, and the normals of the
+// current 4-step Philox block that are still to be used (by segment and competitor, so
+// that they stay with the competitor when ranks change).
 struct WarpStage {
-    float mu[32], sigma[32], P[32], theta[32], kr[32], d0[32], prev0[32];
+    float4 pq[32];  // (mu, sigma, P, theta)
+    float kr[32];
+    float d0[32], prev0[32];
     int init_c[32];
+    float zc[3][64];
 };
-
-struct Params {
-    float mu, sigma, P, theta, kr;
-};
-
-__device__ __forceinline__ Params load_params(const WarpStage &st, int c)
-{
-    return Params{st.mu[c], st.sigma[c], st.P[c], st.theta[c], st.kr[c]};
-}
 
 // (da, ca) comes after (db, cb) in rank order
 __device__ __forceinline__ bool key_gt(float da, int ca, float db, int cb)
@@ -57,60 +53,41 @@ __device__ __forceinline__ bool key_gt(float da, int ca, float db, int cb)
 struct Slot {
     int c;
     float d, prev;
-    uint32_t w1, w2, w3;  // Philox words of the current 4-step block
-    float zs;             // sine half of the current Box-Muller pair
-    Params q;
 };
 
 __device__ __forceinline__ Slot shfl_slot(const Slot &s, int src)
 {
-    Slot o;
-    o.c = __shfl_sync(kFull, s.c, src);
-    o.d = __shfl_sync(kFull, s.d, src);
-    o.prev = __shfl_sync(kFull, s.prev, src);
-    o.w1 = __shfl_sync(kFull, s.w1, src);
-    o.w2 = __shfl_sync(kFull, s.w2, src);
-    o.w3 = __shfl_sync(kFull, s.w3, src);
-    o.zs = __shfl_sync(kFull, s.zs, src);
-    o.q = s.q;  // reloaded from shared memory by the caller when the competitor changes
-    return o;
+    return Slot{__shfl_sync(kFull, s.c, src), __shfl_sync(kFull, s.d, src), __shfl_sync(kFull, s.prev, src)};
 }
 
-// z for step t of competitor s.c in rollout k: one Philox block per 4 steps, one
-// Box-Muller pair per 2 steps; the rest of the block is cached in the slot.
+// z for step t of competitor c in rollout k (Eq. 1's delta(v_c) = mu + sigma z): a
+// Philox block serves steps t .. t+3 (t a multiple of 4); its first z is returned and the
+// other three are cached in shared memory for the following steps.
 template <int DIST>
-__device__ __forceinline__ float draw_z(Slot &s, int t, uint32_t k, uint32_t rid, uint32_t key_lo, uint32_t key_hi)
+__device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uint32_t k, uint32_t rid,
+                                        uint32_t key_lo, uint32_t key_hi)
 {
-    float z;
+    if ((t & 3) != 0) return st.zc[(t & 3) - 1][zi];
+    const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, key_lo, key_hi);
+    float z0, z1, z2, z3;
     if (DIST == BBE_DIST_NORMAL) {
-        if ((t & 1) == 0) {
-            uint32_t wa = s.w2, wb = s.w3;
-            if ((t & 3) == 0) {
-                const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(s.c), rid, key_lo, key_hi);
-                wa = wd.w0;
-                wb = wd.w1;
-                s.w2 = wd.w2;
-                s.w3 = wd.w3;
-            }
-            box_muller(wa, wb, z, s.zs);
-        } else {
-            z = s.zs;
-        }
+        box_muller(wd.w0, wd.w1, z0, z1);
+        box_muller(wd.w2, wd.w3, z2, z3);
+    } else if (DIST == BBE_DIST_UNIFORM) {
+        z0 = uniform_z(wd.w0);
+        z1 = uniform_z(wd.w1);
+        z2 = uniform_z(wd.w2);
+        z3 = uniform_z(wd.w3);
     } else {
-        uint32_t wsel;
-        if ((t & 3) == 0) {
-            const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(s.c), rid, key_lo, key_hi);
-            wsel = wd.w0;
-            s.w1 = wd.w1;
-            s.w2 = wd.w2;
-            s.w3 = wd.w3;
-        } else {
-            const int qq = t & 3;
-            wsel = qq == 1 ? s.w1 : (qq == 2 ? s.w2 : s.w3);
-        }
-        z = DIST == BBE_DIST_UNIFORM ? uniform_z(wsel) : two_point_z(wsel);
+        z0 = two_point_z(wd.w0);
+        z1 = two_point_z(wd.w1);
+        z2 = two_point_z(wd.w2);
+        z3 = two_point_z(wd.w3);
     }
-    return z;
+    st.zc[0][zi] = z1;
+    st.zc[1][zi] = z2;
+    st.zc[2][zi] = z3;
+    return z0;
 }
 
 template <int DIST, int V>
@@ -135,6 +112,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         const int ql = lane - seg * nl;  // lane within the segment
         const bool lane_used = seg < nseg;
         const int segbase = seg * nl;
+        const int zbase = lane_used ? seg * n : 0;  // this segment's row of the z cache
         const unsigned segmask = !lane_used ? 0u : (nl == 32 ? kFull : (((1u << nl) - 1u) << segbase));
         const bool has_next_lane = lane_used && ql + 1 < nl;
         const int rank0 = ql * V;
@@ -149,10 +127,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             const int ci = off + lane;
             const float mu = b.mu[ci], P = b.P[ci];
             my_d0 = b.d0[ci];
-            st.mu[lane] = mu;
-            st.sigma[lane] = b.sigma[ci];
-            st.P[lane] = P;
-            st.theta[lane] = b.theta[ci];
+            st.pq[lane] = make_float4(mu, b.sigma[ci], P, b.theta[ci]);
             st.kr[lane] = __fmul_rn(kKappa, __fsub_rn(__fmul_rn(2.0f, b.rho[ci]), 1.0f));
             st.d0[lane] = my_d0;
             st.prev0[lane] = b.prev0 ? b.prev0[ci] : __fmul_rn(mu, P);
@@ -182,21 +157,20 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             s[v].c = home[v];
             s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
             s[v].prev = st.prev0[home[v]];
-            s[v].w1 = s[v].w2 = s[v].w3 = 0u;
-            s[v].zs = 0.0f;
-            s[v].q = load_params(st, home[v]);
         }
         long long steps = 0;
         bool hit_limit = false;
 
         while (__any_sync(kFull, active)) {
+            __syncwarp();  // z-cache writes of earlier steps are visible to every lane
             const bool running = active && t >= 0;
             // delta(v_c): z for (race, rollout k, step t, competitor c)
             float z[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 z[v] = 0.0f;
-                if (running && valid[v]) z[v] = draw_z<DIST>(s[v], t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
+                if (running && valid[v])
+                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
             }
             // i+: the next rank (same lane, or slot 0 of the next lane)
             float fd[V], fp[V];
@@ -245,10 +219,12 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             bool fin[V], any_fin = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float Rc = __fmaf_rn(s[v].q.kr, __fmaf_rn(s[v].d, invL, -0.5f), 1.0f);
-                const bool blocked = hf[v] && !(__fsub_rn(fd[v], s[v].d) > s[v].q.theta);
+                const float4 q = st.pq[s[v].c];  // (mu, sigma, P, theta)
+                const float kr = st.kr[s[v].c];
+                const float Rc = __fmaf_rn(kr, __fmaf_rn(s[v].d, invL, -0.5f), 1.0f);
+                const bool blocked = hf[v] && !(__fsub_rn(fd[v], s[v].d) > q.w);
                 float Sv = blocked ? __fmul_rn(Rc, fminf(s[v].prev, fp[v]))
-                                   : __fmul_rn(__fmul_rn(Rc, s[v].q.P), __fmaf_rn(s[v].q.sigma, z[v], s[v].q.mu));
+                                   : __fmul_rn(__fmul_rn(Rc, q.z), __fmaf_rn(q.y, z[v], q.x));
                 Sv = fmaxf(Sv, kStepFloor);
                 S[v] = Sv;
                 dn[v] = __fadd_rn(s[v].d, Sv);
@@ -325,7 +301,6 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                             s[v].c = home[v];
                             s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
                             s[v].prev = st.prev0[home[v]];
-                            s[v].q = load_params(st, home[v]);
                         }
                     } else {
 #pragma unroll
@@ -355,15 +330,9 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                         const int pq = lower ? ql + 1 : ql - 1;
                         const bool ok = lane_used && pq >= 0 && pq < nl;
                         const int pl = ok ? segbase + pq : lane;
-                        const float od = __shfl_sync(kFull, s[0].d, pl);
-                        const int oc = __shfl_sync(kFull, s[0].c, pl);
-                        const bool mine_after = key_gt(s[0].d, s[0].c, od, oc);
-                        const bool swap = ok && (lower ? mine_after : !mine_after);
-                        const Slot o = shfl_slot(s[0], swap ? pl : lane);
-                        if (swap) {
-                            s[0] = o;
-                            s[0].q = load_params(st, o.c);
-                        }
+                        const Slot o = shfl_slot(s[0], pl);
+                        const bool mine_after = key_gt(s[0].d, s[0].c, o.d, o.c);
+                        if (ok && (lower ? mine_after : !mine_after)) s[0] = o;
                     }
                     const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
                     const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
@@ -382,22 +351,12 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                         s[V - 1] = tmp;
                     }
                     // pairs (slot 1 of lane q, slot 0 of lane q + 1)
-                    const float xd = __shfl_down_sync(kFull, s[0].d, 1);
-                    const int xc = __shfl_down_sync(kFull, s[0].c, 1);
-                    const float yd = __shfl_up_sync(kFull, s[V - 1].d, 1);
-                    const int yc = __shfl_up_sync(kFull, s[V - 1].c, 1);
-                    const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, xd, xc);
-                    const bool swap_lo = lane_used && ql > 0 && key_gt(yd, yc, s[0].d, s[0].c);
-                    const Slot from_next = shfl_slot(s[0], swap_hi ? lane + 1 : lane);
-                    const Slot from_prev = shfl_slot(s[V - 1], swap_lo ? lane - 1 : lane);
-                    if (swap_hi) {
-                        s[V - 1] = from_next;
-                        s[V - 1].q = load_params(st, from_next.c);
-                    }
-                    if (swap_lo) {
-                        s[0] = from_prev;
-                        s[0].q = load_params(st, from_prev.c);
-                    }
+                    const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
+                    const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
+                    const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, from_next.d, from_next.c);
+                    const bool swap_lo = lane_used && ql > 0 && key_gt(from_prev.d, from_prev.c, s[0].d, s[0].c);
+                    if (swap_hi) s[V - 1] = from_next;
+                    if (swap_lo) s[0] = from_prev;
                     const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
                     const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
                     ooo = (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) ||
