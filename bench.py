@@ -155,6 +155,25 @@ def measured_peaks() -> dict:
     return {}
 
 
+def kernel_traffic(workload: str, races: int):
+    """DRAM bytes per rollout launch from the committed ncu record, or None when the kernel
+    sources changed since the counters were taken (or the workload is not the recorded one)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.json")
+    if races or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in ("bbe_rollout.cu", "bbe_rng.cuh"):
+        with open(os.path.join(ROOT, "paper_2108_02419_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
+        return None
+    w = rec.get("workloads", {}).get(workload)
+    return None if w is None else w["dram_bytes_per_launch"]
+
+
 def competitor_steps(rb: W.RaceBatch, steps_total: np.ndarray) -> int:
     return int((rb.sizes() * steps_total.astype(np.int64)).sum())
 
@@ -332,7 +351,7 @@ def run_gpu(args, rank, world, dist):
     roll_s = statistics.mean(roll_ms) / 1e3
     achieved = ALG_OPS_PER_COMPETITOR_STEP * units_per_step / roll_s
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                "frac": achieved / peak_ops, "traffic": None,
+                "frac": achieved / peak_ops, "traffic": kernel_traffic(args.workload, args.races),
                 "kernel": "rollout_kernel", "ops_per_competitor_step": ALG_OPS_PER_COMPETITOR_STEP,
                 "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (maximum SM clock)"}
 
