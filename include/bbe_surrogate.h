@@ -1,0 +1,106 @@
+/*
+ * bbe_surrogate.h -- learned surrogate of the Monte Carlo win probabilities.
+ *
+ * The paper's rational bettors estimate win probabilities by simulating the race d times
+ * (Section 3); the race simulator is the expensive part of the model (Section 6 moves it to
+ * a GPU because millions of dry-runs are needed).  This surrogate is trained on
+ * (race state, Monte Carlo win probabilities) pairs that bbe_rollout_batch produces and
+ * then answers the same question with one network evaluation per race.  The paper has no
+ * learned model; the network below is this library's design:
+ *
+ *   per competitor c: x_c = [d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1]
+ *   encoder  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)  (width 128)
+ *   context  g = mean over the race's competitors of h3
+ *   head     u = relu(W4 [h3; g] + b4) (256 -> 128), logit = w5 . u + b5
+ *   output   softmax of the logits over the race's competitors (so relabelling the
+ *            competitors relabels the output: permutation equivariance)
+ *   loss     cross-entropy against the Monte Carlo probabilities, mean over races.
+ * Matrix products take bfloat16 operands with float32 accumulation; the master weights and
+ * the Adam state are float32.  Parameters are one float vector of bbe_surrogate_num_params()
+ * values: W1 [128][16] (inputs 5..15 zero), b1 [128], W2 [128][128], b2, W3 [128][128], b3,
+ * W4 [128][256], b4, w5 [128], b5 [1] (row-major [out][in]).
+ *
+ * Conventions are those of bbe.h (status codes, thread-local bbe_last_error, caller-owned
+ * buffers, library-owned handles, stream arguments).
+ */
+#ifndef BBE_SURROGATE_H
+#define BBE_SURROGATE_H
+
+#include "bbe.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbe_surrogate bbe_surrogate; /* opaque, library-owned */
+
+typedef struct {
+    float lr;             /* Adam step size */
+    float beta1, beta2;   /* Adam moment decay rates */
+    float eps;            /* Adam denominator guard */
+    float weight_decay;   /* decoupled weight decay per step (AdamW); 0 = none */
+    int32_t batch_states; /* races per optimizer step, >= 1 */
+    int32_t steps;        /* optimizer steps to run in this call, >= 1 */
+    uint64_t shuffle_seed;/* seed of the per-epoch shuffle of the races */
+} bbe_train_cfg;
+
+/* Number of floats in the parameter vector. */
+BBE_API int64_t bbe_surrogate_num_params(void);
+
+/* bbe_surrogate_create -- new network with He-uniform weights drawn from init_seed and zero
+ * biases, on the current device.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_create(bbe_surrogate **out, uint64_t init_seed);
+
+/* bbe_surrogate_set_params / get_params -- copy the float32 parameter vector from / to host
+ * memory (num_params floats).  Setting resets the Adam state.  Synchronous. */
+BBE_API bbe_status bbe_surrogate_set_params(bbe_surrogate *s, const float *params);
+BBE_API bbe_status bbe_surrogate_get_params(const bbe_surrogate *s, float *params);
+
+/* bbe_surrogate_train -- cfg->steps Adam steps on the races of `states` with targets
+ * `target_probs` (device float[sum n], e.g. from bbe_win_probs; each race's targets should
+ * sum to 1).  Each epoch visits the races in a fresh shuffled order; the epoch position is
+ * kept between calls.  The first call on a handle records the ranges of the training
+ * states (competitor counts, track lengths, the five input features, P, theta) that
+ * bbe_surrogate_infer treats as in range.
+ *   loss_log  device float[cfg->steps] or NULL: mean cross-entropy of each step's batch.
+ * Asynchronous on cuda_stream after the host-side planning.  Errors: BBE_ERR_ARG,
+ * BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *states, const float *target_probs,
+                                       const bbe_train_cfg *cfg, float *loss_log, void *cuda_stream);
+
+/* bbe_surrogate_grad -- gradient of the mean cross-entropy over all races of `states`
+ * (device float[num_params], overwritten) and, if loss is not NULL, the loss (device float[1]),
+ * without changing the parameters.  Asynchronous.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_grad(bbe_surrogate *s, const bbe_batch *states, const float *target_probs,
+                                      float *grad, float *loss, void *cuda_stream);
+
+/* bbe_surrogate_forward -- network output for every race of `states`: probs device
+ * float[sum n] (each race's values sum to 1).  No range check.  Asynchronous. */
+BBE_API bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *states, float *probs,
+                                         void *cuda_stream);
+
+/* bbe_surrogate_infer -- win probabilities for every race of `states`: races inside the
+ * training ranges get the network's output; every other race is simulated with plain Monte
+ * Carlo (bbe_rollout_batch with the race's own rollout budget and stream id, so its
+ * probabilities are exactly those of the Monte Carlo path).
+ *   probs   device float[sum n], overwritten.
+ *   used_mc device uint8[n_races] or NULL: 1 where the race fell back to Monte Carlo.
+ * Synchronises cuda_stream when some race falls back.  Errors: BBE_ERR_ARG,
+ * BBE_ERR_CUDA, BBE_ERR_RANGE (no training ranges recorded yet). */
+BBE_API bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *states, float *probs, uint8_t *used_mc,
+                                       void *cuda_stream);
+
+/* bbe_surrogate_save / load -- checkpoint: parameters, Adam state, step count, epoch
+ * position and training ranges, in a little-endian binary file.  load creates a handle on
+ * the current device.  Errors: BBE_ERR_ARG (bad file), BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_save(const bbe_surrogate *s, const char *path);
+BBE_API bbe_status bbe_surrogate_load(bbe_surrogate **out, const char *path);
+
+/* bbe_surrogate_destroy -- free a handle (NULL is ignored). */
+BBE_API void bbe_surrogate_destroy(bbe_surrogate *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBE_SURROGATE_H */

@@ -243,3 +243,102 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ surrogate (include/bbe_surrogate.h)
+
+class bbe_train_cfg(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("weight_decay", C.c_float), ("batch_states", C.c_int32), ("steps", C.c_int32),
+                ("shuffle_seed", C.c_uint64)]
+
+
+_sg_ready = False
+
+
+def _sg():
+    global _sg_ready
+    L = lib()
+    if not _sg_ready:
+        vp = C.c_void_p
+        sig = {
+            "bbe_surrogate_create": [C.POINTER(vp), C.c_uint64],
+            "bbe_surrogate_set_params": [vp, vp],
+            "bbe_surrogate_get_params": [vp, vp],
+            "bbe_surrogate_train": [vp, vp, vp, C.POINTER(bbe_train_cfg), vp, vp],
+            "bbe_surrogate_grad": [vp, vp, vp, vp, vp, vp],
+            "bbe_surrogate_forward": [vp, vp, vp, vp],
+            "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
+            "bbe_surrogate_save": [vp, C.c_char_p],
+            "bbe_surrogate_load": [C.POINTER(vp), C.c_char_p],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.bbe_surrogate_num_params.argtypes = []
+        L.bbe_surrogate_num_params.restype = C.c_int64
+        L.bbe_surrogate_destroy.argtypes = [vp]
+        L.bbe_surrogate_destroy.restype = None
+        _sg_ready = True
+    return L
+
+
+def bbe_surrogate_num_params() -> int:
+    return int(_sg().bbe_surrogate_num_params())
+
+
+def bbe_surrogate_create(init_seed: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_sg().bbe_surrogate_create(C.byref(h), int(init_seed) & (2**64 - 1)), "bbe_surrogate_create")
+    return h.value
+
+
+def bbe_surrogate_set_params(s: int, params) -> None:
+    p = np.ascontiguousarray(params, np.float32)
+    if p.size != bbe_surrogate_num_params():
+        raise ValueError("wrong parameter count")
+    _check(_sg().bbe_surrogate_set_params(s, _ptr(p)), "bbe_surrogate_set_params")
+
+
+def bbe_surrogate_get_params(s: int) -> np.ndarray:
+    p = np.empty(bbe_surrogate_num_params(), np.float32)
+    _check(_sg().bbe_surrogate_get_params(s, _ptr(p)), "bbe_surrogate_get_params")
+    return p
+
+
+def bbe_surrogate_train(s: int, batch: int, target_probs, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                        weight_decay=0.0, batch_states=4096, steps=1, shuffle_seed=0, loss_log=None,
+                        stream=None) -> None:
+    cfg = bbe_train_cfg(lr, beta1, beta2, eps, weight_decay, batch_states, steps, shuffle_seed)
+    _check(_sg().bbe_surrogate_train(s, batch, _ptr(target_probs, np.float32), C.byref(cfg),
+                                     _ptr(loss_log, np.float32), _stream(stream)), "bbe_surrogate_train")
+
+
+def bbe_surrogate_grad(s: int, batch: int, target_probs, grad, loss=None, stream=None) -> None:
+    _check(_sg().bbe_surrogate_grad(s, batch, _ptr(target_probs, np.float32), _ptr(grad, np.float32),
+                                    _ptr(loss, np.float32), _stream(stream)), "bbe_surrogate_grad")
+
+
+def bbe_surrogate_forward(s: int, batch: int, probs, stream=None) -> None:
+    _check(_sg().bbe_surrogate_forward(s, batch, _ptr(probs, np.float32), _stream(stream)), "bbe_surrogate_forward")
+
+
+def bbe_surrogate_infer(s: int, batch: int, probs, used_mc=None, stream=None) -> None:
+    _check(_sg().bbe_surrogate_infer(s, batch, _ptr(probs, np.float32), _ptr(used_mc, np.uint8), _stream(stream)),
+           "bbe_surrogate_infer")
+
+
+def bbe_surrogate_save(s: int, path: str) -> None:
+    _check(_sg().bbe_surrogate_save(s, str(path).encode()), "bbe_surrogate_save")
+
+
+def bbe_surrogate_load(path: str) -> int:
+    h = C.c_void_p()
+    _check(_sg().bbe_surrogate_load(C.byref(h), str(path).encode()), "bbe_surrogate_load")
+    return h.value
+
+
+def bbe_surrogate_destroy(s: int) -> None:
+    if s:
+        _sg().bbe_surrogate_destroy(s)

@@ -24,42 +24,6 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 
 using bbe::set_error;
 
-struct bbe_batch {
-    int device = 0;
-    int num_sms = 0;
-    int32_t n_races = 0;
-    int32_t n_total = 0;
-    int32_t max_n = 0;
-    uint64_t seed = 0;
-    int32_t dist = 0;
-    uint32_t race_id0 = 0;
-
-    // host copies (kept for scheduling and cost estimates)
-    std::vector<int32_t> h_off;
-    std::vector<float> h_L;
-    std::vector<int64_t> h_R;
-    std::vector<float> h_d0, h_mu;
-
-    // library-owned device memory
-    void *arena = nullptr;
-    bbe::DevBatch dev{};
-    bbe::WorkItem *d_items = nullptr;  // items of one-slot races, then of two-slot races
-    int32_t n_items_v[2] = {0, 0};     // item counts per slots-per-lane value (1, 2)
-    int32_t *d_queue = nullptr;        // two queue heads
-    int32_t *d_status = nullptr;
-
-    bbe_launch_cfg cfg{};
-    int32_t resident[2] = {1, 1};  // rollout-kernel blocks resident per SM, per slots-per-lane
-    cudaStream_t side_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-
-    // graph cache
-    cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    int32_t *g_counts = nullptr;
-    int64_t *g_steps = nullptr;
-};
-
 namespace {
 
 #define BBE_CUDA_TRY(expr)                                                                  \
@@ -251,14 +215,11 @@ T *carve(char *&p, size_t count)
 
 }  // namespace
 
-extern "C" {
-
-const char *bbe_last_error(void) { return bbe::g_last_error.c_str(); }
-
-bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
-                         const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
-                         const float *resp, const float *pref, const float *theta, const float *prev_step,
-                         uint64_t seed, bbe_dist dist, uint32_t race_id0, void *cuda_stream)
+bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
+                            const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
+                            const float *resp, const float *pref, const float *theta, const float *prev_step,
+                            uint64_t seed, bbe_dist dist, uint32_t race_id0, const int32_t *race_ids,
+                            cudaStream_t s)
 {
     if (!out) {
         set_error("out is NULL");
@@ -273,7 +234,6 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
         set_error("unknown distribution");
         return BBE_ERR_ARG;
     }
-    cudaStream_t s = as_stream(cuda_stream);
     std::vector<int32_t> off(size_t(n_races) + 1);
     bbe_status st = copy_in(off.data(), race_off, off.size() * sizeof(int32_t), s, "race_off");
     if (st) return st;
@@ -309,7 +269,13 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     b->h_R.resize(n_races);
     b->h_d0.resize(nt);
     b->h_mu.resize(nt);
-    std::vector<float> h_sigma(nt), h_rho(nt), h_P(nt, 1.0f), h_theta(nt, BBE_THETA_DEFAULT), h_prev;
+    b->h_sigma.resize(nt);
+    b->h_rho.resize(nt);
+    b->h_P.assign(nt, 1.0f);
+    b->h_theta.assign(nt, BBE_THETA_DEFAULT);
+    if (race_ids) b->h_race_ids.assign(race_ids, race_ids + n_races);
+    std::vector<float> &h_sigma = b->h_sigma, &h_rho = b->h_rho, &h_P = b->h_P, &h_theta = b->h_theta,
+                       &h_prev = b->h_prev;
     auto fail = [&](bbe_status code) {
         delete b;
         return code;
@@ -385,7 +351,7 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     // one device arena for the staged batch
     size_t bytes = 0;
     auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
-    add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4);
+    add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4); add(n_races * 4);
     for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
     add(8); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
@@ -400,6 +366,7 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
     float *d_L = carve<float>(p, n_races);
     int64_t *d_R = carve<int64_t>(p, n_races);
     int32_t *d_cr = carve<int32_t>(p, nt);
+    int32_t *d_ids = carve<int32_t>(p, n_races);
     float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
     float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
     float *d_prev = carve<float>(p, nt);
@@ -418,19 +385,33 @@ bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_o
         if ((st = copy_in(u.dst, u.src, u.n, s, "staged batch"))) return fail(st);
     }
     if (prev_step && (st = copy_in(d_prev, h_prev.data(), size_t(nt) * 4, s, "prev_step"))) return fail(st);
+    if (race_ids && (st = copy_in(d_ids, race_ids, size_t(n_races) * 4, s, "race_ids"))) return fail(st);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_error(std::string("staging upload: ") + cudaGetErrorString(e));
         return fail(BBE_ERR_CUDA);
     }
-    b->dev = bbe::DevBatch{d_off, d_L, d_R, d_cr, d_d0, d_mu, d_sigma, d_rho, d_P, d_theta,
-                           prev_step ? d_prev : nullptr, n_races, nt, race_id0, uint32_t(seed), uint32_t(seed >> 32),
-                           int32_t(dist)};
+    b->dev = bbe::DevBatch{d_off,   d_L,      d_R,   d_cr, d_d0, d_mu, d_sigma, d_rho, d_P, d_theta,
+                           prev_step ? d_prev : nullptr, race_ids ? d_ids : nullptr, n_races, nt, race_id0,
+                           uint32_t(seed), uint32_t(seed >> 32), int32_t(dist)};
     b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT, 0};
     for (int v = 1; v <= 2; ++v) b->resident[v - 1] = bbe::rollout_resident_blocks(b->dist, v, 32 * kDefaultWarpsPerBlock);
     if ((st = build_items(b))) return fail(st);
     *out = b;
     return BBE_OK;
+}
+
+extern "C" {
+
+const char *bbe_last_error(void) { return bbe::g_last_error.c_str(); }
+
+bbe_status bbe_race_init(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
+                         const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
+                         const float *resp, const float *pref, const float *theta, const float *prev_step,
+                         uint64_t seed, bbe_dist dist, uint32_t race_id0, void *cuda_stream)
+{
+    return bbe::stage_batch(out, n_races, race_off, track_len, rollouts, pos, mu, sigma, resp, pref, theta,
+                            prev_step, seed, dist, race_id0, nullptr, as_stream(cuda_stream));
 }
 
 bbe_status bbe_rollout_batch(bbe_batch *b, int32_t *win_counts, int64_t *steps_total, void *cuda_stream)

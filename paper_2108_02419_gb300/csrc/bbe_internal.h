@@ -17,6 +17,7 @@ struct DevBatch {
     const int64_t *R;         // [n_races]
     const int32_t *comp_race; // [n_total]: race of each competitor
     const float *d0, *mu, *sigma, *rho, *P, *theta, *prev0;  // [n_total]
+    const int32_t *race_ids;  // [n_races] stream id of each race, or null: race_id0 + r
     int32_t n_races;
     int32_t n_total;
     uint32_t race_id0;
@@ -58,3 +59,55 @@ cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *pr
 void set_error(const std::string &msg);
 
 }  // namespace bbe
+
+// A staged batch of race states (opaque to the ABI, shared by the library's units).
+struct bbe_batch {
+    using DevBatch = bbe::DevBatch;
+    using WorkItem = bbe::WorkItem;
+    int device = 0;
+    int num_sms = 0;
+    int32_t n_races = 0;
+    int32_t n_total = 0;
+    int32_t max_n = 0;
+    uint64_t seed = 0;
+    int32_t dist = 0;
+    uint32_t race_id0 = 0;
+
+    // host copies (scheduling, cost estimates, range checks and sub-batches)
+    std::vector<int32_t> h_off;
+    std::vector<float> h_L;
+    std::vector<int64_t> h_R;
+    std::vector<float> h_d0, h_mu, h_sigma, h_rho, h_P, h_theta;
+    std::vector<float> h_prev;      // empty when the default previous step is used
+    std::vector<int32_t> h_race_ids;  // empty when race r has stream id race_id0 + r
+
+    // library-owned device memory
+    void *arena = nullptr;
+    DevBatch dev{};
+    WorkItem *d_items = nullptr;  // items of one-slot races, then of two-slot races
+    int32_t n_items_v[2] = {0, 0};     // item counts per slots-per-lane value (1, 2)
+    int32_t *d_queue = nullptr;        // two queue heads
+    int32_t *d_status = nullptr;
+
+    bbe_launch_cfg cfg{};
+    int32_t resident[2] = {1, 1};  // rollout-kernel blocks resident per SM, per slots-per-lane
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+    // graph cache
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int32_t *g_counts = nullptr;
+    int64_t *g_steps = nullptr;
+};
+
+
+namespace bbe {
+// bbe_race_init with an optional explicit stream id per race (host array, may be null).
+bbe_status stage_batch(bbe_batch **out, int32_t n_races, const int32_t *race_off, const float *track_len,
+                       const int64_t *rollouts, const float *pos, const float *mu, const float *sigma,
+                       const float *resp, const float *pref, const float *theta, const float *prev_step,
+                       uint64_t seed, bbe_dist dist, uint32_t race_id0, const int32_t *race_ids,
+                       cudaStream_t stream);
+}  // namespace bbe
+

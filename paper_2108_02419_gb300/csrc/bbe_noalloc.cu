@@ -279,7 +279,7 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
     NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int block = 128;
     bbe::DevBatch b{race_off, track_len, rollouts, nullptr, pos, mu, sigma, resp, pref, theta, prev_step,
-                    n_races, n_competitors, race_id0, uint32_t(seed), uint32_t(seed >> 32), int32_t(dist)};
+                    nullptr, n_races, n_competitors, race_id0, uint32_t(seed), uint32_t(seed >> 32), int32_t(dist)};
     for (int v = 2; v >= 1; --v) {
         if (h.n_items[v - 1] == 0) continue;
         bbe::RolloutLaunch l{};

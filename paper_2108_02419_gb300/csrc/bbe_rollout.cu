@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
 
         const float L = b.L[r];
         const float invL = __fdiv_rn(1.0f, L);
-        const uint32_t rid = b.race_id0 + uint32_t(r);
+        const uint32_t rid = b.race_ids ? uint32_t(b.race_ids[r]) : b.race_id0 + uint32_t(r);
         const int kend = w.k_begin + w.k_count;
         int k = w.k_begin + seg;
         bool active = lane_used && k < kend;

@@ -1,0 +1,189 @@
+"""The surrogate network on the GPU (through the C ABI) against the float64 reference in
+oracle/surrogate_ref.py, evaluated with bfloat16 rounding at the same points as the GPU,
+plus training, Monte Carlo fallback and checkpoint behaviour."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate_ref as S
+from paper_2108_02419_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bbe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_02419_gb300 import bbe as B
+    from paper_2108_02419_gb300 import build
+
+    build.build()
+    B.lib()
+    return B
+
+
+def ref_inputs(rb):
+    L = np.repeat(rb.L.astype(np.float64), rb.sizes())
+    return S.features(rb.d0, L, rb.mu, rb.sigma, rb.rho)
+
+
+def dirichlet_targets(rb, seed):
+    rng = np.random.default_rng(seed)
+    t = np.empty(rb.n_total, np.float32)
+    for r in range(rb.n_races):
+        a, b = rb.race_off[r], rb.race_off[r + 1]
+        t[a:b] = rng.dirichlet(np.ones(b - a))
+    return t
+
+
+def test_param_count_matches_reference(bbe):
+    assert bbe.bbe_surrogate_num_params() == S.N_PARAMS
+
+
+def test_forward_matches_reference(bbe):
+    rb = W.uneven_batch(seed=41, n_races=300, rollouts=10)  # 2..24 competitors, many tiles
+    params = S.init_params(1).astype(np.float32)
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        with bbe.Batch(rb) as b:
+            probs = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_forward(s, b.handle, probs)
+            torch.cuda.synchronize()
+            got = probs.cpu().numpy().astype(np.float64)
+        assert np.allclose(bbe.bbe_surrogate_get_params(s), params)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    want, _ = S.forward(params.astype(np.float64), ref_inputs(rb), rb.race_off, bf16=True)
+    sums = np.add.reduceat(got, rb.race_off[:-1])
+    assert np.allclose(sums, 1.0, atol=1e-5)
+    err = np.abs(got - want)
+    assert err.max() < 5e-3 and err.mean() < 3e-4, (err.max(), err.mean())
+
+
+def test_gradient_matches_reference(bbe):
+    rb = W.uneven_batch(seed=42, n_races=150, rollouts=10)
+    target = dirichlet_targets(rb, 3)
+    params = S.init_params(2).astype(np.float32)
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        with bbe.Batch(rb) as b:
+            grad = torch.empty(S.N_PARAMS, dtype=torch.float32, device="cuda")
+            loss = torch.empty(1, dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_grad(s, b.handle, torch.from_numpy(target).cuda(), grad, loss)
+            torch.cuda.synchronize()
+            g = grad.cpu().numpy().astype(np.float64)
+            lv = float(loss.item())
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    x = ref_inputs(rb)
+    want = S.backward(params.astype(np.float64), x, rb.race_off, target.astype(np.float64), bf16=True)
+    want_loss = S.loss(params.astype(np.float64), x, rb.race_off, target.astype(np.float64), bf16=True)
+    assert abs(lv - want_loss) < 1e-3 * abs(want_loss)
+    for name, _ in S.SHAPES[:-1]:  # b5's gradient is ~0 (targets sum to 1)
+        gu, wu = S.unpack(g)[name].ravel(), S.unpack(want)[name].ravel()
+        rel = np.linalg.norm(gu - wu) / np.linalg.norm(wu)
+        assert rel < 2e-2, (name, rel)
+
+
+def test_training_reduces_loss_on_mc_targets(bbe):
+    rb = W.uneven_batch(seed=43, n_races=3000, n_lo=2, n_hi=10, rollouts=2000, rem_lo=100.0, rem_hi=1500.0)
+    s = bbe.bbe_surrogate_create(5)
+    try:
+        with bbe.Batch(rb) as b:
+            counts, _ = b.rollout()
+            probs, _ = b.win_probs(counts)
+            log = torch.empty(300, dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_train(s, b.handle, probs, lr=2e-3, batch_states=512, steps=300, loss_log=log)
+            torch.cuda.synchronize()
+            losses = log.cpu().numpy()
+            out = torch.empty_like(probs)
+            bbe.bbe_surrogate_forward(s, b.handle, out)
+            torch.cuda.synchronize()
+            err = np.abs(out.cpu().numpy() - probs.cpu().numpy())
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    assert np.all(np.isfinite(losses))
+    assert losses[-20:].mean() < 0.6 * losses[:5].mean()
+    assert err.mean() < 0.05
+
+
+def test_infer_falls_back_to_exact_monte_carlo(bbe, tmp_path):
+    train = W.uneven_batch(seed=44, n_races=400, n_lo=2, n_hi=12, rollouts=500)
+    query = W.concat([W.uneven_batch(seed=45, n_races=30, n_lo=2, n_hi=12, rollouts=700),   # in range
+                      W.uneven_batch(seed=46, n_races=10, n_lo=16, n_hi=20, rollouts=700),  # too many competitors
+                      W.uneven_batch(seed=47, n_races=10, n_lo=3, n_hi=6, rollouts=700, rem_lo=20.0, rem_hi=90.0)])
+    s = bbe.bbe_surrogate_create(6)
+    try:
+        with bbe.Batch(train) as tb:
+            c, _ = tb.rollout()
+            p, _ = tb.win_probs(c)
+            bbe.bbe_surrogate_train(s, tb.handle, p, batch_states=128, steps=20)
+        with bbe.Batch(query) as qb:
+            probs = torch.empty(query.n_total, dtype=torch.float32, device="cuda")
+            used = torch.empty(query.n_races, dtype=torch.uint8, device="cuda")
+            bbe.bbe_surrogate_infer(s, qb.handle, probs, used)
+            counts, _ = qb.rollout()
+            mc_p, _ = qb.win_probs(counts)
+            torch.cuda.synchronize()
+            used = used.cpu().numpy()
+            got, mc = probs.cpu().numpy(), mc_p.cpu().numpy()
+        assert used[:30].sum() == 0 and used[30:].sum() == 20
+        for r in range(30, 50):
+            a, e = query.race_off[r], query.race_off[r + 1]
+            assert np.array_equal(got[a:e], mc[a:e])  # the fallback is the Monte Carlo path itself
+        sums = np.add.reduceat(got.astype(np.float64), query.race_off[:-1])
+        assert np.allclose(sums, 1.0, atol=1e-5)
+        # checkpoint round trip keeps parameters, ranges and outputs
+        path = tmp_path / "sg.bin"
+        bbe.bbe_surrogate_save(s, str(path))
+        s2 = bbe.bbe_surrogate_load(str(path))
+        try:
+            assert np.array_equal(bbe.bbe_surrogate_get_params(s2), bbe.bbe_surrogate_get_params(s))
+            with bbe.Batch(query) as qb:
+                probs2 = torch.empty_like(probs)
+                used2 = torch.empty(query.n_races, dtype=torch.uint8, device="cuda")
+                bbe.bbe_surrogate_infer(s2, qb.handle, probs2, used2)
+                torch.cuda.synchronize()
+                assert np.array_equal(probs2.cpu().numpy(), got)
+                assert np.array_equal(used2.cpu().numpy(), used)
+        finally:
+            bbe.bbe_surrogate_destroy(s2)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+
+
+def test_infer_without_training_ranges_is_refused(bbe):
+    rb = W.uneven_batch(seed=48, n_races=4, rollouts=10)
+    s = bbe.bbe_surrogate_create(7)
+    try:
+        with bbe.Batch(rb) as b:
+            probs = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+            with pytest.raises(bbe.BbeError) as ei:
+                bbe.bbe_surrogate_infer(s, b.handle, probs)
+            assert ei.value.status == -7
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+
+
+def test_relabelling_competitors_relabels_output(bbe):
+    rb = W.uneven_batch(seed=49, n_races=40, rollouts=10)
+    rng = np.random.default_rng(0)
+    perm = np.concatenate([rb.race_off[r] + rng.permutation(rb.race_off[r + 1] - rb.race_off[r])
+                           for r in range(rb.n_races)])
+    pb = W.from_arrays(rb.sizes(), rb.L, rb.rollouts, rb.d0[perm], rb.mu[perm], rb.sigma[perm], rb.rho[perm])
+    s = bbe.bbe_surrogate_create(8)
+    try:
+        outs = []
+        for batch in (rb, pb):
+            with bbe.Batch(batch) as b:
+                probs = torch.empty(batch.n_total, dtype=torch.float32, device="cuda")
+                bbe.bbe_surrogate_forward(s, b.handle, probs)
+                torch.cuda.synchronize()
+                outs.append(probs.cpu().numpy())
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    assert np.allclose(outs[1], outs[0][perm], atol=2e-3)
