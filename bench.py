@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--races", type=int, default=0, help="use only the first N races (profiling of a small case)")
+    ap.add_argument("--surrogate", default="full", choices=["full", "small", "off"],
+                    help="learned-surrogate leg: full = 2e6 training states x 1e4 rollouts, 20 epochs")
     return ap.parse_args()
 
 
@@ -247,6 +249,130 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- surrogate leg
+
+# algorithmic FLOPs per competitor row of the surrogate network (one forward pass):
+# 2 x (5*128 + 128*128 + 128*128 + 256*128 + 128)
+SURROGATE_FWD_FLOPS_PER_ROW = 2 * (5 * 128 + 2 * 128 * 128 + 256 * 128 + 128)
+
+
+def run_surrogate(mode: str, dev, stream) -> dict:
+    """Training-data generation, training, held-out error and inference throughput of the
+    learned surrogate, next to plain Monte Carlo on the uneven workload."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    full = mode == "full"
+    n_train = 2_000_000 if full else 200_000
+    epochs = 20 if full else 4
+    B = 4096
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    out = {"mode": mode, "train_states": n_train, "train_rollouts": 10000, "epochs": epochs, "batch": B}
+
+    def timed(fn):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    # C3: (state, win-prob) pairs from the uneven generator at 1e4 rollouts, on the GPU
+    gen = W.uneven_batch(seed=100, n_races=n_train, rollouts=10000)
+    t0 = time.perf_counter()
+    tb = bbe.Batch(gen, stream=stream)
+    out["train_stage_s"] = time.perf_counter() - t0
+    counts = torch.empty(gen.n_total, dtype=torch.int32, device=dev)
+    steps_t = torch.empty(gen.n_races, dtype=torch.int64, device=dev)
+    probs = torch.empty(gen.n_total, dtype=torch.float32, device=dev)
+    out["gen_s"] = timed(lambda: (tb.rollout(counts, steps_t, stream=stream), tb.win_probs(counts, probs, stream=stream)))
+    gcs = int((gen.sizes() * steps_t.cpu().numpy()).sum())
+    out["gen_competitor_steps_per_s"] = gcs / out["gen_s"]
+    s = bbe.bbe_surrogate_create(1)
+    try:
+        nsteps = int(epochs * n_train / B)
+        log = torch.empty(nsteps, dtype=torch.float32, device=dev)
+        lr0, chunk = 2e-3, 250
+
+        def train():
+            done = 0
+            while done < nsteps:
+                k = min(chunk, nsteps - done)
+                lr = lr0 * 0.5 * (1.0 + np.cos(np.pi * done / nsteps))  # cosine decay, per chunk
+                bbe.bbe_surrogate_train(s, tb.handle, probs, lr=float(lr), batch_states=B, steps=k,
+                                        loss_log=log[done:done + k], shuffle_seed=7, stream=stream)
+                done += k
+
+        out["train_s"] = timed(train)
+        L = log.cpu().numpy()
+        rows = float(gen.sizes().mean()) * B * nsteps
+        out.update(train_steps=nsteps, loss_first=float(L[:10].mean()), loss_last=float(L[-10:].mean()),
+                   train_states_per_s=nsteps * B / out["train_s"],
+                   train_tflops=3 * SURROGATE_FWD_FLOPS_PER_ROW * rows / out["train_s"] / 1e12)
+        tb.close()
+        # held-out error against 1e5-rollout Monte Carlo
+        ho = W.uneven_batch(seed=300, n_races=10000, rollouts=100000)
+        hb = bbe.Batch(ho, stream=stream)
+        hc = torch.empty(ho.n_total, dtype=torch.int32, device=dev)
+        hp = torch.empty(ho.n_total, dtype=torch.float32, device=dev)
+        hs = torch.empty(ho.n_races, dtype=torch.int64, device=dev)
+        timed(lambda: (hb.rollout(hc, hs, stream=stream), hb.win_probs(hc, hp, stream=stream)))
+        q = torch.empty_like(hp)
+        used = torch.empty(ho.n_races, dtype=torch.uint8, device=dev)
+        bbe.bbe_surrogate_infer(s, hb.handle, q, used, stream=stream)
+        stream.synchronize()
+        P, Q = hp.cpu().numpy().astype(np.float64), q.cpu().numpy().astype(np.float64)
+        err = np.abs(P - Q)
+        kl = np.where(P > 0, P * (np.log(np.maximum(P, 1e-30)) - np.log(np.maximum(Q, 1e-30))), 0.0)
+        mc_cs_per_rollout = float((ho.sizes() * hs.cpu().numpy()).sum()) / float(ho.rollouts.sum())
+        out["heldout"] = {"states": ho.n_races, "reference_rollouts": 100000, "max_abs": float(err.max()),
+                          "mean_abs": float(err.mean()), "p99_abs": float(np.quantile(err, 0.99)),
+                          "kl_mean": float(np.add.reduceat(kl, ho.race_off[:-1]).mean()),
+                          "kl_max": float(np.add.reduceat(kl, ho.race_off[:-1]).max()),
+                          "used_mc": int(used.cpu().numpy().sum())}
+        hb.close()
+        # C4: 1e6 queries drawn as in the uneven workload
+        qrb = W.uneven_batch(seed=400, n_races=1_000_000, rollouts=10000)
+        t0 = time.perf_counter()
+        qb = bbe.Batch(qrb, stream=stream)
+        out["query_stage_s"] = time.perf_counter() - t0
+        qp = torch.empty(qrb.n_total, dtype=torch.float32, device=dev)
+        qu = torch.empty(qrb.n_races, dtype=torch.uint8, device=dev)
+        bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)  # plans once per batch
+        ts = [timed(lambda: bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)) for _ in range(3)]
+        t_inf = min(ts)
+        qrows = float(qrb.n_total)
+        out["infer"] = {"states": qrb.n_races, "s": t_inf, "win_prob_vectors_per_s": qrb.n_races / t_inf,
+                        "used_mc": int(qu.cpu().numpy().sum()),
+                        "tflops": SURROGATE_FWD_FLOPS_PER_ROW * qrows / t_inf / 1e12}
+        qb.close()
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    # plain Monte Carlo on the uneven workload (10,000 snapshots, budgets 1e3..1e5)
+    u = W.uneven_batch(seed=0)
+    with bbe.Batch(u, stream=stream) as ub:
+        uc = torch.empty(u.n_total, dtype=torch.int32, device=dev)
+        us = torch.empty(u.n_races, dtype=torch.int64, device=dev)
+        up = torch.empty(u.n_total, dtype=torch.float32, device=dev)
+        timed(lambda: (ub.rollout(uc, us, stream=stream), ub.win_probs(uc, up, stream=stream)))
+        t_mc = min(timed(lambda: (ub.rollout(uc, us, stream=stream), ub.win_probs(uc, up, stream=stream)))
+                   for _ in range(2))
+        mc_cs = float((u.sizes() * us.cpu().numpy()).sum())
+    mc_rate = u.n_races / t_mc
+    # Monte Carlo at the surrogate's mean-abs error: E|N(0, p(1-p)/R)| = sqrt(2 p (1-p) / (pi R))
+    sq = float(np.mean(np.sqrt(P * (1 - P))))
+    r_match = 2.0 / np.pi * (sq / max(out["heldout"]["mean_abs"], 1e-12)) ** 2
+    cs_per_s = mc_cs / t_mc
+    mc_rate_matched = cs_per_s / (max(r_match, 1.0) * mc_cs_per_rollout)
+    out["mc"] = {"workload": "uneven 10,000 snapshots, rollouts floor(10^U(3,5))", "win_prob_vectors_per_s": mc_rate,
+                 "competitor_steps_per_s": cs_per_s, "rollouts_matching_surrogate_mean_abs": r_match,
+                 "win_prob_vectors_per_s_at_matched_mean_abs": mc_rate_matched}
+    out["gain_vs_mc"] = out["infer"]["win_prob_vectors_per_s"] / mc_rate
+    out["gain_vs_mc_matched_mean_abs"] = out["infer"]["win_prob_vectors_per_s"] / mc_rate_matched
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU leg
 
 def run_gpu(args, rank, world, dist):
@@ -361,8 +487,14 @@ def run_gpu(args, rank, world, dist):
         v, desc, _ = oracle_sample(rb, args.cpu_seconds, threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
+    batch_cfg = batch.cfg()
+    batch.close()
+    sur = None
+    if rank == 0 and args.surrogate != "off" and not args.races:
+        sur = run_surrogate(args.surrogate, dev, stream)
+
     cfg = workload_config(args.workload, rb)
-    cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch.cfg(),
+    cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch_cfg,
                 "rollouts_per_step_per_gpu": rollouts_per_step, "competitor_steps_per_step_per_gpu": units_per_step,
                 "parallelism": f"races x{world} (weak)"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -371,8 +503,7 @@ def run_gpu(args, rank, world, dist):
             "win_prob_vectors_per_s": rb.n_races * world * args.steps / t_max,
             "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps}
-    batch.close()
+            "gpu_launches": 2 * args.steps, "surrogate": sur}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

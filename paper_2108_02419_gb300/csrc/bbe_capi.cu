@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -38,14 +39,32 @@ namespace {
 constexpr int32_t kDefaultWarpsPerBlock = 4;
 constexpr int32_t kDefaultBlocksPerSm = 16;
 constexpr int32_t kDefaultRolloutsPerLane = 32;
+constexpr int64_t kMaxItemsPerRace = 256;
+constexpr int64_t kMaxItems = int64_t(1) << 21;
 
 bool finite(float x) { return std::isfinite(x); }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+bool is_host_memory(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeUnregistered || at.type == cudaMemoryTypeHost;
+}
+
+// copy caller memory (host or device) into a host vector: memcpy for host memory, an
+// asynchronous device-to-host copy otherwise (the caller synchronises the stream)
 bbe_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s, const char *what)
 {
     if (bytes == 0) return BBE_OK;
+    if (is_host_memory(src)) {
+        std::memcpy(dst, src, bytes);
+        return BBE_OK;
+    }
     cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
     if (e != cudaSuccess) {
         set_error(std::string("copy of ") + what + ": " + cudaGetErrorString(e));
@@ -90,11 +109,17 @@ bbe_status build_items(bbe_batch *b)
     std::vector<bbe::WorkItem> items[2];
     std::vector<double> cost[2];
     const int64_t per_lane = b->cfg.rollouts_per_lane;
+    // keep the whole list near kMaxItems items: very large batches get larger items
+    int64_t total_rollouts = 0;
+    for (int r = 0; r < b->n_races; ++r) total_rollouts += b->h_R[r];
+    const int64_t min_chunk = (total_rollouts + kMaxItems - 1) / kMaxItems;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
         const int v = slots_for(n, b->cfg.slots_per_lane);
         const int nseg = 32 / ((n + v - 1) / v);
-        const int64_t chunk = per_lane * nseg;
+        // at least rollouts_per_lane per segment, at most kMaxItemsPerRace items per race
+        const int64_t chunk = std::max<int64_t>(
+            std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace), min_chunk);
         const double st = est_steps(b, r);
         for (int64_t k = 0; k < b->h_R[r]; k += chunk) {
             const int64_t cnt = std::min<int64_t>(chunk, b->h_R[r] - k);
@@ -258,6 +283,8 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     const int32_t nt = off[n_races];
 
     auto b = new bbe_batch();
+    static std::atomic<uint64_t> next_serial{1};
+    b->serial = next_serial.fetch_add(1);
     b->n_races = n_races;
     b->n_total = nt;
     b->max_n = max_n;
@@ -372,20 +399,26 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_prev = carve<float>(p, nt);
     b->d_queue = carve<int32_t>(p, 2);
     b->d_status = carve<int32_t>(p, 1);
-    struct {
+    struct Up {
         void *dst;
         const void *src;
         size_t n;
-    } ups[] = {{d_off, off.data(), off.size() * 4},       {d_L, b->h_L.data(), size_t(n_races) * 4},
+    };
+    Up ups[] = {{d_off, off.data(), off.size() * 4},       {d_L, b->h_L.data(), size_t(n_races) * 4},
                {d_R, b->h_R.data(), size_t(n_races) * 8}, {d_cr, comp_race.data(), size_t(nt) * 4},
                {d_d0, b->h_d0.data(), size_t(nt) * 4},   {d_mu, b->h_mu.data(), size_t(nt) * 4},
                {d_sigma, h_sigma.data(), size_t(nt) * 4}, {d_rho, h_rho.data(), size_t(nt) * 4},
                {d_P, h_P.data(), size_t(nt) * 4},         {d_theta, h_theta.data(), size_t(nt) * 4}};
-    for (auto &u : ups) {
-        if ((st = copy_in(u.dst, u.src, u.n, s, "staged batch"))) return fail(st);
+    std::vector<Up> all(std::begin(ups), std::end(ups));
+    if (prev_step) all.push_back({d_prev, h_prev.data(), size_t(nt) * 4});
+    if (race_ids) all.push_back({d_ids, b->h_race_ids.data(), size_t(n_races) * 4});
+    for (auto &u : all) {
+        cudaError_t ce = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, s);
+        if (ce != cudaSuccess) {
+            set_error(std::string("staging upload: ") + cudaGetErrorString(ce));
+            return fail(BBE_ERR_CUDA);
+        }
     }
-    if (prev_step && (st = copy_in(d_prev, h_prev.data(), size_t(nt) * 4, s, "prev_step"))) return fail(st);
-    if (race_ids && (st = copy_in(d_ids, race_ids, size_t(n_races) * 4, s, "race_ids"))) return fail(st);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_error(std::string("staging upload: ") + cudaGetErrorString(e));

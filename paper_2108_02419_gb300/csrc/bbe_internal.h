@@ -64,6 +64,7 @@ void set_error(const std::string &msg);
 struct bbe_batch {
     using DevBatch = bbe::DevBatch;
     using WorkItem = bbe::WorkItem;
+    uint64_t serial = 0;  // unique per staged batch (cache key for plans built from it)
     int device = 0;
     int num_sms = 0;
     int32_t n_races = 0;

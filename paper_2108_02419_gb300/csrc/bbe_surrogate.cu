@@ -662,6 +662,16 @@ struct bbe_surrogate {
     size_t ws_tiles = 0;
     float *d_loss = nullptr;
     SgRanges ranges;
+    uint64_t ranges_version = 1;
+    // inference plan cached per (batch, ranges): network races packed into tiles, fallback races
+    uint64_t iplan_serial = 0, iplan_version = 0;
+    std::vector<int32_t> iplan_mc;
+    std::vector<uint8_t> iplan_flag;
+    int64_t iplan_tiles = 0;
+    SgTile *d_itiles = nullptr;
+    size_t itiles_cap = 0;
+    int32_t *d_iorder = nullptr;
+    size_t iorder_cap = 0;
 };
 
 namespace {
@@ -876,7 +886,8 @@ bbe_status upload_params(bbe_surrogate *s, const float *host)
 void free_surrogate(bbe_surrogate *s)
 {
     for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->d_tiles,
-                    (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss})
+                    (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
+                    (void *)s->d_iorder})
         if (p) cudaFree(p);
 }
 
@@ -992,7 +1003,10 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     bbe_status e;
     if ((e = ensure_attrs())) return e;
-    if (!s->ranges.valid) record_ranges(s->ranges, b);
+    if (!s->ranges.valid) {
+        record_ranges(s->ranges, b);
+        s->ranges_version += 1;
+    }
     if (s->plan_batch != b || int64_t(s->epoch_order.size()) != b->n_races) {
         s->plan_batch = b;
         s->epoch_order.clear();
@@ -1049,18 +1063,43 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         return BBE_ERR_RANGE;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    std::vector<int32_t> net, mc;
-    std::vector<uint8_t> flag(b->n_races, 0);
-    for (int r = 0; r < b->n_races; ++r) {
-        if (in_range(s->ranges, b, r)) {
-            net.push_back(r);
-        } else {
-            mc.push_back(r);
-            flag[r] = 1;
+    bbe_status e;
+    if ((e = ensure_attrs())) return e;
+    if (s->iplan_serial != b->serial || s->iplan_version != s->ranges_version) {
+        // range check and tile packing on the host, once per (batch, ranges)
+        std::vector<int32_t> net;
+        s->iplan_mc.clear();
+        s->iplan_flag.assign(b->n_races, 0);
+        for (int r = 0; r < b->n_races; ++r) {
+            if (in_range(s->ranges, b, r)) {
+                net.push_back(r);
+            } else {
+                s->iplan_mc.push_back(r);
+                s->iplan_flag[r] = 1;
+            }
         }
+        std::vector<SgTile> tiles;
+        pack_tiles(b->h_off, net.data(), int64_t(net.size()), 0, tiles);
+        if ((e = ensure_buf(s->d_iorder, s->iorder_cap, net.size()))) return e;
+        if ((e = ensure_buf(s->d_itiles, s->itiles_cap, tiles.size()))) return e;
+        SG_TRY(cudaMemcpyAsync(s->d_iorder, net.data(), net.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        SG_TRY(cudaMemcpyAsync(s->d_itiles, tiles.data(), tiles.size() * sizeof(SgTile), cudaMemcpyHostToDevice, st));
+        SG_TRY(cudaStreamSynchronize(st));
+        s->iplan_tiles = int64_t(tiles.size());
+        s->iplan_serial = b->serial;
+        s->iplan_version = s->ranges_version;
     }
-    bbe_status e = forward_all(s, b, net, probs, st);
-    if (e) return e;
+    if (s->iplan_tiles > 0) {
+        SgArgs a = base_args(s, b);
+        a.tiles = s->d_itiles;
+        a.order = s->d_iorder;
+        a.probs = probs;
+        a.train = 0;
+        sg_forward<<<unsigned(s->iplan_tiles), NTHREADS, fwd_smem(), st>>>(a);
+        SG_TRY(cudaGetLastError());
+    }
+    const std::vector<int32_t> &mc = s->iplan_mc;
+    const std::vector<uint8_t> &flag = s->iplan_flag;
     if (!mc.empty()) {
         // plain Monte Carlo for the out-of-range races, with their own stream ids
         std::vector<int32_t> off(1, 0), ids;
@@ -1205,6 +1244,7 @@ bbe_status bbe_surrogate_load(bbe_surrogate **out, const char *path)
     s->epoch = epoch;
     s->cursor = cursor;
     s->ranges = ranges;
+    s->ranges_version += 1;
     *out = s;
     return BBE_OK;
 }
