@@ -2,8 +2,10 @@
 
 The network maps a race state to a win-probability vector, permutation-equivariantly:
 
-  per competitor c of a race (n competitors, track length L), features
-    x_c = [ d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1 ]   (5 values)
+  per competitor c of a race (n competitors, track length L), features: the raw quantities
+    [ d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1 ] and six values derived
+    from them per race (expected finish time and its spread, lag behind the race's fastest
+    expected finisher, gap to the competitor ahead, 1/n; see features())
   encoder (3 layers, width 128, ReLU):  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)
   context: g = mean over the race's competitors of h3
   head:    u_c = relu(W4 [h3_c ; g] + b4)        (256 -> 128)
@@ -15,6 +17,7 @@ The network maps a race state to a win-probability vector, permutation-equivaria
 Parameters live in one flat float vector in this order (row-major [out][in] matrices; W1 is
 stored with its input dimension padded from 5 to 16 with zeros):
   W1 [128][16], b1 [128], W2 [128][128], b2, W3 [128][128], b3, W4 [128][256], b4, w5 [128], b5 [1].
+W1's columns 14..15 multiply zero inputs.
 
 With ``bf16=True`` the forward pass rounds to bfloat16 (round to nearest even) exactly where a
 mixed-precision implementation keeps bfloat16 values: the weight matrices, the features, and
@@ -27,7 +30,7 @@ from __future__ import annotations
 import numpy as np
 
 H = 128
-FIN = 5
+FIN = 14
 KIN = 16
 L_SCALE = 5000.0
 
@@ -59,15 +62,62 @@ def bf16_round(x):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def features(d, L, mu, sigma, rho):
-    """The 5 input features of each competitor (float64), padded to 16 columns with zeros."""
+def features(d, L, mu, sigma, rho, race_off=None):
+    """Input features of each competitor (float64), 16 columns.
+
+    Columns 0..4 are the raw quantities [d/L, (L-d)/5000, mu-16, sigma-1, 2 rho-1].  With
+    race_off given, columns 5..10 are derived from them per race:
+      v = mu (1 + 0.1 (2 rho - 1) d/L)   expected speed (the responsiveness law averaged
+                                          over the rest of the track)
+      T = (L - d) / v                     expected steps to the line;  s = sigma sqrt(T) / v
+      x5 = T / 100,  x6 = min(T - Tmin, 100) / 10,  x7 = s,
+      x8 = min((T - Tmin) / sqrt(s^2 + s_min^2 + 0.01), 20) / 5,
+      x9 = min(gap to the nearest competitor strictly ahead, 100) / 10 (100 when none),
+      x10 = 1 / n,
+      x11 = min(gap to the nearest competitor strictly behind, 100) / 10 (100 when none),
+      x12 = min(g_a / (v - v_a) / T, 2) / 2 when the nearest competitor ahead (gap g_a, speed
+            v_a) is slower, else 1: the share of its remaining race after which this competitor
+            would catch it,
+      x13 = min(g_b / (v_b - v) / T_b, 2) / 2 when the nearest competitor behind (gap g_b, speed
+            v_b, time T_b) is faster, else 1,
+    where Tmin is the race's least T and s_min the s of that competitor; "nearest" takes the
+    lowest index among equal positions, like i+ of Eq. 1.  Columns 14..15 are zero."""
     d, L, mu, sigma, rho = (np.asarray(a, np.float64) for a in (d, L, mu, sigma, rho))
     x = np.zeros((d.size, KIN))
-    x[:, 0] = d / L
+    frac = d / L
+    x[:, 0] = frac
     x[:, 1] = (L - d) / L_SCALE
     x[:, 2] = mu - 16.0
     x[:, 3] = sigma - 1.0
     x[:, 4] = 2.0 * rho - 1.0
+    if race_off is None:
+        return x
+    v = mu * (1.0 + 0.1 * (2.0 * rho - 1.0) * frac)
+    T = (L - d) / v
+    sd = sigma * np.sqrt(T) / v
+    off = np.asarray(race_off, np.int64)
+    for r in range(off.size - 1):
+        a, b = off[r], off[r + 1]
+        k = a + int(np.argmin(T[a:b]))
+        lag = T[a:b] - T[k]
+        x[a:b, 5] = T[a:b] / 100.0
+        x[a:b, 6] = np.minimum(lag, 100.0) / 10.0
+        x[a:b, 7] = sd[a:b]
+        x[a:b, 8] = np.minimum(lag / np.sqrt(sd[a:b] ** 2 + sd[k] ** 2 + 0.01), 20.0) / 5.0
+        for c in range(a, b):
+            ia = ib = None
+            for i in range(a, b):
+                if d[i] > d[c] and (ia is None or d[i] < d[ia]):
+                    ia = i
+                if d[i] < d[c] and (ib is None or d[i] > d[ib]):
+                    ib = i
+            ga = d[ia] - d[c] if ia is not None else 100.0
+            gb = d[c] - d[ib] if ib is not None else 100.0
+            x[c, 9] = min(ga, 100.0) / 10.0
+            x[c, 11] = min(gb, 100.0) / 10.0
+            x[c, 12] = min(ga / (v[c] - v[ia]) / T[c], 2.0) / 2.0 if ia is not None and v[c] > v[ia] else 1.0
+            x[c, 13] = min(gb / (v[ib] - v[c]) / T[ib], 2.0) / 2.0 if ib is not None and v[ib] > v[c] else 1.0
+        x[a:b, 10] = 1.0 / (b - a)
     return x
 
 

@@ -31,7 +31,8 @@ using bf16 = __nv_bfloat16;
 
 constexpr int H = 128;        // hidden width
 constexpr int KIN = 16;       // input features padded to one k-step
-constexpr int FIN = 5;        // real input features
+constexpr int FIN = 14;       // input features in use (raw and derived)
+constexpr int RAW = 5;        // raw per-competitor quantities (range-checked at inference)
 constexpr int TILE = 128;     // rows per tile
 constexpr int MAX_STATES = 64;
 constexpr int NTHREADS = 256;
@@ -260,24 +261,76 @@ __device__ void build_rowmap(RowMap &m, const SgArgs &a, const SgTile &t, int ti
     __syncthreads();
 }
 
-// the 5 input features of a row (float32), rounded to bfloat16 into xrow[0..15]
-__device__ void row_features(bf16 *xrow, const SgArgs &a, const RowMap &m, int row)
+// Input features of every row (float32, rounded to bfloat16 into x[row][0..15]): the raw
+// quantities [d/L, (L-d)/5000, mu-16, sigma-1, 2 rho-1] and, per race, the expected finish
+// time T = (L-d)/v with v = mu (1 + 0.1 (2 rho - 1) d/L), its spread s = sigma sqrt(T)/v, the
+// lag behind the race's least T and its z-score, the gap to the nearest competitor strictly
+// ahead, and 1/n.  Called by all threads of the block.
+struct FeatScratch {
+    float T[TILE], sd[TILE], d[TILE], v[TILE], raw[TILE][RAW];
+};
+
+__device__ void tile_features(bf16 *x, int ldx, bf16 *ws_x, FeatScratch &fs, const SgArgs &a, const RowMap &m,
+                              int tid)
 {
-    float f[KIN];
-#pragma unroll
-    for (int k = 0; k < KIN; ++k) f[k] = 0.0f;
-    const int r = m.row_race[row];
-    if (r >= 0) {
-        const int i = a.b.race_off[r] + m.row_comp[row];
-        const float L = a.b.L[r], d = a.b.d0[i];
-        f[0] = d / L;
-        f[1] = (L - d) / L_SCALE;
-        f[2] = a.b.mu[i] - 16.0f;
-        f[3] = a.b.sigma[i] - 1.0f;
-        f[4] = 2.0f * a.b.rho[i] - 1.0f;
+    if (tid < TILE) {
+        const int r = m.row_race[tid];
+        if (r >= 0) {
+            const int i = a.b.race_off[r] + m.row_comp[tid];
+            const float L = a.b.L[r], d = a.b.d0[i], mu = a.b.mu[i], sigma = a.b.sigma[i], rho = a.b.rho[i];
+            const float frac = d / L;
+            const float v = mu * (1.0f + 0.1f * (2.0f * rho - 1.0f) * frac);
+            const float T = (L - d) / v;
+            fs.T[tid] = T;
+            fs.v[tid] = v;
+            fs.sd[tid] = sigma * sqrtf(T) / v;
+            fs.d[tid] = d;
+            fs.raw[tid][0] = frac;
+            fs.raw[tid][1] = (L - d) / L_SCALE;
+            fs.raw[tid][2] = mu - 16.0f;
+            fs.raw[tid][3] = sigma - 1.0f;
+            fs.raw[tid][4] = 2.0f * rho - 1.0f;
+        }
     }
+    __syncthreads();
+    if (tid < TILE) {
+        float f[KIN];
 #pragma unroll
-    for (int k = 0; k < KIN; ++k) xrow[k] = __float2bfloat16_rn(f[k]);
+        for (int k = 0; k < KIN; ++k) f[k] = 0.0f;
+        if (m.row_race[tid] >= 0) {
+            const int st = m.row_state[tid];
+            const int r0 = m.state_row0[st], r1 = m.state_row0[st + 1];
+            int kmin = r0, ia = -1, ib = -1;
+            const float dc = fs.d[tid];
+            for (int q = r0; q < r1; ++q) {
+                if (fs.T[q] < fs.T[kmin]) kmin = q;
+                if (fs.d[q] > dc && (ia < 0 || fs.d[q] < fs.d[ia])) ia = q;
+                if (fs.d[q] < dc && (ib < 0 || fs.d[q] > fs.d[ib])) ib = q;
+            }
+            const float ga = ia >= 0 ? fs.d[ia] - dc : 100.0f;
+            const float gb = ib >= 0 ? dc - fs.d[ib] : 100.0f;
+            const float gap = ga;
+            const float lag = fs.T[tid] - fs.T[kmin];
+            const float vc = fs.v[tid];
+            f[11] = fminf(gb, 100.0f) / 10.0f;
+            f[12] = (ia >= 0 && vc > fs.v[ia]) ? fminf(ga / (vc - fs.v[ia]) / fs.T[tid], 2.0f) / 2.0f : 1.0f;
+            f[13] = (ib >= 0 && fs.v[ib] > vc) ? fminf(gb / (fs.v[ib] - vc) / fs.T[ib], 2.0f) / 2.0f : 1.0f;
+#pragma unroll
+            for (int k = 0; k < RAW; ++k) f[k] = fs.raw[tid][k];
+            f[5] = fs.T[tid] / 100.0f;
+            f[6] = fminf(lag, 100.0f) / 10.0f;
+            f[7] = fs.sd[tid];
+            f[8] = fminf(lag / sqrtf(fs.sd[tid] * fs.sd[tid] + fs.sd[kmin] * fs.sd[kmin] + 0.01f), 20.0f) / 5.0f;
+            f[9] = fminf(gap, 100.0f) / 10.0f;
+            f[10] = 1.0f / float(r1 - r0);
+        }
+#pragma unroll
+        for (int k = 0; k < KIN; ++k) {
+            const bf16 v = __float2bfloat16_rn(f[k]);
+            x[tid * ldx + k] = v;
+            if (ws_x) ws_x[tid * KIN + k] = v;
+        }
+    }
 }
 
 // mean over each race's rows of h (bf16, stride ldh) into g (bf16, stride ldg, per row);
@@ -306,6 +359,7 @@ struct FwdSmem {
     bf16 hg[TILE * LD_2H];
     float logit[TILE];
     RowMap m;
+    FeatScratch fs;
 };
 
 // bias + ReLU epilogue of a [16 x 128] warp block into shared memory (and optionally global)
@@ -338,12 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sg_forward(SgArgs a)
     const SgTile t = a.tiles[blockIdx.x];
     build_rowmap(sm.m, a, t, tid);
     bf16 *ws = a.train ? a.ws + size_t(blockIdx.x) * (WS_X + 4 * WS_H) : nullptr;
-    if (tid < TILE) {
-        row_features(sm.x + tid * LD_IN, a, sm.m, tid);
-        if (ws) {
-            for (int k = 0; k < KIN; ++k) ws[tid * KIN + k] = sm.x[tid * LD_IN + k];
-        }
-    }
+    tile_features(sm.x, LD_IN, ws, sm.fs, a, sm.m, tid);
     load_rows<KIN>(sm.w, LD_IN, a.wb + OFF_W1, tid);
     __syncthreads();
     float acc[16][4];
@@ -638,7 +687,7 @@ struct SgRanges {
     int32_t valid = 0;
     int32_t n_lo = 0, n_hi = 0;
     float L_lo = 0, L_hi = 0;
-    float f_lo[FIN] = {}, f_hi[FIN] = {};
+    float f_lo[RAW] = {}, f_hi[RAW] = {};
     float P_lo = 0, P_hi = 0, th_lo = 0, th_hi = 0;
     int32_t had_prev = 0;
 };
@@ -801,7 +850,7 @@ void record_ranges(SgRanges &R, const bbe_batch *b)
     R.n_hi = 0;
     R.L_lo = R.P_lo = R.th_lo = INFINITY;
     R.L_hi = R.P_hi = R.th_hi = -INFINITY;
-    for (int k = 0; k < FIN; ++k) {
+    for (int k = 0; k < RAW; ++k) {
         R.f_lo[k] = INFINITY;
         R.f_hi[k] = -INFINITY;
     }
@@ -814,7 +863,7 @@ void record_ranges(SgRanges &R, const bbe_batch *b)
         R.L_lo = std::min(R.L_lo, L);
         R.L_hi = std::max(R.L_hi, L);
         for (int i = b->h_off[r]; i < b->h_off[r + 1]; ++i) {
-            for (int k = 0; k < FIN; ++k) {
+            for (int k = 0; k < RAW; ++k) {
                 const float f = feature(k, b->h_d0[i], L, b->h_mu[i], b->h_sigma[i], b->h_rho[i]);
                 R.f_lo[k] = std::min(R.f_lo[k], f);
                 R.f_hi[k] = std::max(R.f_hi[k], f);
@@ -835,7 +884,7 @@ bool in_range(const SgRanges &R, const bbe_batch *b, int r)
     if (!(L >= R.L_lo && L <= R.L_hi)) return false;
     if (!b->h_prev.empty() && !R.had_prev) return false;
     for (int i = b->h_off[r]; i < b->h_off[r + 1]; ++i) {
-        for (int k = 0; k < FIN; ++k) {
+        for (int k = 0; k < RAW; ++k) {
             const float f = feature(k, b->h_d0[i], L, b->h_mu[i], b->h_sigma[i], b->h_rho[i]);
             if (!(f >= R.f_lo[k] && f <= R.f_hi[k])) return false;
         }

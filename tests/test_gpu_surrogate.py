@@ -26,7 +26,7 @@ def bbe():
 
 def ref_inputs(rb):
     L = np.repeat(rb.L.astype(np.float64), rb.sizes())
-    return S.features(rb.d0, L, rb.mu, rb.sigma, rb.rho)
+    return S.features(rb.d0, L, rb.mu, rb.sigma, rb.rho, rb.race_off)
 
 
 def dirichlet_targets(rb, seed):

@@ -89,3 +89,30 @@ def test_bf16_backward_close_to_float64():
     g16 = S.backward(params, x, off, t, bf16=True)[:-1]
     cos = g16 @ g64 / (np.linalg.norm(g16) * np.linalg.norm(g64))
     assert cos > 0.97, cos  # same direction; bfloat16 products cancel less exactly than float64
+
+
+def test_derived_features_worked_example():
+    # race of three on L = 1000: c0 at 0 (mu 10, rho 1/2), c1 at 500 (mu 10, rho 1), c2 at 520
+    L = np.full(3, 1000.0)
+    d = np.array([0.0, 500.0, 520.0])
+    mu = np.array([10.0, 10.0, 8.0])
+    sig = np.array([1.0, 2.0, 0.0])
+    rho = np.array([0.5, 1.0, 0.5])
+    x = S.features(d, L, mu, sig, rho, [0, 3])
+    T = np.array([100.0, 500.0 / 10.5, 60.0])  # v = mu (1 + 0.1 (2 rho - 1) d / L)
+    assert np.allclose(x[:, 5], T / 100)
+    assert np.allclose(x[:, 6], (T - T[1]) / 10)          # c1 has the least expected finish time
+    sd = sig * np.sqrt(T) / np.array([10.0, 10.5, 8.0])
+    assert np.allclose(x[:, 7], sd)
+    assert x[1, 8] == 0.0 and np.isclose(x[0, 8], min((T[0] - T[1]) / np.sqrt(sd[0] ** 2 + sd[1] ** 2 + 0.01), 20) / 5)
+    assert np.allclose(x[:, 9], [10.0, 2.0, 10.0])        # gaps ahead: 500 -> capped 100, 20, none -> 100
+    assert np.allclose(x[:, 10], 1 / 3)
+    assert np.allclose(x[:, 11], [10.0, 10.0, 2.0])       # gaps behind: none, 500 -> 100, 20
+    catch = 20.0 / (10.5 - 8.0) / T[1]                     # c1 closes 20 units at 2.5 units a step
+    assert np.allclose(x[:, 12], [1.0, catch / 2, 1.0])   # c0 is slower than c1; c2 leads
+    assert np.allclose(x[:, 13], [1.0, 1.0, catch / 2])   # only c2 has a faster competitor behind
+    assert np.all(x[:, 14:] == 0)
+    # relabelling the competitors relabels the features
+    perm = [2, 0, 1]
+    xp = S.features(d[perm], L, mu[perm], sig[perm], rho[perm], [0, 3])
+    assert np.allclose(xp, x[perm])
