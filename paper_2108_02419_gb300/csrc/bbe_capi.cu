@@ -94,20 +94,37 @@ double est_steps(const bbe_batch *b, int r)
     return 1.0 + double(b->h_L[r] - lead) / double(std::max(vmax, 1e-3f));
 }
 
-// Competitors per lane for a race of n: two when that fills more of the warp's lanes.
+// Slots-per-lane groups: group g holds races run with kSlots[g] competitors per lane.
+constexpr int kGroups = 3;
+constexpr int kSlots[kGroups] = {1, 2, 4};
+
+int group_of(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
+
+// Competitors per lane for a race of n: the choice that fills most of a warp's
+// competitor slots (ties go to more slots per lane, which shares the per-lane work of a
+// step among more competitors); `mode` forces a value where the race is large enough.
 int slots_for(int n, int mode)
 {
     if (mode == 1 || n < 2) return 1;
     if (mode == 2) return 2;
-    const int used1 = n * (32 / n);
-    const int used2 = n * (32 / ((n + 1) / 2));  // of 64 slots
-    return 2 * used1 < used2 ? 2 : 1;
+    if (mode == 4) return n >= 4 ? 4 : 2;
+    int best = 1;
+    double best_fill = 0.0;
+    for (int v : kSlots) {
+        const int lanes = (n + v - 1) / v;
+        const double fill = double(n * (32 / lanes)) / double(32 * v);
+        if (fill >= best_fill) {
+            best_fill = fill;
+            best = v;
+        }
+    }
+    return best;
 }
 
 bbe_status build_items(bbe_batch *b)
 {
-    std::vector<bbe::WorkItem> items[2];
-    std::vector<double> cost[2];
+    std::vector<bbe::WorkItem> items[kGroups];
+    std::vector<double> cost[kGroups];
     const int64_t per_lane = b->cfg.rollouts_per_lane;
     // keep the whole list near kMaxItems items: very large batches get larger items
     int64_t total_rollouts = 0;
@@ -116,6 +133,7 @@ bbe_status build_items(bbe_batch *b)
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
         const int v = slots_for(n, b->cfg.slots_per_lane);
+        const int g = group_of(v);
         const int nseg = 32 / ((n + v - 1) / v);
         // at least rollouts_per_lane per segment, at most kMaxItemsPerRace items per race
         const int64_t chunk = std::max<int64_t>(
@@ -123,22 +141,24 @@ bbe_status build_items(bbe_batch *b)
         const double st = est_steps(b, r);
         for (int64_t k = 0; k < b->h_R[r]; k += chunk) {
             const int64_t cnt = std::min<int64_t>(chunk, b->h_R[r] - k);
-            items[v - 1].push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
-            cost[v - 1].push_back(double((cnt + nseg - 1) / nseg) * st);
+            items[g].push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
+            cost[g].push_back(double((cnt + nseg - 1) / nseg) * st);
         }
     }
-    if (items[0].size() + items[1].size() > size_t(INT32_MAX)) {
+    size_t total = 0;
+    for (int g = 0; g < kGroups; ++g) total += items[g].size();
+    if (total > size_t(INT32_MAX)) {
         set_error("work list too long; raise rollouts_per_lane");
         return BBE_ERR_RANGE;
     }
     std::vector<bbe::WorkItem> sorted;
-    sorted.reserve(items[0].size() + items[1].size());
-    for (int v = 0; v < 2; ++v) {
-        std::vector<int32_t> order(items[v].size());
+    sorted.reserve(total);
+    for (int g = 0; g < kGroups; ++g) {
+        std::vector<int32_t> order(items[g].size());
         std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[v][x] > cost[v][y]; });
-        for (int32_t i : order) sorted.push_back(items[v][i]);
-        b->n_items_v[v] = int32_t(items[v].size());
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[g][x] > cost[g][y]; });
+        for (int32_t i : order) sorted.push_back(items[g][i]);
+        b->n_items_v[g] = int32_t(items[g].size());
     }
 
     if (b->d_items) cudaFree(b->d_items);
@@ -153,51 +173,58 @@ bbe_status check_cfg(const bbe_launch_cfg &c)
 {
     if (c.warps_per_block < 1 || c.warps_per_block > 16 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
         c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30) ||
-        c.slots_per_lane < 0 || c.slots_per_lane > 2) {
+        !(c.slots_per_lane == 0 || c.slots_per_lane == 1 || c.slots_per_lane == 2 || c.slots_per_lane == 4)) {
         set_error("launch configuration out of range");
         return BBE_ERR_ARG;
     }
     return BBE_OK;
 }
 
-bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *steps, int v)
+bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *steps, int g)
 {
     bbe::RolloutLaunch l{};
     l.b = b->dev;
-    l.items = b->d_items + (v == 2 ? b->n_items_v[0] : 0);
-    l.n_items = b->n_items_v[v - 1];
-    l.queue = b->d_queue + (v - 1);
+    int first = 0;
+    for (int h = 0; h < g; ++h) first += b->n_items_v[h];
+    l.items = b->d_items + first;
+    l.n_items = b->n_items_v[g];
+    l.queue = b->d_queue + g;
     l.counts = counts;
     l.steps = reinterpret_cast<unsigned long long *>(steps);
     l.status = b->d_status;
     l.max_steps = b->cfg.max_steps;
     l.block = 32 * b->cfg.warps_per_block;
     // persistent grid: never more blocks than can be resident at once
-    l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident[v - 1])));
+    l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident[g])));
     return l;
 }
 
-// The launch sequence of one rollout pass: reset queues, status and outputs, then the
-// persistent kernels (two-slot races first).  With a side stream the two kernels are
-// forked so that the second fills SMs as the first one's blocks retire.
+// The launch sequence of one rollout pass: reset queues, status and outputs, then one
+// persistent kernel per non-empty slots-per-lane group, the group with most slots first.
+// With a side stream the first kernel runs on `s` and the others on `side`, so that they
+// fill SMs as the first kernel's blocks retire.
 cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cudaStream_t s, cudaStream_t side)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, kGroups * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, size_t(b->n_total) * sizeof(int32_t), s);
     if (e == cudaSuccess && steps) e = cudaMemsetAsync(steps, 0, size_t(b->n_races) * sizeof(int64_t), s);
-    const bool both = b->n_items_v[0] > 0 && b->n_items_v[1] > 0;
-    if (e == cudaSuccess && both && side) {
+    int groups[kGroups], ng = 0;
+    for (int g = kGroups - 1; g >= 0; --g)
+        if (b->n_items_v[g] > 0) groups[ng++] = g;
+    if (e != cudaSuccess || ng == 0) return e;
+    if (ng > 1 && side) {
         e = cudaEventRecord(b->ev_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_fork, 0);
-        if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps, 2), 2, s);
-        if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps, 1), 1, side);
+        if (e == cudaSuccess) e = bbe::launch_rollout(make_launch(b, counts, steps, groups[0]), kSlots[groups[0]], s);
+        for (int i = 1; i < ng && e == cudaSuccess; ++i)
+            e = bbe::launch_rollout(make_launch(b, counts, steps, groups[i]), kSlots[groups[i]], side);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
         return e;
     }
-    if (e == cudaSuccess && b->n_items_v[1] > 0) e = bbe::launch_rollout(make_launch(b, counts, steps, 2), 2, s);
-    if (e == cudaSuccess && b->n_items_v[0] > 0) e = bbe::launch_rollout(make_launch(b, counts, steps, 1), 1, s);
+    for (int i = 0; i < ng && e == cudaSuccess; ++i)
+        e = bbe::launch_rollout(make_launch(b, counts, steps, groups[i]), kSlots[groups[i]], s);
     return e;
 }
 
@@ -380,7 +407,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
     add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4); add(n_races * 4);
     for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
-    add(8); add(4);
+    add(4 * kGroups); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
@@ -397,7 +424,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
     float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
     float *d_prev = carve<float>(p, nt);
-    b->d_queue = carve<int32_t>(p, 2);
+    b->d_queue = carve<int32_t>(p, kGroups);
     b->d_status = carve<int32_t>(p, 1);
     struct Up {
         void *dst;
@@ -428,7 +455,8 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
                            prev_step ? d_prev : nullptr, race_ids ? d_ids : nullptr, n_races, nt, race_id0,
                            uint32_t(seed), uint32_t(seed >> 32), int32_t(dist)};
     b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT, 0};
-    for (int v = 1; v <= 2; ++v) b->resident[v - 1] = bbe::rollout_resident_blocks(b->dist, v, 32 * kDefaultWarpsPerBlock);
+    for (int g = 0; g < kGroups; ++g)
+        b->resident[g] = bbe::rollout_resident_blocks(b->dist, kSlots[g], 32 * kDefaultWarpsPerBlock);
     if ((st = build_items(b))) return fail(st);
     *out = b;
     return BBE_OK;
@@ -501,7 +529,8 @@ bbe_status bbe_batch_set_cfg(bbe_batch *b, const bbe_launch_cfg *cfg)
     if (st) return st;
     const bool rebuild = c.rollouts_per_lane != b->cfg.rollouts_per_lane || c.slots_per_lane != b->cfg.slots_per_lane;
     b->cfg = c;
-    for (int v = 1; v <= 2; ++v) b->resident[v - 1] = bbe::rollout_resident_blocks(b->dist, v, 32 * c.warps_per_block);
+    for (int g = 0; g < kGroups; ++g)
+        b->resident[g] = bbe::rollout_resident_blocks(b->dist, kSlots[g], 32 * c.warps_per_block);
     free_graph(b);
     return rebuild ? build_items(b) : BBE_OK;
 }

@@ -49,7 +49,7 @@ struct RolloutLaunch {
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;
 
-// slots_per_lane: competitors held per lane (1 or 2).
+// slots_per_lane: competitors held per lane (1, 2 or 4).
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
 // Blocks of `block` threads of the rollout kernel that fit on one SM at once.
 int rollout_resident_blocks(int dist, int slots_per_lane, int block);
@@ -85,13 +85,13 @@ struct bbe_batch {
     // library-owned device memory
     void *arena = nullptr;
     DevBatch dev{};
-    WorkItem *d_items = nullptr;  // items of one-slot races, then of two-slot races
-    int32_t n_items_v[2] = {0, 0};     // item counts per slots-per-lane value (1, 2)
-    int32_t *d_queue = nullptr;        // two queue heads
+    WorkItem *d_items = nullptr;  // items grouped by slots per lane (1, 2, 4)
+    int32_t n_items_v[3] = {0, 0, 0};  // item counts per group
+    int32_t *d_queue = nullptr;        // one queue head per group
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};
-    int32_t resident[2] = {1, 1};  // rollout-kernel blocks resident per SM, per slots-per-lane
+    int32_t resident[3] = {1, 1, 1};  // rollout-kernel blocks resident per SM, per group
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 

@@ -1,7 +1,7 @@
 // bbe_rollout.cu -- the Monte Carlo rollout kernel and the win-probability finaliser.
 //
 // One warp runs the rollouts of one race at a time.  A race of n competitors occupies a
-// segment of ceil(n / V) lanes, each lane holding V consecutive ranks (V = 1 or 2), and a
+// segment of ceil(n / V) lanes, each lane holding V consecutive ranks (V = 1, 2 or 4), and a
 // warp packs floor(32 / lanes) segments, each running its own sequence of rollouts of the
 // same race (Section 3 dry-runs).  Warps pull work items (race, rollout range) from a
 // global queue: one persistent launch per V covers races of any size mix.  The race's
@@ -40,7 +40,7 @@ struct WarpStage {
     float kr[32];
     float d0[32], prev0[32];
     int init_c[32];
-    float zc[3][64];
+    float zc[3][128];
 };
 
 // (da, ca) comes after (db, cb) in rank order
@@ -275,10 +275,11 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                         wv = bv;
                     }
                 }
-                int cw = __shfl_sync(kFull, s[0].c, wl);
-                if (V == 2) {
-                    const int cw1 = __shfl_sync(kFull, s[V - 1].c, wl);
-                    cw = wv ? cw1 : cw;
+                int cw = 0;
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    const int cu = __shfl_sync(kFull, s[u].c, wl);
+                    cw = wv == u ? cu : cw;
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v)
@@ -339,28 +340,47 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                     ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd2, nc2);
                 }
             } else {
-                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                bool ooo = (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) ||
-                           (has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc));
+                // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs are the
+                // inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of lane q+1)
+                bool ooo = false;
+#pragma unroll
+                for (int v = 0; v + 1 < V; ++v)
+                    ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
+                {
+                    const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                    ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc);
+                }
                 while (__any_sync(kFull, ooo)) {
-                    // pairs (slot 0, slot 1) within each lane
-                    if (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) {
-                        const Slot tmp = s[0];
-                        s[0] = s[V - 1];
-                        s[V - 1] = tmp;
+#pragma unroll
+                    for (int v = 0; v + 1 < V; v += 2) {
+                        if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
+                            const Slot tmp = s[v];
+                            s[v] = s[v + 1];
+                            s[v + 1] = tmp;
+                        }
                     }
-                    // pairs (slot 1 of lane q, slot 0 of lane q + 1)
+#pragma unroll
+                    for (int v = 1; v + 1 < V; v += 2) {
+                        if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
+                            const Slot tmp = s[v];
+                            s[v] = s[v + 1];
+                            s[v + 1] = tmp;
+                        }
+                    }
                     const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
                     const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
                     const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, from_next.d, from_next.c);
                     const bool swap_lo = lane_used && ql > 0 && key_gt(from_prev.d, from_prev.c, s[0].d, s[0].c);
                     if (swap_hi) s[V - 1] = from_next;
                     if (swap_lo) s[0] = from_prev;
+                    ooo = false;
+#pragma unroll
+                    for (int v = 0; v + 1 < V; ++v)
+                        ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
                     const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
                     const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
-                    ooo = (valid[V - 1] && key_gt(s[0].d, s[0].c, s[V - 1].d, s[V - 1].c)) ||
-                          (has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2));
+                    ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2);
                 }
             }
         }
@@ -425,12 +445,20 @@ int resident_v(int dist, int block)
 
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
-    return slots_per_lane == 2 ? launch_v<2>(l, stream) : launch_v<1>(l, stream);
+    switch (slots_per_lane) {
+    case 4: return launch_v<4>(l, stream);
+    case 2: return launch_v<2>(l, stream);
+    default: return launch_v<1>(l, stream);
+    }
 }
 
 int rollout_resident_blocks(int dist, int slots_per_lane, int block)
 {
-    return slots_per_lane == 2 ? resident_v<2>(dist, block) : resident_v<1>(dist, block);
+    switch (slots_per_lane) {
+    case 4: return resident_v<4>(dist, block);
+    case 2: return resident_v<2>(dist, block);
+    default: return resident_v<1>(dist, block);
+    }
 }
 
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
