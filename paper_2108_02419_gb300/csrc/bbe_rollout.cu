@@ -164,18 +164,11 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         while (__any_sync(kFull, active)) {
             __syncwarp();  // z-cache writes of earlier steps are visible to every lane
             const bool running = active && t >= 0;
-            // delta(v_c): z for (race, rollout k, step t, competitor c)
-            float z[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                z[v] = 0.0f;
-                if (running && valid[v])
-                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
-            }
-            // i+: the next rank (same lane, or slot 0 of the next lane)
+            // i+: the next rank (same lane, or slot 0 of the next lane).  The same shuffles
+            // verify the rank order: every slot's next rank must be strictly in front.
             float fd[V], fp[V];
             bool hf[V];
-            {
+            auto next_ranks = [&]() {
                 const float nd = __shfl_down_sync(kFull, s[0].d, 1);
                 const float np = __shfl_down_sync(kFull, s[0].prev, 1);
 #pragma unroll
@@ -187,31 +180,112 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                 fd[V - 1] = nd;
                 fp[V - 1] = np;
                 hf[V - 1] = valid[V - 1] && has_next_lane;
-            }
-            bool tie = false;
+            };
+            next_ranks();
+            bool bad = false;
 #pragma unroll
-            for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
-            if (__any_sync(kFull, running && tie)) {
-                // equal positions: the first later rank with a larger position
+            for (int v = 0; v < V; ++v) bad |= hf[v] && !(fd[v] > s[v].d);
+            if (__any_sync(kFull, bad)) {
+                // an overtake in the last step (or equal positions): restore rank order by
+                // odd-even transposition, then handle ties by a search over the segment
+                if (V == 1) {
+                    const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                    bool ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
+                    while (__any_sync(kFull, ooo)) {
+    #pragma unroll
+                        for (int ph = 0; ph < 2; ++ph) {
+                            const bool lower = ((ql - ph) & 1) == 0;
+                            const int pq = lower ? ql + 1 : ql - 1;
+                            const bool ok = lane_used && pq >= 0 && pq < nl;
+                            const int pl = ok ? segbase + pq : lane;
+                            const Slot o = shfl_slot(s[0], pl);
+                            const bool mine_after = key_gt(s[0].d, s[0].c, o.d, o.c);
+                            if (ok && (lower ? mine_after : !mine_after)) s[0] = o;
+                        }
+                        const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
+                        const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
+                        ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd2, nc2);
+                    }
+                } else {
+                    // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs are the
+                    // inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of lane q+1)
+                    bool ooo = false;
+    #pragma unroll
+                    for (int v = 0; v + 1 < V; ++v)
+                        ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
+                    {
+                        const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                        const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                        ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc);
+                    }
+                    while (__any_sync(kFull, ooo)) {
+    #pragma unroll
+                        for (int v = 0; v + 1 < V; v += 2) {
+                            if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
+                                const Slot tmp = s[v];
+                                s[v] = s[v + 1];
+                                s[v + 1] = tmp;
+                            }
+                        }
+    #pragma unroll
+                        for (int v = 1; v + 1 < V; v += 2) {
+                            if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
+                                const Slot tmp = s[v];
+                                s[v] = s[v + 1];
+                                s[v + 1] = tmp;
+                            }
+                        }
+                        const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
+                        const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
+                        const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, from_next.d, from_next.c);
+                        const bool swap_lo = lane_used && ql > 0 && key_gt(from_prev.d, from_prev.c, s[0].d, s[0].c);
+                        if (swap_hi) s[V - 1] = from_next;
+                        if (swap_lo) s[0] = from_prev;
+                        ooo = false;
+    #pragma unroll
+                        for (int v = 0; v + 1 < V; ++v)
+                            ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
+                        const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
+                        const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
+                        ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2);
+                    }
+                }
+
+                next_ranks();
+                bool tie = false;
 #pragma unroll
-                for (int v = 0; v < V; ++v) hf[v] = false;
-                for (int j = 0; j < nl; ++j) {
-                    const int src = lane_used ? segbase + j : lane;
+                for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
+                if (__any_sync(kFull, tie)) {
+                    // equal positions: the first later rank with a larger position
 #pragma unroll
-                    for (int u = 0; u < V; ++u) {
-                        const float dj = __shfl_sync(kFull, s[u].d, src);
-                        const float pj = __shfl_sync(kFull, s[u].prev, src);
-                        const int rj = j * V + u;
+                    for (int v = 0; v < V; ++v) hf[v] = false;
+                    for (int j = 0; j < nl; ++j) {
+                        const int src = lane_used ? segbase + j : lane;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            if (valid[v] && rj > rank0 + v && rj < n && !hf[v] && dj > s[v].d) {
-                                hf[v] = true;
-                                fd[v] = dj;
-                                fp[v] = pj;
+                        for (int u = 0; u < V; ++u) {
+                            const float dj = __shfl_sync(kFull, s[u].d, src);
+                            const float pj = __shfl_sync(kFull, s[u].prev, src);
+                            const int rj = j * V + u;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                if (valid[v] && rj > rank0 + v && rj < n && !hf[v] && dj > s[v].d) {
+                                    hf[v] = true;
+                                    fd[v] = dj;
+                                    fp[v] = pj;
+                                }
                             }
                         }
                     }
                 }
+            }
+            // delta(v_c): z for (race, rollout k, step t, competitor c)
+            float z[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                z[v] = 0.0f;
+                if (running && valid[v])
+                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
             }
             // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
@@ -319,70 +393,6 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             }
             ++gstep;
 
-            // restore rank order after overtakes (odd-even transposition)
-            if (V == 1) {
-                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                bool ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
-                while (__any_sync(kFull, ooo)) {
-#pragma unroll
-                    for (int ph = 0; ph < 2; ++ph) {
-                        const bool lower = ((ql - ph) & 1) == 0;
-                        const int pq = lower ? ql + 1 : ql - 1;
-                        const bool ok = lane_used && pq >= 0 && pq < nl;
-                        const int pl = ok ? segbase + pq : lane;
-                        const Slot o = shfl_slot(s[0], pl);
-                        const bool mine_after = key_gt(s[0].d, s[0].c, o.d, o.c);
-                        if (ok && (lower ? mine_after : !mine_after)) s[0] = o;
-                    }
-                    const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
-                    const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
-                    ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd2, nc2);
-                }
-            } else {
-                // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs are the
-                // inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of lane q+1)
-                bool ooo = false;
-#pragma unroll
-                for (int v = 0; v + 1 < V; ++v)
-                    ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
-                {
-                    const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                    const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                    ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc);
-                }
-                while (__any_sync(kFull, ooo)) {
-#pragma unroll
-                    for (int v = 0; v + 1 < V; v += 2) {
-                        if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
-                            const Slot tmp = s[v];
-                            s[v] = s[v + 1];
-                            s[v + 1] = tmp;
-                        }
-                    }
-#pragma unroll
-                    for (int v = 1; v + 1 < V; v += 2) {
-                        if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
-                            const Slot tmp = s[v];
-                            s[v] = s[v + 1];
-                            s[v + 1] = tmp;
-                        }
-                    }
-                    const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
-                    const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
-                    const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, from_next.d, from_next.c);
-                    const bool swap_lo = lane_used && ql > 0 && key_gt(from_prev.d, from_prev.c, s[0].d, s[0].c);
-                    if (swap_hi) s[V - 1] = from_next;
-                    if (swap_lo) s[0] = from_prev;
-                    ooo = false;
-#pragma unroll
-                    for (int v = 0; v + 1 < V; ++v)
-                        ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
-                    const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
-                    const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
-                    ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2);
-                }
-            }
         }
         // one reduction per work item: wins of each home competitor summed over segments
 #pragma unroll
