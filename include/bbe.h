@@ -81,8 +81,9 @@ typedef struct {
     int32_t blocks_per_sm;      /* 1..32; grid = SMs x blocks_per_sm (persistent) */
     int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 */
     int32_t max_steps;          /* step limit per rollout, 1..2^30 */
-    int32_t slots_per_lane;     /* competitors per lane: 0 = automatic (2 where it fills more lanes),
-                                   1 = one everywhere, 2 = two for every race with n >= 2 */
+    int32_t slots_per_lane;     /* competitors per lane: 0 = automatic (the layout measured fastest
+                                   for the race's competitor count), 1, 2 or 4 = that layout for every
+                                   race large enough for it */
 } bbe_launch_cfg;
 
 /* bbe_race_init -- validate a batch of race states and stage it on the current device.
