@@ -190,6 +190,7 @@ bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *ste
     l.block = 32 * b->cfg.warps_per_block;
     // persistent grid: never more blocks than can be resident at once
     l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident[g])));
+    bbe::fill_round_keys(l);
     return l;
 }
 

@@ -44,7 +44,17 @@ struct RolloutLaunch {
     int32_t *status;          // device status bits
     int32_t max_steps;
     int32_t grid, block;
+    uint32_t round_key[20];  // Philox round keys (k0, k1) of rounds 0..9, from the seed
 };
+
+// Philox4x32-10 key schedule: round i uses (seed_lo + i * 0x9E3779B9, seed_hi + i * 0xBB67AE85).
+inline void fill_round_keys(RolloutLaunch &l)
+{
+    for (int i = 0; i < 10; ++i) {
+        l.round_key[2 * i] = l.b.seed_lo + uint32_t(i) * 0x9E3779B9u;
+        l.round_key[2 * i + 1] = l.b.seed_hi + uint32_t(i) * 0xBB67AE85u;
+    }
+}
 
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;

@@ -293,6 +293,7 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
         l.max_steps = BBE_MAX_STEPS_DEFAULT;
         l.block = block;
         l.grid = sms * std::max(1, std::min(16, bbe::rollout_resident_blocks(int(dist), v, block)));
+        bbe::fill_round_keys(l);
         NA_TRY(bbe::launch_rollout(l, v, s));
     }
     int32_t status = 0;

@@ -26,21 +26,22 @@ struct Words4 {
     uint32_t w0, w1, w2, w3;
 };
 
+// Philox4x32-10 with the round keys given: rk[2i], rk[2i+1] are the key words of round i.
+// With rk in the kernel's parameter block every round is two 32x32->64 multiplies and two
+// three-input XORs with constant-bank operands.
 __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                uint32_t k0, uint32_t k1)
+                                                const uint32_t (&rk)[20])
 {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        c0 = hi1 ^ c1 ^ k0;
-        c2 = hi0 ^ c3 ^ k1;
+        const uint64_t p0 = uint64_t(0xD2511F53u) * c0;
+        const uint64_t p1 = uint64_t(0xCD9E8D57u) * c2;
+        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+        const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+        c0 = hi1 ^ c1 ^ rk[2 * i];
+        c2 = hi0 ^ c3 ^ rk[2 * i + 1];
         c1 = lo1;
         c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
     return Words4{c0, c1, c2, c3};
 }

@@ -65,10 +65,10 @@ __device__ __forceinline__ Slot shfl_slot(const Slot &s, int src)
 // other three are cached in shared memory for the following steps.
 template <int DIST>
 __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uint32_t k, uint32_t rid,
-                                        uint32_t key_lo, uint32_t key_hi)
+                                        const uint32_t (&rk)[20])
 {
     if ((t & 3) != 0) return st.zc[(t & 3) - 1][zi];
-    const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, key_lo, key_hi);
+    const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, rk);
     float z0, z1, z2, z3;
     if (DIST == BBE_DIST_NORMAL) {
         box_muller(wd.w0, wd.w1, z0, z1);
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             for (int v = 0; v < V; ++v) {
                 z[v] = 0.0f;
                 if (running && valid[v])
-                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, b.seed_lo, b.seed_hi);
+                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
             }
             // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
