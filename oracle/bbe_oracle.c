@@ -37,7 +37,7 @@
  * competitor c.  NORMAL: Box-Muller (Box & Muller, 1958) on word pair (t >> 1) & 1,
  * cosine branch for even t, sine branch for odd t.  UNIFORM: sqrt(3) * (2u - 1).
  * TWO_POINT: +-1 from the top bit.  log and sin/cos(2 pi u) are evaluated with the
- * fixed operation sequences below, written from their series (atanh series for log,
+ * fixed operation sequences below (a fitted polynomial for log after an exact range reduction,
  * Taylor series for sin and cos after an exact quadrant reduction).
  */
 #include <math.h>
@@ -83,16 +83,17 @@ static uint32_t bits_from_f32(float f) { uint32_t b; memcpy(&b, &f, 4); return b
 
 /* Natural log of a positive normal binary32 x.
  * x = 2^e * m with m in (sqrt(1/2), sqrt(2)];  f = m - 1 is exact (Sterbenz);
- * log m = 2 atanh(s) with s = f / (2 + f), |s| <= 0.1716, and
- * 2 atanh(s) = 2s + s^3 (2/3 + 2/5 s^2 + 2/7 s^4 + 2/9 s^6 + 2/11 s^8)  (truncation < 1e-9);
- * log x = e ln2 + log m with ln2 split into a 16-bit head and a tail (Cody & Waite). */
+ * log m = f * g(f) with g(f) ~ log(1 + f) / f a degree-9 polynomial on [sqrt(1/2) - 1, sqrt(2) - 1]
+ * (coefficients fitted by least squares on Chebyshev nodes, reweighted towards the minimax
+ * relative error, 4e-9 before rounding to binary32), evaluated by Horner's rule with fused
+ * multiply-adds; log x = e ln2 + log m with ln2 split into a 16-bit head and a tail
+ * (Cody & Waite). */
 float bbe_oracle_log(float x)
 {
-    const float A1 = 0x1.555556p-1f;   /* 2/3  */
-    const float A2 = 0x1.99999ap-2f;   /* 2/5  */
-    const float A3 = 0x1.24924ap-2f;   /* 2/7  */
-    const float A4 = 0x1.c71c72p-3f;   /* 2/9  */
-    const float A5 = 0x1.745d18p-3f;   /* 2/11 */
+    static const float G[10] = {
+        0x1.000000p+0f, -0x1.fffff8p-2f, 0x1.555552p-2f, -0x1.000428p-2f, 0x1.99a2f8p-3f,
+        -0x1.542678p-3f, 0x1.228226p-3f, -0x1.0f4ebcp-3f, 0x1.07eecap-3f, -0x1.36ee94p-4f,
+    };
     const float LN2_HI = 0x1.62e4p-1f;
     const float LN2_LO = 0x1.7f7d1cp-20f;
     uint32_t b = bits_from_f32(x);
@@ -104,14 +105,9 @@ float bbe_oracle_log(float x)
     }
     float m = f32_from_bits(mb);
     float f = m - 1.0f;
-    float s = f / (2.0f + f);
-    float z = s * s;
-    float p = fmaf(z, A5, A4);
-    p = fmaf(z, p, A3);
-    p = fmaf(z, p, A2);
-    p = fmaf(z, p, A1);
-    float sz = s * z;
-    float logm = fmaf(sz, p, s + s);
+    float g = G[9];
+    for (int k = 8; k >= 0; --k) g = fmaf(f, g, G[k]);
+    float logm = f * g;
     float ef = (float)e;
     return fmaf(ef, LN2_HI, fmaf(ef, LN2_LO, logm));
 }

@@ -8,9 +8,10 @@
 // fused multiply-add, divide and square root is an explicit round-to-nearest intrinsic),
 // so the results do not depend on compiler contraction or on the CUDA math library:
 //
-//   log x:  x = 2^e m, m in (sqrt(1/2), sqrt(2)], f = m - 1, s = f / (2 + f),
-//           log m = 2s + s^3 (2/3 + 2/5 s^2 + 2/7 s^4 + 2/9 s^6 + 2/11 s^8) [Horner, fma],
-//           log x = e ln2_hi + (e ln2_lo + log m).
+//   log x:  x = 2^e m, m in (sqrt(1/2), sqrt(2)], f = m - 1 (exact),
+//           log m = f g(f), g a degree-9 fit of log(1 + f) / f on [sqrt(1/2) - 1, sqrt(2) - 1]
+//           (least squares on Chebyshev nodes reweighted towards the minimax relative
+//           error) [Horner, fma], log x = e ln2_hi + (e ln2_lo + log m).
 //   sincos: u = m24 2^-24, q = round(4u) by integer arithmetic, f = u - q/4 exactly,
 //           Taylor series of sin(2 pi f) to degree 9 and cos(2 pi f) to degree 10 in f
 //           [Horner, fma], then the quadrant rotation by q mod 4.
@@ -56,13 +57,16 @@ __device__ __forceinline__ float log_f32(float x)
     mb = halve ? mb - 0x00800000u : mb;
     e = halve ? e + 1 : e;
     const float f = __fsub_rn(__uint_as_float(mb), 1.0f);
-    const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
-    const float z = __fmul_rn(s, s);
-    float p = __fmaf_rn(z, 0x1.745d18p-3f, 0x1.c71c72p-3f);
-    p = __fmaf_rn(z, p, 0x1.24924ap-2f);
-    p = __fmaf_rn(z, p, 0x1.99999ap-2f);
-    p = __fmaf_rn(z, p, 0x1.555556p-1f);
-    const float logm = __fmaf_rn(__fmul_rn(s, z), p, __fadd_rn(s, s));
+    float g = __fmaf_rn(f, -0x1.36ee94p-4f, 0x1.07eecap-3f);
+    g = __fmaf_rn(f, g, -0x1.0f4ebcp-3f);
+    g = __fmaf_rn(f, g, 0x1.228226p-3f);
+    g = __fmaf_rn(f, g, -0x1.542678p-3f);
+    g = __fmaf_rn(f, g, 0x1.99a2f8p-3f);
+    g = __fmaf_rn(f, g, -0x1.000428p-2f);
+    g = __fmaf_rn(f, g, 0x1.555552p-2f);
+    g = __fmaf_rn(f, g, -0x1.fffff8p-2f);
+    g = __fmaf_rn(f, g, 1.0f);
+    const float logm = __fmul_rn(f, g);
     const float ef = __int2float_rn(e);
     return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, logm));
 }
