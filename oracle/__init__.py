@@ -33,14 +33,25 @@ STEP_LIMIT = -5
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wextra"]
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file (this one, or a test's deliberately broken copy)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-I", _HERE, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (contraction off, no fast-math). Returns the .so path."""
+    """Compile the oracle with gcc (contraction off, no fast-math). Returns the .so path.
+
+    The environment variable BBE_ORACLE_LIB names another build to load instead (the
+    mutation tests use it to run the pins against broken copies)."""
+    if os.environ.get("BBE_ORACLE_LIB"):
+        return os.environ["BBE_ORACLE_LIB"]
     os.makedirs(_BUILD, exist_ok=True)
     stale = force or not os.path.exists(_SO) or max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_SO)
     if stale:
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _SO)
+        compile_source(_SRC, _SO)
     return _SO
 
 
