@@ -16,7 +16,8 @@
  *            competitors relabels the output: permutation equivariance)
  *   loss     cross-entropy against the Monte Carlo probabilities, mean over races.
  * Matrix products take bfloat16 operands with float32 accumulation; the master weights and
- * the Adam state are float32.  Parameters are one float vector of bbe_surrogate_num_params()
+ * the Adam state are float32.  The forward kernel waits on the tensor cores with a bounded
+ * wait (2 s); a wait that gives up is reported by bbe_surrogate_status.  Parameters are one float vector of bbe_surrogate_num_params()
  * values: W1 [128][16] (inputs 5..15 zero), b1 [128], W2 [128][128], b2, W3 [128][128], b3,
  * W4 [128][256], b4, w5 [128], b5 [1] (row-major [out][in]).
  *
@@ -89,6 +90,12 @@ BBE_API bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *stat
  * BBE_ERR_CUDA, BBE_ERR_RANGE (no training ranges recorded yet). */
 BBE_API bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *states, float *probs, uint8_t *used_mc,
                                        void *cuda_stream);
+
+/* bbe_surrogate_status -- synchronise cuda_stream and report whether a kernel launched on
+ * this handle gave up a bounded device wait since the last call (the flag is then cleared;
+ * the outputs of the affected calls are undefined).  Errors: BBE_ERR_TIMEOUT, BBE_ERR_ARG,
+ * BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_status(bbe_surrogate *s, void *cuda_stream);
 
 /* bbe_surrogate_save / load -- checkpoint: parameters, Adam state, step count, epoch
  * position and training ranges, in a little-endian binary file.  load creates a handle on

@@ -269,6 +269,7 @@ def _sg():
             "bbe_surrogate_grad": [vp, vp, vp, vp, vp, vp],
             "bbe_surrogate_forward": [vp, vp, vp, vp],
             "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
+            "bbe_surrogate_status": [vp, vp],
             "bbe_surrogate_save": [vp, C.c_char_p],
             "bbe_surrogate_load": [C.POINTER(vp), C.c_char_p],
         }
@@ -327,6 +328,11 @@ def bbe_surrogate_forward(s: int, batch: int, probs, stream=None) -> None:
 def bbe_surrogate_infer(s: int, batch: int, probs, used_mc=None, stream=None) -> None:
     _check(_sg().bbe_surrogate_infer(s, batch, _ptr(probs, np.float32), _ptr(used_mc, np.uint8), _stream(stream)),
            "bbe_surrogate_infer")
+
+
+def bbe_surrogate_status(s: int, stream=None) -> None:
+    """Synchronise and raise BBEError(BBE_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(_sg().bbe_surrogate_status(s, _stream(stream)), "bbe_surrogate_status")
 
 
 def bbe_surrogate_save(s: int, path: str) -> None:

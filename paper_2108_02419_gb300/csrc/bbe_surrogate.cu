@@ -2,14 +2,13 @@
 // forward, backward and Adam kernels and the C ABI around them.
 //
 // Work is cut into tiles of at most 128 competitor rows holding whole races (at most 64),
-// so that the mean-pooled context and the per-race softmax stay inside one thread block.
-// A block of 8 warps processes one tile; warp w owns rows 16w..16w+15.  Every matrix
-// product runs on the tensor cores with mma.sync m16n8k16 (bfloat16 operands staged in
-// shared memory, loaded with ldmatrix, float32 accumulators in registers):
-//   forward   Y[rows][out] = X[rows][in] . W[out][in]^T
-//   backward  dX = dY . W,   dW += dY^T . X  (reduced over the tile's rows, then added to
-//             the float32 gradient with vector atomics)
-// The layer weights are streamed into shared memory one layer at a time.
+// so that the mean-pooled context and the per-race softmax stay inside one tile.
+//   forward   Y[rows][out] = X[rows][in] . W[out][in]^T on the fifth-generation tensor cores
+//             (tcgen05.mma, bfloat16 operands in shared memory, float32 accumulators in
+//             tensor memory), persistent blocks with the weights resident (sg_forward_tc).
+//   backward  dX = dY . W,   dW += dY^T . X  with mma.sync m16n8k16 (one 8-warp block per
+//             tile, warp w owns rows 16w..16w+15, operands loaded with ldmatrix, float32
+//             accumulators in registers, dW added to the float32 gradient with vector atomics).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -51,6 +50,17 @@ constexpr int OFF_W5 = OFF_B4 + H;
 constexpr int OFF_B5 = OFF_W5 + H;
 constexpr int N_PARAMS = OFF_B5 + 1;
 
+// bfloat16 image of W1..W4 in the canonical K-major operand layout of the tensor-core
+// descriptors (element offsets); kept in step with the float32 parameters by the optimizer
+constexpr int WC_W1 = 0;
+constexpr int WC_W2 = WC_W1 + H * KIN;
+constexpr int WC_W3 = WC_W2 + H * H;
+constexpr int WC_W4 = WC_W3 + H * H;
+constexpr int WC_ELEMS = WC_W4 + H * 2 * H;
+
+constexpr int TC_THREADS = 256;                  // forward: two warpgroups, one tile pipeline each
+constexpr long long kWaitNs = 2000000000LL;      // limit of every device-side wait (2 s)
+
 // shared-memory row strides (bf16 elements): +8 keeps ldmatrix rows on distinct banks
 constexpr int LD_IN = KIN + 8;   // 24
 constexpr int LD_H = H + 8;      // 136
@@ -69,6 +79,7 @@ struct SgTile {
 
 struct SgArgs {
     const bf16 *wb;        // bfloat16 copy of the parameters (flat layout)
+    const bf16 *wc;        // bfloat16 W1..W4 in the canonical operand layout (WC_*)
     const float *wf;       // float32 master parameters (biases and w5 are read from here)
     const SgTile *tiles;
     const int32_t *order;  // race indices in tile order
@@ -81,6 +92,8 @@ struct SgArgs {
     bf16 *ws;              // training workspace, tile-major
     float *ws_dlogit;      // training: d loss / d logit per tile row
     int train;
+    int *status;           // set to 1 when a bounded device wait gave up
+    long long wait_ns;     // limit of each wait
 };
 
 // ------------------------------------------------------------------ tensor-core helpers
@@ -118,26 +131,6 @@ __device__ __forceinline__ void zero_acc(float (&acc)[NT][4])
 {
 #pragma unroll
     for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-}
-
-// acc[16 rows][8*NT] += A[16 rows][K] . W[8*NT][K]^T   (A: this warp's rows; W: [out][in])
-template <int NT, int K>
-__device__ __forceinline__ void gemm_xwT(float (&acc)[NT][4], const bf16 *A, int lda, const bf16 *W, int ldw,
-                                         int lane)
-{
-#pragma unroll
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[4];
-        ldsm_x4(a, A + (lane & 15) * lda + k0 + (lane >> 4) * 8);
-#pragma unroll
-        for (int j = 0; j < NT; j += 2) {
-            const int mi = lane >> 3;
-            uint32_t bq[4];
-            ldsm_x4(bq, W + (j * 8 + (lane & 7) + (mi >> 1) * 8) * ldw + k0 + (mi & 1) * 8);
-            mma16816(acc[j], a, bq[0], bq[1]);
-            mma16816(acc[j + 1], a, bq[2], bq[3]);
-        }
-    }
 }
 
 // acc[16 rows][8*NT] += dY[16 rows][N] . W[N][8*NT]   (W: [reduction][out] block of [out..][in])
@@ -223,6 +216,16 @@ __device__ __forceinline__ void atomic_add_colsum(float *g, const float (&v)[NT]
 
 // ------------------------------------------------------------------ tile bookkeeping
 
+// barrier of the threads that work on one tile: the whole block (backward) or one
+// warpgroup (forward; named barrier 1 + group)
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id;
+    __device__ void operator()() const { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+};
+
 struct RowMap {
     int row_race[TILE];   // race index of each row (-1: padding)
     int row_comp[TILE];   // competitor index within its race
@@ -232,14 +235,16 @@ struct RowMap {
     int state_race[MAX_STATES];
 };
 
-__device__ void build_rowmap(RowMap &m, const SgArgs &a, const SgTile &t, int tid)
+// called by the tile's threads (tid 0..127 at least)
+template <typename Sync>
+__device__ void build_rowmap(RowMap &m, const SgArgs &a, const SgTile &t, int tid, Sync sync)
 {
     if (tid < t.ns) {
         const int r = a.order[t.s0 + tid];
         m.state_race[tid] = r;
         m.state_n[tid] = a.b.race_off[r + 1] - a.b.race_off[r];
     }
-    __syncthreads();
+    sync();
     if (tid == 0) {
         int row = 0;
         for (int i = 0; i < t.ns; ++i) {
@@ -249,7 +254,7 @@ __device__ void build_rowmap(RowMap &m, const SgArgs &a, const SgTile &t, int ti
         m.state_row0[t.ns] = row;
     }
     if (tid < TILE) m.row_race[tid] = -1;
-    __syncthreads();
+    sync();
     if (tid < t.ns) {
         const int r0 = m.state_row0[tid];
         for (int c = 0; c < m.state_n[tid]; ++c) {
@@ -258,20 +263,20 @@ __device__ void build_rowmap(RowMap &m, const SgArgs &a, const SgTile &t, int ti
             m.row_state[r0 + c] = tid;
         }
     }
-    __syncthreads();
+    sync();
 }
 
-// Input features of every row (float32, rounded to bfloat16 into x[row][0..15]): the raw
-// quantities [d/L, (L-d)/5000, mu-16, sigma-1, 2 rho-1] and, per race, the expected finish
+// Input features of tile row `tid` (float32; zeros for padding rows and for tid >= 128): the
+// raw quantities [d/L, (L-d)/5000, mu-16, sigma-1, 2 rho-1] and, per race, the expected finish
 // time T = (L-d)/v with v = mu (1 + 0.1 (2 rho - 1) d/L), its spread s = sigma sqrt(T)/v, the
-// lag behind the race's least T and its z-score, the gap to the nearest competitor strictly
-// ahead, and 1/n.  Called by all threads of the block.
+// lag behind the race's least T and its z-score, the gaps to the nearest competitors strictly
+// ahead and behind, 1/n, and the catch-up shares.  Called by all threads of the tile.
 struct FeatScratch {
     float T[TILE], sd[TILE], d[TILE], v[TILE], raw[TILE][RAW];
 };
 
-__device__ void tile_features(bf16 *x, int ldx, bf16 *ws_x, FeatScratch &fs, const SgArgs &a, const RowMap &m,
-                              int tid)
+template <typename Sync>
+__device__ void tile_features(float (&f)[KIN], FeatScratch &fs, const SgArgs &a, const RowMap &m, int tid, Sync sync)
 {
     if (tid < TILE) {
         const int r = m.row_race[tid];
@@ -292,44 +297,34 @@ __device__ void tile_features(bf16 *x, int ldx, bf16 *ws_x, FeatScratch &fs, con
             fs.raw[tid][4] = 2.0f * rho - 1.0f;
         }
     }
-    __syncthreads();
-    if (tid < TILE) {
-        float f[KIN];
+    sync();
 #pragma unroll
-        for (int k = 0; k < KIN; ++k) f[k] = 0.0f;
-        if (m.row_race[tid] >= 0) {
-            const int st = m.row_state[tid];
-            const int r0 = m.state_row0[st], r1 = m.state_row0[st + 1];
-            int kmin = r0, ia = -1, ib = -1;
-            const float dc = fs.d[tid];
-            for (int q = r0; q < r1; ++q) {
-                if (fs.T[q] < fs.T[kmin]) kmin = q;
-                if (fs.d[q] > dc && (ia < 0 || fs.d[q] < fs.d[ia])) ia = q;
-                if (fs.d[q] < dc && (ib < 0 || fs.d[q] > fs.d[ib])) ib = q;
-            }
-            const float ga = ia >= 0 ? fs.d[ia] - dc : 100.0f;
-            const float gb = ib >= 0 ? dc - fs.d[ib] : 100.0f;
-            const float gap = ga;
-            const float lag = fs.T[tid] - fs.T[kmin];
-            const float vc = fs.v[tid];
-            f[11] = fminf(gb, 100.0f) / 10.0f;
-            f[12] = (ia >= 0 && vc > fs.v[ia]) ? fminf(ga / (vc - fs.v[ia]) / fs.T[tid], 2.0f) / 2.0f : 1.0f;
-            f[13] = (ib >= 0 && fs.v[ib] > vc) ? fminf(gb / (fs.v[ib] - vc) / fs.T[ib], 2.0f) / 2.0f : 1.0f;
-#pragma unroll
-            for (int k = 0; k < RAW; ++k) f[k] = fs.raw[tid][k];
-            f[5] = fs.T[tid] / 100.0f;
-            f[6] = fminf(lag, 100.0f) / 10.0f;
-            f[7] = fs.sd[tid];
-            f[8] = fminf(lag / sqrtf(fs.sd[tid] * fs.sd[tid] + fs.sd[kmin] * fs.sd[kmin] + 0.01f), 20.0f) / 5.0f;
-            f[9] = fminf(gap, 100.0f) / 10.0f;
-            f[10] = 1.0f / float(r1 - r0);
+    for (int k = 0; k < KIN; ++k) f[k] = 0.0f;
+    if (tid < TILE && m.row_race[tid] >= 0) {
+        const int st = m.row_state[tid];
+        const int r0 = m.state_row0[st], r1 = m.state_row0[st + 1];
+        int kmin = r0, ia = -1, ib = -1;
+        const float dc = fs.d[tid];
+        for (int q = r0; q < r1; ++q) {
+            if (fs.T[q] < fs.T[kmin]) kmin = q;
+            if (fs.d[q] > dc && (ia < 0 || fs.d[q] < fs.d[ia])) ia = q;
+            if (fs.d[q] < dc && (ib < 0 || fs.d[q] > fs.d[ib])) ib = q;
         }
+        const float ga = ia >= 0 ? fs.d[ia] - dc : 100.0f;
+        const float gb = ib >= 0 ? dc - fs.d[ib] : 100.0f;
+        const float lag = fs.T[tid] - fs.T[kmin];
+        const float vc = fs.v[tid];
 #pragma unroll
-        for (int k = 0; k < KIN; ++k) {
-            const bf16 v = __float2bfloat16_rn(f[k]);
-            x[tid * ldx + k] = v;
-            if (ws_x) ws_x[tid * KIN + k] = v;
-        }
+        for (int k = 0; k < RAW; ++k) f[k] = fs.raw[tid][k];
+        f[5] = fs.T[tid] / 100.0f;
+        f[6] = fminf(lag, 100.0f) / 10.0f;
+        f[7] = fs.sd[tid];
+        f[8] = fminf(lag / sqrtf(fs.sd[tid] * fs.sd[tid] + fs.sd[kmin] * fs.sd[kmin] + 0.01f), 20.0f) / 5.0f;
+        f[9] = fminf(ga, 100.0f) / 10.0f;
+        f[10] = 1.0f / float(r1 - r0);
+        f[11] = fminf(gb, 100.0f) / 10.0f;
+        f[12] = (ia >= 0 && vc > fs.v[ia]) ? fminf(ga / (vc - fs.v[ia]) / fs.T[tid], 2.0f) / 2.0f : 1.0f;
+        f[13] = (ib >= 0 && fs.v[ib] > vc) ? fminf(gb / (fs.v[ib] - vc) / fs.T[ib], 2.0f) / 2.0f : 1.0f;
     }
 }
 
@@ -350,135 +345,418 @@ __device__ void pool_context(bf16 *g, int ldg, const bf16 *h, int ldh, const Row
     }
 }
 
-// ------------------------------------------------------------------ forward
+// ------------------------------------------------------------------ forward (tcgen05)
+//
+// A persistent block of two warpgroups runs two independent tile pipelines that share one
+// copy of the layer weights, kept in shared memory for the whole launch in the canonical
+// K-major operand layout (8-row x 16-byte core matrices, no swizzle).  The optimizer keeps
+// a bfloat16 image of W1..W4 in that layout in global memory, so four bulk asynchronous
+// copies bring them in.  Per layer, one thread of the warpgroup issues tcgen05.mma
+// (M = 128 tile rows, N = 128 outputs, K = 16 per instruction) into the pipeline's 128
+// tensor-memory columns and commits to the pipeline's mbarrier; then the four warps read
+// the float32 accumulators back (warp w of the group reads TMEM lanes 32w..32w+31, one tile
+// row per thread), add the bias, apply ReLU and write bfloat16 activations over the layer's
+// input, which the finished product no longer reads.  The head [h3 ; g] W4^T is two
+// accumulating products: h3 against the first 128 columns of W4, then, once the per-race
+// mean g has replaced h3 in place, g against the other 128.  While one pipeline waits for
+// its product the other one runs its epilogue on the CUDA cores.
 
-struct FwdSmem {
-    bf16 w[TILE * LD_2H];
-    bf16 x[TILE * LD_IN];
-    bf16 ha[TILE * LD_H];
-    bf16 hg[TILE * LD_2H];
-    float logit[TILE];
-    RowMap m;
-    FeatScratch fs;
-};
-
-// bias + ReLU epilogue of a [16 x 128] warp block into shared memory (and optionally global)
-template <int NT>
-__device__ __forceinline__ void relu_store(float (&acc)[NT][4], const float *bias, bf16 *dst, int ld, bf16 *gdst,
-                                           int row0, int lane)
+// byte offset of element (row, k) of a canonical K-major operand with kdim columns
+__host__ __device__ constexpr uint32_t canon_off(int row, int k, int kdim)
 {
-    const int gr = lane >> 2, tc = (lane & 3) * 2;
+    return uint32_t(((row >> 3) * (kdim >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait until phase `parity` of the mbarrier has completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit_ns)
+{
+    const uint32_t addr = smem_addr(bar);
+    const long long t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// bulk asynchronous copy global -> shared (16-byte aligned, size a multiple of 16), completing
+// on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor of a canonical K-major operand without swizzle: start
+// address, byte distance to the next core matrix along K (lbo) and along M or N (sbo), and
+// the fixed descriptor version 1 at bit 46
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// instruction descriptor of kind::f16: float32 D, bfloat16 A and B, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(H >> 3) << 17) | (uint32_t(TILE >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 16 consecutive float32 columns of this thread's TMEM lane into r[O..O+15]
+template <int O>
+__device__ __forceinline__ void tmem_ld16(uint32_t (&r)[32], uint32_t taddr)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[O + 0]), "=r"(r[O + 1]), "=r"(r[O + 2]), "=r"(r[O + 3]), "=r"(r[O + 4]), "=r"(r[O + 5]),
+          "=r"(r[O + 6]), "=r"(r[O + 7]), "=r"(r[O + 8]), "=r"(r[O + 9]), "=r"(r[O + 10]), "=r"(r[O + 11]),
+          "=r"(r[O + 12]), "=r"(r[O + 13]), "=r"(r[O + 14]), "=r"(r[O + 15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// accumulator row (this thread's TMEM lane) -> bias + ReLU -> bfloat16 into the canonical
+// activation tile and, when training, into the workspace row
+__device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
+                                                 bf16 *ws_row)
+{
+#pragma unroll 1
+    for (int c0 = 0; c0 < H; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld16<0>(r, taddr + c0);
+        tmem_ld16<16>(r, taddr + c0 + 16);
+        tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int col = j * 8 + tc;
-        const float b0 = bias[col], b1 = bias[col + 1];
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(acc[j][0] + b0, 0.0f), fmaxf(acc[j][1] + b1, 0.0f));
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(acc[j][2] + b0, 0.0f), fmaxf(acc[j][3] + b1, 0.0f));
-        *reinterpret_cast<__nv_bfloat162 *>(dst + (row0 + gr) * ld + col) = lo;
-        *reinterpret_cast<__nv_bfloat162 *>(dst + (row0 + gr + 8) * ld + col) = hi;
-        if (gdst) {
-            *reinterpret_cast<__nv_bfloat162 *>(gdst + (row0 + gr) * H + col) = lo;
-            *reinterpret_cast<__nv_bfloat162 *>(gdst + (row0 + gr + 8) * H + col) = hi;
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = q * 8 + 2 * e;
+                pk[e] = pack_bf16x2(fmaxf(__uint_as_float(r[j]) + bias[c0 + j], 0.0f),
+                                    fmaxf(__uint_as_float(r[j + 1]) + bias[c0 + j + 1], 0.0f));
+            }
+            const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4 *>(act + canon_off(row, c0 + q * 8, H)) = v;
+            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + c0 + q * 8) = v;
         }
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) sg_forward(SgArgs a)
+// head epilogue: u = bfloat16(relu(acc + b4)) (workspace row when training), returns w5 . u
+__device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, bf16 *ws_row)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FwdSmem &sm = *reinterpret_cast<FwdSmem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int row0 = warp * 16;
-    const SgTile t = a.tiles[blockIdx.x];
-    build_rowmap(sm.m, a, t, tid);
-    bf16 *ws = a.train ? a.ws + size_t(blockIdx.x) * (WS_X + 4 * WS_H) : nullptr;
-    tile_features(sm.x, LD_IN, ws, sm.fs, a, sm.m, tid);
-    load_rows<KIN>(sm.w, LD_IN, a.wb + OFF_W1, tid);
-    __syncthreads();
-    float acc[16][4];
-    // layer 1: h1 = relu(W1 x + b1) -> ha
-    zero_acc(acc);
-    gemm_xwT<16, KIN>(acc, sm.x + row0 * LD_IN, LD_IN, sm.w, LD_IN, lane);
-    relu_store(acc, a.wf + OFF_B1, sm.ha, LD_H, ws ? ws + WS_X : nullptr, row0, lane);
-    __syncthreads();
-    // layer 2: h2 = relu(W2 h1 + b2) -> hg[:, 0:128]
-    load_rows<H>(sm.w, LD_H, a.wb + OFF_W2, tid);
-    __syncthreads();
-    zero_acc(acc);
-    gemm_xwT<16, H>(acc, sm.ha + row0 * LD_H, LD_H, sm.w, LD_H, lane);
-    relu_store(acc, a.wf + OFF_B2, sm.hg, LD_2H, ws ? ws + WS_X + WS_H : nullptr, row0, lane);
-    __syncthreads();
-    // layer 3: h3 = relu(W3 h2 + b3) -> ha
-    load_rows<H>(sm.w, LD_H, a.wb + OFF_W3, tid);
-    __syncthreads();
-    zero_acc(acc);
-    gemm_xwT<16, H>(acc, sm.hg + row0 * LD_2H, LD_2H, sm.w, LD_H, lane);
-    relu_store(acc, a.wf + OFF_B3, sm.ha, LD_H, ws ? ws + WS_X + 2 * WS_H : nullptr, row0, lane);
-    __syncthreads();
-    // [h3 ; g] -> hg
-    load_rows<2 * H>(sm.w, LD_2H, a.wb + OFF_W4, tid);
-    pool_context(sm.hg + H, LD_2H, sm.ha, LD_H, sm.m, t.ns, tid);
-    for (int i = tid; i < TILE * (H / 8); i += NTHREADS) {
-        const int r = i / (H / 8), v = i - r * (H / 8);
-        *reinterpret_cast<uint4 *>(sm.hg + r * LD_2H + v * 8) = *reinterpret_cast<const uint4 *>(sm.ha + r * LD_H + v * 8);
-    }
-    __syncthreads();
-    // head: u = relu(W4 [h3; g] + b4); logit = w5 . bf16(u) + b5
-    zero_acc(acc);
-    gemm_xwT<16, 2 * H>(acc, sm.hg + row0 * LD_2H, LD_2H, sm.w, LD_2H, lane);
-    {
-        const int gr = lane >> 2, tc = (lane & 3) * 2;
-        const float *b4 = a.wf + OFF_B4, *w5 = a.wf + OFF_W5;
-        bf16 *wu = ws ? ws + WS_X + 3 * WS_H : nullptr;
-        float s_lo = 0.0f, s_hi = 0.0f;
+    float s = 0.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < H; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld16<0>(r, taddr + c0);
+        tmem_ld16<16>(r, taddr + c0 + 16);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = j * 8 + tc;
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(acc[j][0] + b4[col], 0.0f), fmaxf(acc[j][1] + b4[col + 1], 0.0f));
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(acc[j][2] + b4[col], 0.0f), fmaxf(acc[j][3] + b4[col + 1], 0.0f));
-            s_lo += __low2float(lo) * w5[col] + __high2float(lo) * w5[col + 1];
-            s_hi += __low2float(hi) * w5[col] + __high2float(hi) * w5[col + 1];
-            if (wu) {
-                *reinterpret_cast<__nv_bfloat162 *>(wu + (row0 + gr) * H + col) = lo;
-                *reinterpret_cast<__nv_bfloat162 *>(wu + (row0 + gr + 8) * H + col) = hi;
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = q * 8 + 2 * e;
+                const __nv_bfloat162 u = __floats2bfloat162_rn(fmaxf(__uint_as_float(r[j]) + b4[c0 + j], 0.0f),
+                                                               fmaxf(__uint_as_float(r[j + 1]) + b4[c0 + j + 1], 0.0f));
+                s += __low2float(u) * w5[c0 + j] + __high2float(u) * w5[c0 + j + 1];
+                pk[e] = *reinterpret_cast<const uint32_t *>(&u);
             }
-        }
-        s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
-        s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
-        s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 1);
-        s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
-        if ((lane & 3) == 0) {
-            sm.logit[row0 + gr] = s_lo + a.wf[OFF_B5];
-            sm.logit[row0 + gr + 8] = s_hi + a.wf[OFF_B5];
+            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + c0 + q * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
-    __syncthreads();
-    // softmax over each race's rows; training: d loss / d logit and the loss
-    if (tid < t.ns) {
-        const int r0 = sm.m.state_row0[tid], r1 = sm.m.state_row0[tid + 1];
-        const int race = sm.m.state_race[tid];
-        const int base = a.b.race_off[race];
-        float mx = -INFINITY;
-        for (int row = r0; row < r1; ++row) mx = fmaxf(mx, sm.logit[row]);
-        float sum = 0.0f;
-        for (int row = r0; row < r1; ++row) sum += expf(sm.logit[row] - mx);
-        const float lsum = logf(sum);
-        float tsum = 0.0f, lossv = 0.0f;
-        if (a.train)
-            for (int row = r0; row < r1; ++row) tsum += a.target[base + (row - r0)];
+    return s;
+}
+
+// g = bfloat16(mean of h3 over each race's rows), written over the race's rows of the
+// canonical tile; one work item is (race, 8-column chunk).  Padding rows keep h3.
+__device__ void tc_pool_inplace(unsigned char *act, const RowMap &m, int ns, int ltid)
+{
+    const int items = ns * (H / 8);
+    for (int i = ltid; i < items; i += 128) {
+        const int st = i % ns, c = i / ns;
+        const int r0 = m.state_row0[st], r1 = m.state_row0[st + 1];
+        float sum[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sum[e] = 0.0f;
         for (int row = r0; row < r1; ++row) {
-            const float lq = sm.logit[row] - mx - lsum;  // log q
-            const float q = expf(lq);
-            if (a.probs) a.probs[base + (row - r0)] = q;
-            if (a.train) {
-                const float tv = a.target[base + (row - r0)];
-                a.ws_dlogit[size_t(blockIdx.x) * TILE + row] = (q * tsum - tv) * a.inv_races;
-                lossv -= tv * lq;
+            const uint4 v = *reinterpret_cast<const uint4 *>(act + canon_off(row, c * 8, H));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                sum[2 * e] += __uint_as_float(w[e] << 16);
+                sum[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
             }
         }
-        if (a.train && a.loss_acc) atomicAdd(a.loss_acc, lossv * a.inv_races);
+        const float n = float(r1 - r0);
+        const uint4 g = make_uint4(pack_bf16x2(sum[0] / n, sum[1] / n), pack_bf16x2(sum[2] / n, sum[3] / n),
+                                   pack_bf16x2(sum[4] / n, sum[5] / n), pack_bf16x2(sum[6] / n, sum[7] / n));
+        for (int row = r0; row < r1; ++row) *reinterpret_cast<uint4 *>(act + canon_off(row, c * 8, H)) = g;
     }
-    if (a.train && tid < TILE && tid >= t.nrows) a.ws_dlogit[size_t(blockIdx.x) * TILE + tid] = 0.0f;
+}
+
+struct __align__(128) TcPipe {
+    unsigned char x[TILE * KIN * 2];  // features, canonical K-major (K = 16)
+    unsigned char act[TILE * H * 2];  // h1, h2, h3, then g (canonical, K = 128); feature scratch before layer 1
+    RowMap m;
+    float logit[TILE];
+};
+
+struct TcSmem {
+    unsigned char w[WC_ELEMS * 2];  // W1, W2, W3, W4 (canonical image)
+    TcPipe pipe[2];
+    float bias[4][H];               // b1, b2, b3, b4
+    float w5[H];
+    float b5;
+    int abort[2];
+    uint32_t tmem_base;
+    unsigned long long mbar_w, mbar[2];
+};
+static_assert(sizeof(TcSmem) <= 227 * 1024, "forward shared memory");
+static_assert(sizeof(FeatScratch) <= TILE * H * 2, "feature scratch aliases the activation tile");
+
+// wait for this pipeline's product; on a timeout flag the pipeline and the launch
+__device__ __forceinline__ bool group_wait(TcSmem &sm, int wg, uint32_t &phase, const SgArgs &a)
+{
+    // warp-uniform, since the epilogue's tensor-memory loads are warp-collective
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&sm.mbar[wg], phase, a.wait_ns));
+    phase ^= 1u;
+    if (!done) {
+        *reinterpret_cast<volatile int *>(&sm.abort[wg]) = 1;
+        atomicOr(a.status, 1);
+    }
+    tc_after_sync();
+    return done;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_tiles)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int wg = tid >> 7, ltid = tid & 127;
+    TcPipe &P = sm.pipe[wg];
+    const GroupSync sync{1 + wg};
+    volatile int *abort_flag = &sm.abort[wg];
+
+    if (tid == 0) {
+        mbar_init(&sm.mbar_w, 1);
+        mbar_init(&sm.mbar[0], 1);
+        mbar_init(&sm.mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sm.abort[0] = sm.abort[1] = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem_base)),
+                     "r"(2 * H)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 4 * H; i += TC_THREADS) {
+        const int l = i / H, c = i - l * H;
+        sm.bias[l][c] = a.wf[(l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : l == 2 ? OFF_B3 : OFF_B4) + c];
+    }
+    if (tid < H) sm.w5[tid] = a.wf[OFF_W5 + tid];
+    if (tid == 0) sm.b5 = a.wf[OFF_B5];
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+        mbar_expect_tx(&sm.mbar_w, WC_ELEMS * 2);
+        bulk_g2s(sm.w + WC_W1 * 2, a.wc + WC_W1, (WC_W2 - WC_W1) * 2, &sm.mbar_w);
+        bulk_g2s(sm.w + WC_W2 * 2, a.wc + WC_W2, (WC_W3 - WC_W2) * 2, &sm.mbar_w);
+        bulk_g2s(sm.w + WC_W3 * 2, a.wc + WC_W3, (WC_W4 - WC_W3) * 2, &sm.mbar_w);
+        bulk_g2s(sm.w + WC_W4 * 2, a.wc + WC_W4, (WC_ELEMS - WC_W4) * 2, &sm.mbar_w);
+    }
+
+    const uint32_t tmem = sm.tmem_base + uint32_t(wg * H);                  // this pipeline's columns
+    const uint32_t taddr = tmem + (uint32_t((warp & 3) * 32) << 16);        // this warp's lanes
+    const uint32_t sx = smem_addr(P.x), sact = smem_addr(P.act), sw = smem_addr(sm.w);
+    const int row = ltid;  // tile row of this thread = its TMEM lane
+    uint32_t phase = 0;
+    bool weights_ready = false;
+
+    for (int ti = wg * gridDim.x + blockIdx.x; ti < n_tiles; ti += 2 * gridDim.x) {
+        const SgTile t = a.tiles[ti];
+        bf16 *ws = a.train ? a.ws + size_t(ti) * (WS_X + 4 * WS_H) : nullptr;
+        build_rowmap(P.m, a, t, ltid, sync);
+        {
+            float f[KIN];
+            tile_features(f, *reinterpret_cast<FeatScratch *>(P.act), a, P.m, ltid, sync);
+            const uint4 lo = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                                        pack_bf16x2(f[6], f[7]));
+            const uint4 hi = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
+                                        pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
+            *reinterpret_cast<uint4 *>(P.x + canon_off(row, 0, KIN)) = lo;
+            *reinterpret_cast<uint4 *>(P.x + canon_off(row, 8, KIN)) = hi;
+            if (ws) {
+                *reinterpret_cast<uint4 *>(ws + row * KIN) = lo;
+                *reinterpret_cast<uint4 *>(ws + row * KIN + 8) = hi;
+            }
+        }
+        fence_async_smem();
+        sync();
+
+        // layer 1: h1 = relu(W1 x + b1)
+        if (ltid == 0) {
+            const bool have_w = weights_ready || mbar_wait(&sm.mbar_w, 0, a.wait_ns);
+            tc_after_sync();
+            if (have_w) {
+                tc_mma(tmem, smem_desc(sx, 128, 2 * 128), smem_desc(sw + WC_W1 * 2, 128, 2 * 128), 0u);
+                tc_commit(&sm.mbar[wg]);
+            } else {
+                *abort_flag = 1;
+                atomicOr(a.status, 1);
+                mbar_arrive(&sm.mbar[wg]);  // release the group's waiters
+            }
+        }
+        weights_ready = true;
+        if (group_wait(sm, wg, phase, a)) tc_epilogue_relu(taddr, sm.bias[0], P.act, row, ws ? ws + WS_X + row * H : nullptr);
+        fence_async_smem();
+        tc_before_sync();
+        sync();
+        if (*abort_flag) break;
+
+        // layers 2 and 3: h = relu(W h_prev + b), in place
+        for (int l = 1; l <= 2; ++l) {
+            if (ltid == 0) {
+                tc_after_sync();
+                const uint32_t wl = sw + uint32_t(l == 1 ? WC_W2 : WC_W3) * 2;
+#pragma unroll
+                for (int ks = 0; ks < H / 16; ++ks)
+                    tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128), smem_desc(wl + ks * 256, 128, 16 * 128),
+                           ks > 0 ? 1u : 0u);
+                tc_commit(&sm.mbar[wg]);
+            }
+            if (group_wait(sm, wg, phase, a))
+                tc_epilogue_relu(taddr, sm.bias[l], P.act, row, ws ? ws + WS_X + l * WS_H + row * H : nullptr);
+            fence_async_smem();
+            tc_before_sync();
+            sync();
+            if (*abort_flag) break;
+        }
+        if (*abort_flag) break;
+
+        // head, first half: h3 . W4[:, 0:128]^T
+        if (ltid == 0) {
+            tc_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < H / 16; ++ks)
+                tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128), smem_desc(sw + WC_W4 * 2 + ks * 256, 128, 32 * 128),
+                       ks > 0 ? 1u : 0u);
+            tc_commit(&sm.mbar[wg]);
+        }
+        if (group_wait(sm, wg, phase, a)) tc_pool_inplace(P.act, P.m, t.ns, ltid);
+        fence_async_smem();
+        tc_before_sync();
+        sync();
+        if (*abort_flag) break;
+
+        // head, second half: + g . W4[:, 128:256]^T; u = relu(. + b4), logit = w5 . u + b5
+        if (ltid == 0) {
+            tc_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < H / 16; ++ks)
+                tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128),
+                       smem_desc(sw + WC_W4 * 2 + (H / 16 + ks) * 256, 128, 32 * 128), 1u);
+            tc_commit(&sm.mbar[wg]);
+        }
+        float logit = 0.0f;
+        if (group_wait(sm, wg, phase, a))
+            logit = tc_epilogue_head(taddr, sm.bias[3], sm.w5, ws ? ws + WS_X + 3 * WS_H + row * H : nullptr) + sm.b5;
+        P.logit[row] = logit;
+        tc_before_sync();
+        sync();
+        if (*abort_flag) break;
+
+        // softmax over each race's rows; training: d loss / d logit and the loss
+        if (ltid < t.ns) {
+            const int r0 = P.m.state_row0[ltid], r1 = P.m.state_row0[ltid + 1];
+            const int base = a.b.race_off[P.m.state_race[ltid]];
+            float mx = -INFINITY;
+            for (int q = r0; q < r1; ++q) mx = fmaxf(mx, P.logit[q]);
+            float sum = 0.0f;
+            for (int q = r0; q < r1; ++q) sum += expf(P.logit[q] - mx);
+            const float lsum = logf(sum);
+            float tsum = 0.0f, lossv = 0.0f;
+            if (a.train)
+                for (int q = r0; q < r1; ++q) tsum += a.target[base + (q - r0)];
+            for (int q = r0; q < r1; ++q) {
+                const float lq = P.logit[q] - mx - lsum;  // log q
+                const float qv = expf(lq);
+                if (a.probs) a.probs[base + (q - r0)] = qv;
+                if (a.train) {
+                    const float tv = a.target[base + (q - r0)];
+                    a.ws_dlogit[size_t(ti) * TILE + q] = (qv * tsum - tv) * a.inv_races;
+                    lossv -= tv * lq;
+                }
+            }
+            if (a.train && a.loss_acc) atomicAdd(a.loss_acc, lossv * a.inv_races);
+        }
+        if (a.train && ltid >= t.nrows) a.ws_dlogit[size_t(ti) * TILE + ltid] = 0.0f;
+        sync();
+    }
+    // every product this block issued has been waited for (or its wait gave up)
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(2 * H) : "memory");
+    }
 }
 
 // ------------------------------------------------------------------ backward
@@ -520,7 +798,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sg_backward(SgArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = warp * 16;
     const SgTile t = a.tiles[blockIdx.x];
-    build_rowmap(sm.m, a, t, tid);
+    build_rowmap(sm.m, a, t, tid, BlockSync{});
     const bf16 *ws = a.ws + size_t(blockIdx.x) * (WS_X + 4 * WS_H);
     const bf16 *ws_x = ws, *ws_h1 = ws + WS_X, *ws_h2 = ws_h1 + WS_H, *ws_h3 = ws_h2 + WS_H, *ws_u = ws_h3 + WS_H;
     float *g = a.grad;
@@ -642,7 +920,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) sg_backward(SgArgs a)
 
 // ------------------------------------------------------------------ optimizer
 
-__global__ void sg_adam(float *w, float *m, float *v, const float *grad, bf16 *wb, int n, float lr, float b1,
+// position of flat parameter i in the canonical bfloat16 image of W1..W4 (-1: not a matrix weight)
+__device__ __forceinline__ int canon_index(int i)
+{
+    int base, k_dim, j;
+    if (i < OFF_B1) {
+        base = WC_W1, k_dim = KIN, j = i - OFF_W1;
+    } else if (i >= OFF_W2 && i < OFF_B2) {
+        base = WC_W2, k_dim = H, j = i - OFF_W2;
+    } else if (i >= OFF_W3 && i < OFF_B3) {
+        base = WC_W3, k_dim = H, j = i - OFF_W3;
+    } else if (i >= OFF_W4 && i < OFF_B4) {
+        base = WC_W4, k_dim = 2 * H, j = i - OFF_W4;
+    } else {
+        return -1;
+    }
+    const int n = j / k_dim, k = j - n * k_dim;
+    return base + int(canon_off(n, k, k_dim) / 2);
+}
+
+__global__ void sg_adam(float *w, float *m, float *v, const float *grad, bf16 *wb, bf16 *wc, int n, float lr, float b1,
                         float b2, float eps, float wd, float c1, float c2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -655,13 +952,20 @@ __global__ void sg_adam(float *w, float *m, float *v, const float *grad, bf16 *w
     const float mh = mi / c1, vh = vi / c2;
     const float wi = w[i] - lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
     w[i] = wi;
-    wb[i] = __float2bfloat16_rn(wi);
+    const bf16 h = __float2bfloat16_rn(wi);
+    wb[i] = h;
+    const int ci = canon_index(i);
+    if (ci >= 0) wc[ci] = h;
 }
 
-__global__ void sg_to_bf16(const float *w, bf16 *wb, int n)
+__global__ void sg_to_bf16(const float *w, bf16 *wb, bf16 *wc, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
+    if (i >= n) return;
+    const bf16 h = __float2bfloat16_rn(w[i]);
+    wb[i] = h;
+    const int ci = canon_index(i);
+    if (ci >= 0) wc[ci] = h;
 }
 
 __global__ void scatter_probs(const float *src, const int32_t *dst_index, float *dst, int n)
@@ -695,6 +999,8 @@ struct SgRanges {
 struct bbe_surrogate {
     float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;  // float32 [N_PARAMS]
     bf16 *wb = nullptr;                                                // bfloat16 copy
+    bf16 *wc = nullptr;                                                // canonical W1..W4 image
+    int *d_status = nullptr;                                           // bounded-wait status word
     int64_t step = 0;
     // training plan state
     uint64_t epoch = 0;
@@ -725,16 +1031,29 @@ struct bbe_surrogate {
 
 namespace {
 
-size_t fwd_smem() { return sizeof(FwdSmem); }
+size_t fwd_smem() { return sizeof(TcSmem); }
 size_t bwd_smem() { return sizeof(BwdSmem); }
 
 bbe_status ensure_attrs()
 {
     static bool done = false;
     if (done) return BBE_OK;
-    SG_TRY(cudaFuncSetAttribute(sg_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
+    SG_TRY(cudaFuncSetAttribute(sg_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
     SG_TRY(cudaFuncSetAttribute(sg_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bwd_smem())));
     done = true;
+    return BBE_OK;
+}
+
+// persistent forward over n_tiles tiles: two tile pipelines per block, at most one block per SM
+bbe_status launch_forward(const SgArgs &a, int64_t n_tiles, cudaStream_t st)
+{
+    if (n_tiles <= 0) return BBE_OK;
+    int dev = 0, sms = 0;
+    SG_TRY(cudaGetDevice(&dev));
+    SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n_tiles + 1) / 2, sms));
+    sg_forward_tc<<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
+    SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
 
@@ -786,7 +1105,10 @@ SgArgs base_args(const bbe_surrogate *s, const bbe_batch *b)
 {
     SgArgs a{};
     a.wb = s->wb;
+    a.wc = s->wc;
     a.wf = s->w;
+    a.status = s->d_status;
+    a.wait_ns = kWaitNs;
     a.b = b->dev;
     a.tiles = s->d_tiles;
     a.order = s->d_order;
@@ -824,8 +1146,7 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.ws_dlogit = s->ws_dlogit;
     a.train = 1;
     SG_TRY(cudaMemsetAsync(s->grad, 0, N_PARAMS * sizeof(float), st));
-    sg_forward<<<unsigned(nt), NTHREADS, fwd_smem(), st>>>(a);
-    SG_TRY(cudaGetLastError());
+    if ((e = launch_forward(a, nt, st))) return e;
     sg_backward<<<unsigned(nt), NTHREADS, bwd_smem(), st>>>(a);
     SG_TRY(cudaGetLastError());
     return BBE_OK;
@@ -914,6 +1235,9 @@ bbe_status alloc_surrogate(bbe_surrogate *s)
     SG_TRY(cudaMalloc(&s->v, N_PARAMS * sizeof(float)));
     SG_TRY(cudaMalloc(&s->grad, N_PARAMS * sizeof(float)));
     SG_TRY(cudaMalloc(&s->wb, N_PARAMS * sizeof(bf16)));
+    SG_TRY(cudaMalloc(&s->wc, WC_ELEMS * sizeof(bf16)));
+    SG_TRY(cudaMalloc(&s->d_status, sizeof(int)));
+    SG_TRY(cudaMemset(s->d_status, 0, sizeof(int)));
     SG_TRY(cudaMalloc(&s->d_loss, sizeof(float)));
     SG_TRY(cudaMemset(s->m, 0, N_PARAMS * sizeof(float)));
     SG_TRY(cudaMemset(s->v, 0, N_PARAMS * sizeof(float)));
@@ -923,7 +1247,7 @@ bbe_status alloc_surrogate(bbe_surrogate *s)
 bbe_status upload_params(bbe_surrogate *s, const float *host)
 {
     SG_TRY(cudaMemcpy(s->w, host, N_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
-    sg_to_bf16<<<(N_PARAMS + 255) / 256, 256>>>(s->w, s->wb, N_PARAMS);
+    sg_to_bf16<<<(N_PARAMS + 255) / 256, 256>>>(s->w, s->wb, s->wc, N_PARAMS);
     SG_TRY(cudaGetLastError());
     SG_TRY(cudaMemset(s->m, 0, N_PARAMS * sizeof(float)));
     SG_TRY(cudaMemset(s->v, 0, N_PARAMS * sizeof(float)));
@@ -934,7 +1258,8 @@ bbe_status upload_params(bbe_surrogate *s, const float *host)
 
 void free_surrogate(bbe_surrogate *s)
 {
-    for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->d_tiles,
+    for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->wc,
+                    (void *)s->d_status, (void *)s->d_tiles,
                     (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
                     (void *)s->d_iorder})
         if (p) cudaFree(p);
@@ -953,9 +1278,7 @@ bbe_status forward_all(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     SgArgs a = base_args(s, b);
     a.probs = probs;
     a.train = 0;
-    sg_forward<<<unsigned(tiles.size()), NTHREADS, fwd_smem(), st>>>(a);
-    SG_TRY(cudaGetLastError());
-    return BBE_OK;
+    return launch_forward(a, int64_t(tiles.size()), st);
 }
 
 }  // namespace
@@ -1082,7 +1405,7 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
         s->step += 1;
         const float c1 = 1.0f - std::pow(cfg->beta1, float(s->step));
         const float c2 = 1.0f - std::pow(cfg->beta2, float(s->step));
-        sg_adam<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->w, s->m, s->v, s->grad, s->wb, N_PARAMS, cfg->lr,
+        sg_adam<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->w, s->m, s->v, s->grad, s->wb, s->wc, N_PARAMS, cfg->lr,
                                                        cfg->beta1, cfg->beta2, cfg->eps, cfg->weight_decay, c1, c2);
         SG_TRY(cudaGetLastError());
     }
@@ -1144,8 +1467,7 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         a.order = s->d_iorder;
         a.probs = probs;
         a.train = 0;
-        sg_forward<<<unsigned(s->iplan_tiles), NTHREADS, fwd_smem(), st>>>(a);
-        SG_TRY(cudaGetLastError());
+        if ((e = launch_forward(a, s->iplan_tiles, st))) return e;
     }
     const std::vector<int32_t> &mc = s->iplan_mc;
     const std::vector<uint8_t> &flag = s->iplan_flag;
@@ -1211,6 +1533,24 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
     if (used_mc) {
         SG_TRY(cudaMemcpyAsync(used_mc, flag.data(), flag.size(), cudaMemcpyHostToDevice, st));
         SG_TRY(cudaStreamSynchronize(st));
+    }
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_status(bbe_surrogate *s, void *cuda_stream)
+{
+    if (!s) {
+        bbe::set_error("surrogate is NULL");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int h = 0;
+    SG_TRY(cudaStreamSynchronize(st));
+    SG_TRY(cudaMemcpy(&h, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        SG_TRY(cudaMemset(s->d_status, 0, sizeof(int)));
+        bbe::set_error("a surrogate kernel gave up a bounded device wait");
+        return BBE_ERR_TIMEOUT;
     }
     return BBE_OK;
 }

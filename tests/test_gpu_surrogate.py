@@ -51,7 +51,7 @@ def test_forward_matches_reference(bbe):
         with bbe.Batch(rb) as b:
             probs = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
             bbe.bbe_surrogate_forward(s, b.handle, probs)
-            torch.cuda.synchronize()
+            bbe.bbe_surrogate_status(s)
             got = probs.cpu().numpy().astype(np.float64)
         assert np.allclose(bbe.bbe_surrogate_get_params(s), params)
     finally:
@@ -61,6 +61,31 @@ def test_forward_matches_reference(bbe):
     assert np.allclose(sums, 1.0, atol=1e-5)
     err = np.abs(got - want)
     assert err.max() < 5e-3 and err.mean() < 3e-4, (err.max(), err.mean())
+
+
+def test_forward_persistent_blocks_match_reference(bbe):
+    # more tiles than the persistent grid has tile pipelines (two per SM), full 64-race tiles
+    # of two competitors, single-competitor races
+    rb = W.concat([W.uniform_batch(seed=51, n_races=3000, n=20, rollouts=10),
+                   W.uneven_batch(seed=52, n_races=1500, n_lo=2, n_hi=2, rollouts=10),
+                   W.uneven_batch(seed=53, n_races=300, n_lo=1, n_hi=3, rollouts=10)])
+    params = S.init_params(3).astype(np.float32)
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        with bbe.Batch(rb) as b:
+            probs = torch.full((rb.n_total,), float("nan"), dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_forward(s, b.handle, probs)
+            bbe.bbe_surrogate_status(s)
+            got = probs.cpu().numpy().astype(np.float64)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    want, _ = S.forward(params.astype(np.float64), ref_inputs(rb), rb.race_off, bf16=True)
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - want)
+    assert err.max() < 5e-3 and err.mean() < 3e-4, (err.max(), err.mean())
+    single = np.flatnonzero(np.diff(rb.race_off) == 1)
+    assert np.all(got[rb.race_off[single]] == 1.0)
 
 
 def test_gradient_matches_reference(bbe):
