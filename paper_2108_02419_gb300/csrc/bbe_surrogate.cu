@@ -58,11 +58,11 @@ constexpr int WC_W3 = WC_W2 + H * H;
 constexpr int WC_W4 = WC_W3 + H * H;
 constexpr int WC_ELEMS = WC_W4 + H * 2 * H;
 
-constexpr int TC_THREADS = 256;                  // forward: two warpgroups, one tile pipeline each
+constexpr int TC_THREADS = 512;                  // forward: two tile pipelines of two warpgroups each
+constexpr int TC_PIPE = 256;                     // threads of one pipeline
 constexpr long long kWaitNs = 2000000000LL;      // limit of every device-side wait (2 s)
 
 // shared-memory row strides (bf16 elements): +8 keeps ldmatrix rows on distinct banks
-constexpr int LD_IN = KIN + 8;   // 24
 constexpr int LD_H = H + 8;      // 136
 constexpr int LD_2H = 2 * H + 8; // 264
 
@@ -74,6 +74,16 @@ struct SgTile {
     int32_t s0;     // first position in the order array
     int32_t ns;     // races in the tile
     int32_t nrows;  // competitor rows
+    int32_t pad;
+};
+
+// race layout of a tile, written by the feature kernel and moved into the tensor-core
+// kernel by a bulk copy (size a multiple of 16 bytes)
+struct TileMeta {
+    int32_t ns, nrows;
+    int32_t state_row0[MAX_STATES + 1];  // first row of each race; [ns] = rows in use
+    int32_t state_race[MAX_STATES];      // race index of each race slot
+    int8_t row_state[TILE];              // race slot of each row (-1: padding)
     int32_t pad;
 };
 
@@ -92,6 +102,9 @@ struct SgArgs {
     bf16 *ws;              // training workspace, tile-major
     float *ws_dlogit;      // training: d loss / d logit per tile row
     int train;
+    unsigned char *xbuf;   // forward: per-tile features, canonical operand layout (TILE * KIN bf16)
+    TileMeta *meta;        // forward: per-tile race layout
+    float *logits;         // forward: per-tile-row logits
     int *status;           // set to 1 when a bounded device wait gave up
     long long wait_ns;     // limit of each wait
 };
@@ -216,14 +229,14 @@ __device__ __forceinline__ void atomic_add_colsum(float *g, const float (&v)[NT]
 
 // ------------------------------------------------------------------ tile bookkeeping
 
-// barrier of the threads that work on one tile: the whole block (backward) or one
-// warpgroup (forward; named barrier 1 + group)
+// barrier of the threads that work on one tile: the whole block, or the threads of one
+// forward tile pipeline (named barrier 1 + pipeline)
 struct BlockSync {
     __device__ void operator()() const { __syncthreads(); }
 };
 struct GroupSync {
-    int id;
-    __device__ void operator()() const { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+    int id, count;
+    __device__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
 };
 
 struct RowMap {
@@ -328,8 +341,9 @@ __device__ void tile_features(float (&f)[KIN], FeatScratch &fs, const SgArgs &a,
     }
 }
 
-// mean over each race's rows of h (bf16, stride ldh) into g (bf16, stride ldg, per row);
-// padding rows get zeros so that nothing undefined reaches a matrix product
+// mean over each race's rows of h (bf16, stride ldh) into g (bf16, stride ldg, per row), as
+// bfloat16(sum x (1/n)) like the forward kernel; padding rows get zeros so that nothing
+// undefined reaches a matrix product
 __device__ void pool_context(bf16 *g, int ldg, const bf16 *h, int ldh, const RowMap &m, int ns, int tid)
 {
     if (tid < H) {
@@ -338,7 +352,7 @@ __device__ void pool_context(bf16 *g, int ldg, const bf16 *h, int ldh, const Row
             const int r0 = m.state_row0[s], r1 = m.state_row0[s + 1];
             float sum = 0.0f;
             for (int row = r0; row < r1; ++row) sum += __bfloat162float(h[row * ldh + col]);
-            const bf16 gv = __float2bfloat16_rn(sum / float(r1 - r0));
+            const bf16 gv = __float2bfloat16_rn(sum * (1.0f / float(r1 - r0)));
             for (int row = r0; row < r1; ++row) g[row * ldg + col] = gv;
         }
         for (int row = m.state_row0[ns]; row < TILE; ++row) g[row * ldg + col] = __float2bfloat16_rn(0.0f);
@@ -347,19 +361,25 @@ __device__ void pool_context(bf16 *g, int ldg, const bf16 *h, int ldh, const Row
 
 // ------------------------------------------------------------------ forward (tcgen05)
 //
-// A persistent block of two warpgroups runs two independent tile pipelines that share one
-// copy of the layer weights, kept in shared memory for the whole launch in the canonical
-// K-major operand layout (8-row x 16-byte core matrices, no swizzle).  The optimizer keeps
-// a bfloat16 image of W1..W4 in that layout in global memory, so four bulk asynchronous
-// copies bring them in.  Per layer, one thread of the warpgroup issues tcgen05.mma
-// (M = 128 tile rows, N = 128 outputs, K = 16 per instruction) into the pipeline's 128
-// tensor-memory columns and commits to the pipeline's mbarrier; then the four warps read
-// the float32 accumulators back (warp w of the group reads TMEM lanes 32w..32w+31, one tile
-// row per thread), add the bias, apply ReLU and write bfloat16 activations over the layer's
-// input, which the finished product no longer reads.  The head [h3 ; g] W4^T is two
-// accumulating products: h3 against the first 128 columns of W4, then, once the per-race
-// mean g has replaced h3 in place, g against the other 128.  While one pipeline waits for
-// its product the other one runs its epilogue on the CUDA cores.
+// Three launches.  sg_prep (one 128-thread block per tile, many blocks per SM so that the
+// scattered loads of the race data overlap) writes each tile's bfloat16 features in the
+// canonical operand layout and a record of its race layout.  sg_forward_tc is persistent:
+// a block of two warpgroups runs two independent tile pipelines that share one copy of the
+// layer weights, kept in shared memory for the whole launch in the canonical K-major
+// operand layout (8-row x 16-byte core matrices, no swizzle); the optimizer keeps a
+// bfloat16 image of W1..W4 in that layout in global memory, so four bulk asynchronous
+// copies bring them in, and each tile's features and layout record arrive the same way,
+// double-buffered one tile ahead.  Per layer, one thread of the warpgroup issues
+// tcgen05.mma (M = 128 tile rows, N = 128 outputs, K = 16 per instruction) into the
+// pipeline's 128 tensor-memory columns and commits to the pipeline's mbarrier; then the
+// four warps read the float32 accumulators back (warp w of the group reads TMEM lanes
+// 32w..32w+31, one tile row per thread), add the bias, apply ReLU and write bfloat16
+// activations over the layer's input, which the finished product no longer reads.  The
+// head [h3 ; g] W4^T is two accumulating products: h3 against the first 128 columns of W4,
+// then, once the per-race mean g has replaced h3 in place, g against the other 128.  While
+// one pipeline waits for its product the other one runs its epilogue on the CUDA cores.
+// sg_softmax (one warp per tile) turns the logits into per-race probabilities and, when
+// training, the loss and its gradient with respect to the logits.
 
 // byte offset of element (row, k) of a canonical K-major operand with kdim columns
 __host__ __device__ constexpr uint32_t canon_off(int row, int k, int kdim)
@@ -430,15 +450,32 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
 }
 
-// instruction descriptor of kind::f16: float32 D, bfloat16 A and B, both K-major, N = 128, M = 128
+// instruction descriptor of kind::f16: float32 D, bfloat16 A and B, A K-major, N = 128,
+// M = 128; B K-major (kIdesc) or MN-major (kIdescBmn, bit 16).  For an MN-major operand without
+// swizzle the descriptor's lbo is the byte distance between core matrices along K and sbo
+// the distance along N.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(H >> 3) << 17) | (uint32_t(TILE >> 4) << 24);
+constexpr uint32_t kIdescBmn = kIdesc | (1u << 16);
 
+// D (+)= A . B^T with A and B in shared memory
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// D (+)= A . B^T with A in tensor memory (lane = row, 8 columns of bfloat16 pairs per K = 16,
+// even k in the low half) and B in shared memory
+__device__ __forceinline__ void tc_mma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bd), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -449,9 +486,10 @@ __device__ __forceinline__ void tc_commit(unsigned long long *bar)
 }
 
 // 16 consecutive float32 columns of this thread's TMEM lane into r[O..O+15]
-template <int O>
-__device__ __forceinline__ void tmem_ld16(uint32_t (&r)[32], uint32_t taddr)
+template <int O, int N>
+__device__ __forceinline__ void tmem_ld16(uint32_t (&r)[N], uint32_t taddr)
 {
+    static_assert(O + 16 <= N, "register range");
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[O + 0]), "=r"(r[O + 1]), "=r"(r[O + 2]), "=r"(r[O + 3]), "=r"(r[O + 4]), "=r"(r[O + 5]),
@@ -462,22 +500,50 @@ __device__ __forceinline__ void tmem_ld16(uint32_t (&r)[32], uint32_t taddr)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// r[O..O+15] into 16 consecutive 32-bit columns of this thread's TMEM lane
+template <int O, int N>
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[N])
+{
+    static_assert(O + 16 <= N, "register range");
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[O + 0]), "r"(r[O + 1]), "r"(r[O + 2]), "r"(r[O + 3]), "r"(r[O + 4]), "r"(r[O + 5]), "r"(r[O + 6]),
+        "r"(r[O + 7]), "r"(r[O + 8]), "r"(r[O + 9]), "r"(r[O + 10]), "r"(r[O + 11]), "r"(r[O + 12]), "r"(r[O + 13]),
+        "r"(r[O + 14]), "r"(r[O + 15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// accumulator row (this thread's TMEM lane) -> bias + ReLU -> bfloat16 into the canonical
-// activation tile and, when training, into the workspace row
-__device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
-                                                 bf16 *ws_row)
+// bfloat16 pair {relu(lo), relu(hi)} rounded to nearest (lo in the low half)
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
 {
-#pragma unroll 1
-    for (int c0 = 0; c0 < H; c0 += 32) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// Epilogues.  Two threads share a tile row (its TMEM lane): thread half ch handles the 64
+// accumulator columns [64 ch, 64 ch + 64).
+
+// bias + ReLU -> bfloat16 into the canonical activation tile and, when training, into the
+// workspace row
+__device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
+                                                 bf16 *ws_row, int c0)
+{
+    unsigned char *arow = act + (row >> 3) * 2048 + (row & 7) * 16;
+#pragma unroll
+    for (int cb = c0; cb < c0 + 64; cb += 32) {
         uint32_t r[32];
-        tmem_ld16<0>(r, taddr + c0);
-        tmem_ld16<16>(r, taddr + c0 + 16);
+        tmem_ld16<0>(r, taddr + cb);
+        tmem_ld16<16>(r, taddr + cb + 16);
         tmem_wait_ld();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -485,25 +551,24 @@ __device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bi
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = q * 8 + 2 * e;
-                pk[e] = pack_bf16x2(fmaxf(__uint_as_float(r[j]) + bias[c0 + j], 0.0f),
-                                    fmaxf(__uint_as_float(r[j + 1]) + bias[c0 + j + 1], 0.0f));
+                pk[e] = relu_bf16x2(__uint_as_float(r[j]) + bias[cb + j], __uint_as_float(r[j + 1]) + bias[cb + j + 1]);
             }
             const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *reinterpret_cast<uint4 *>(act + canon_off(row, c0 + q * 8, H)) = v;
-            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + c0 + q * 8) = v;
+            *reinterpret_cast<uint4 *>(arow + ((cb >> 3) + q) * 128) = v;
+            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + cb + q * 8) = v;
         }
     }
 }
 
-// head epilogue: u = bfloat16(relu(acc + b4)) (workspace row when training), returns w5 . u
-__device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, bf16 *ws_row)
+// head: u = bfloat16(relu(acc + b4)) (workspace row when training); returns this half's w5 . u
+__device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, bf16 *ws_row, int c0)
 {
     float s = 0.0f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < H; c0 += 32) {
+#pragma unroll
+    for (int cb = c0; cb < c0 + 64; cb += 32) {
         uint32_t r[32];
-        tmem_ld16<0>(r, taddr + c0);
-        tmem_ld16<16>(r, taddr + c0 + 16);
+        tmem_ld16<0>(r, taddr + cb);
+        tmem_ld16<16>(r, taddr + cb + 16);
         tmem_wait_ld();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -511,49 +576,57 @@ __device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = q * 8 + 2 * e;
-                const __nv_bfloat162 u = __floats2bfloat162_rn(fmaxf(__uint_as_float(r[j]) + b4[c0 + j], 0.0f),
-                                                               fmaxf(__uint_as_float(r[j + 1]) + b4[c0 + j + 1], 0.0f));
-                s += __low2float(u) * w5[c0 + j] + __high2float(u) * w5[c0 + j + 1];
-                pk[e] = *reinterpret_cast<const uint32_t *>(&u);
+                pk[e] = relu_bf16x2(__uint_as_float(r[j]) + b4[cb + j], __uint_as_float(r[j + 1]) + b4[cb + j + 1]);
+                s += __uint_as_float(pk[e] << 16) * w5[cb + j] + __uint_as_float(pk[e] & 0xFFFF0000u) * w5[cb + j + 1];
             }
-            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + c0 + q * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + cb + q * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
     return s;
 }
 
-// g = bfloat16(mean of h3 over each race's rows), written over the race's rows of the
-// canonical tile; one work item is (race, 8-column chunk).  Padding rows keep h3.
-__device__ void tc_pool_inplace(unsigned char *act, const RowMap &m, int ns, int ltid)
+// Row `row` of the pooling matrix S, k in [c0, c0 + 64), into 32 TMEM columns of bfloat16
+// pairs: S[row][k] = 1 when rows row and k belong to the same race (r0 <= k < r1; a zero row
+// for padding), so that S . h3 sums h3 over the race of every row.
+__device__ __forceinline__ void tc_store_pool_row(uint32_t taddr_s, int r0, int r1, int c0)
 {
-    const int items = ns * (H / 8);
-    for (int i = ltid; i < items; i += 128) {
-        const int st = i % ns, c = i / ns;
-        const int r0 = m.state_row0[st], r1 = m.state_row0[st + 1];
-        float sum[8];
+    const uint32_t n = uint32_t(r1 - r0);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) sum[e] = 0.0f;
-        for (int row = r0; row < r1; ++row) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(act + canon_off(row, c * 8, H));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[16];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                sum[2 * e] += __uint_as_float(w[e] << 16);
-                sum[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
-            }
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t t = uint32_t(c0 + 32 * h + 2 * j - r0);  // k - r0, wrapping below r0
+            v[j] = (t < n ? 0x3F80u : 0u) | (t + 1u < n ? 0x3F800000u : 0u);
         }
-        const float n = float(r1 - r0);
-        const uint4 g = make_uint4(pack_bf16x2(sum[0] / n, sum[1] / n), pack_bf16x2(sum[2] / n, sum[3] / n),
-                                   pack_bf16x2(sum[4] / n, sum[5] / n), pack_bf16x2(sum[6] / n, sum[7] / n));
-        for (int row = r0; row < r1; ++row) *reinterpret_cast<uint4 *>(act + canon_off(row, c * 8, H)) = g;
+        tmem_st16<0>(taddr_s + c0 / 2 + 16 * h, v);
+    }
+}
+
+// pooled sums (TMEM accumulator columns [c0, c0 + 64)) -> g = bfloat16(sum x inv_n) -> 32
+// TMEM columns of bfloat16 pairs, the A operand of the head's second product
+__device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t taddr_g, float inv_n, int c0)
+{
+#pragma unroll
+    for (int cb = c0; cb < c0 + 64; cb += 32) {
+        uint32_t r[32];
+        tmem_ld16<0>(r, taddr_d + cb);
+        tmem_ld16<16>(r, taddr_d + cb + 16);
+        tmem_wait_ld();
+        uint32_t g[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            g[j] = pack_bf16x2(__uint_as_float(r[2 * j]) * inv_n, __uint_as_float(r[2 * j + 1]) * inv_n);
+        tmem_st16<0>(taddr_g + cb / 2, g);
     }
 }
 
 struct __align__(128) TcPipe {
-    unsigned char x[TILE * KIN * 2];  // features, canonical K-major (K = 16)
-    unsigned char act[TILE * H * 2];  // h1, h2, h3, then g (canonical, K = 128); feature scratch before layer 1
-    RowMap m;
-    float logit[TILE];
+    unsigned char xb[2][TILE * KIN * 2];  // features of this and the next tile, canonical K-major (K = 16)
+    TileMeta mt[2];                       // their race layout
+    unsigned char act[TILE * H * 2];      // h1, h2, h3, then g (canonical, K = 128)
+    unsigned long long mbar_in[2];        // bulk copies of xb[i], mt[i]
+    float logit_part[2][TILE];            // the two column halves of w5 . u
 };
 
 struct TcSmem {
@@ -567,7 +640,7 @@ struct TcSmem {
     unsigned long long mbar_w, mbar[2];
 };
 static_assert(sizeof(TcSmem) <= 227 * 1024, "forward shared memory");
-static_assert(sizeof(FeatScratch) <= TILE * H * 2, "feature scratch aliases the activation tile");
+static_assert(sizeof(TileMeta) % 16 == 0, "tile layout records are moved by bulk copies");
 
 // wait for this pipeline's product; on a timeout flag the pipeline and the launch
 __device__ __forceinline__ bool group_wait(TcSmem &sm, int wg, uint32_t &phase, const SgArgs &a)
@@ -583,26 +656,72 @@ __device__ __forceinline__ bool group_wait(TcSmem &sm, int wg, uint32_t &phase, 
     return done;
 }
 
+// bulk copies of tile ti's features and race layout into buffer i of the pipeline
+__device__ __forceinline__ void load_tile_inputs(TcPipe &P, int i, int ti, const SgArgs &a)
+{
+    mbar_expect_tx(&P.mbar_in[i], uint32_t(TILE * KIN * 2 + sizeof(TileMeta)));
+    bulk_g2s(P.xb[i], a.xbuf + size_t(ti) * (TILE * KIN * 2), TILE * KIN * 2, &P.mbar_in[i]);
+    bulk_g2s(&P.mt[i], a.meta + ti, uint32_t(sizeof(TileMeta)), &P.mbar_in[i]);
+}
+
+// Tile features and race layout (one 128-thread block per tile): x in the canonical operand
+// layout (and row-major into the training workspace), the tile's race layout record.
+__global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
+{
+    __shared__ RowMap m;
+    __shared__ FeatScratch fs;
+    const int tid = threadIdx.x, ti = blockIdx.x;
+    const SgTile t = a.tiles[ti];
+    build_rowmap(m, a, t, tid, BlockSync{});
+    float f[KIN];
+    tile_features(f, fs, a, m, tid, BlockSync{});
+    const uint4 lo = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                                pack_bf16x2(f[6], f[7]));
+    const uint4 hi = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]), pack_bf16x2(f[12], f[13]),
+                                pack_bf16x2(f[14], f[15]));
+    unsigned char *xt = a.xbuf + size_t(ti) * (TILE * KIN * 2);
+    *reinterpret_cast<uint4 *>(xt + canon_off(tid, 0, KIN)) = lo;
+    *reinterpret_cast<uint4 *>(xt + canon_off(tid, 8, KIN)) = hi;
+    if (a.train) {
+        bf16 *wx = a.ws + size_t(ti) * (WS_X + 4 * WS_H) + tid * KIN;
+        *reinterpret_cast<uint4 *>(wx) = lo;
+        *reinterpret_cast<uint4 *>(wx + 8) = hi;
+    }
+    TileMeta &mt = a.meta[ti];
+    if (tid == 0) {
+        mt.ns = t.ns;
+        mt.nrows = t.nrows;
+    }
+    if (tid <= t.ns) mt.state_row0[tid] = m.state_row0[tid];
+    if (tid < t.ns) mt.state_race[tid] = m.state_race[tid];
+    mt.row_state[tid] = int8_t(m.row_race[tid] >= 0 ? m.row_state[tid] : -1);
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_tiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int wg = tid >> 7, ltid = tid & 127;
-    TcPipe &P = sm.pipe[wg];
-    const GroupSync sync{1 + wg};
-    volatile int *abort_flag = &sm.abort[wg];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int p = tid / TC_PIPE, pt = tid % TC_PIPE;  // pipeline, thread within it
+    const int ch = (pt >> 7) & 1;                     // column half of this thread
+    TcPipe &P = sm.pipe[p];
+    const GroupSync sync{1 + p, TC_PIPE};
+    volatile int *abort_flag = &sm.abort[p];
+    const int first = p * gridDim.x + blockIdx.x, stride = 2 * gridDim.x;
 
-    if (tid == 0) {
-        mbar_init(&sm.mbar_w, 1);
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
+    if (pt == 0) {
+        if (p == 0) {
+            mbar_init(&sm.mbar_w, 1);
+            sm.abort[0] = sm.abort[1] = 0;
+        }
+        mbar_init(&sm.mbar[p], 1);
+        mbar_init(&P.mbar_in[0], 1);
+        mbar_init(&P.mbar_in[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sm.abort[0] = sm.abort[1] = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem_base)),
-                     "r"(2 * H)
+                     "r"(4 * H)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -622,50 +741,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
         bulk_g2s(sm.w + WC_W3 * 2, a.wc + WC_W3, (WC_W4 - WC_W3) * 2, &sm.mbar_w);
         bulk_g2s(sm.w + WC_W4 * 2, a.wc + WC_W4, (WC_ELEMS - WC_W4) * 2, &sm.mbar_w);
     }
+    if (pt == 0 && first < n_tiles) load_tile_inputs(P, 0, first, a);
 
-    const uint32_t tmem = sm.tmem_base + uint32_t(wg * H);                  // this pipeline's columns
-    const uint32_t taddr = tmem + (uint32_t((warp & 3) * 32) << 16);        // this warp's lanes
-    const uint32_t sx = smem_addr(P.x), sact = smem_addr(P.act), sw = smem_addr(sm.w);
-    const int row = ltid;  // tile row of this thread = its TMEM lane
+    // this pipeline's 256 TMEM columns: accumulator D [0, 128), pooling matrix S [128, 192),
+    // context g [192, 256); this warp reads and writes lanes 32 (warp % 4) .. 32 (warp % 4) + 31
+    const uint32_t tmem = sm.tmem_base + uint32_t(p * 2 * H);
+    const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
+    const uint32_t td = tmem + lane_off, ts = tmem + H + lane_off, tg = tmem + H + H / 2 + lane_off;
+    const uint32_t sact = smem_addr(P.act), sw = smem_addr(sm.w);
+    const int row = (warp & 3) * 32 + lane;  // tile row of this thread = its TMEM lane
+    const int c0 = ch * (H / 2);             // first accumulator column of this thread
     uint32_t phase = 0;
     bool weights_ready = false;
+    int pending = first < n_tiles ? 0 : -1;  // input buffer with a copy in flight (issuing thread)
+    uint32_t pending_parity = 0;
 
-    for (int ti = wg * gridDim.x + blockIdx.x; ti < n_tiles; ti += 2 * gridDim.x) {
-        const SgTile t = a.tiles[ti];
-        bf16 *ws = a.train ? a.ws + size_t(ti) * (WS_X + 4 * WS_H) : nullptr;
-        build_rowmap(P.m, a, t, ltid, sync);
-        {
-            float f[KIN];
-            tile_features(f, *reinterpret_cast<FeatScratch *>(P.act), a, P.m, ltid, sync);
-            const uint4 lo = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
-                                        pack_bf16x2(f[6], f[7]));
-            const uint4 hi = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
-                                        pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
-            *reinterpret_cast<uint4 *>(P.x + canon_off(row, 0, KIN)) = lo;
-            *reinterpret_cast<uint4 *>(P.x + canon_off(row, 8, KIN)) = hi;
-            if (ws) {
-                *reinterpret_cast<uint4 *>(ws + row * KIN) = lo;
-                *reinterpret_cast<uint4 *>(ws + row * KIN + 8) = hi;
-            }
+    int k = 0;
+    for (int ti = first; ti < n_tiles; ti += stride, ++k) {
+        const int ib = k & 1;
+        const uint32_t in_parity = uint32_t(k >> 1) & 1u;
+        const bool in_ok = __all_sync(0xffffffffu, mbar_wait(&P.mbar_in[ib], in_parity, a.wait_ns));
+        if (!in_ok) {
+            *abort_flag = 1;
+            atomicOr(a.status, 1);
         }
-        fence_async_smem();
-        sync();
+        bf16 *ws = a.train ? a.ws + size_t(ti) * (WS_X + 4 * WS_H) : nullptr;
+        const TileMeta &mt = P.mt[ib];
 
-        // layer 1: h1 = relu(W1 x + b1)
-        if (ltid == 0) {
+        // layer 1: h1 = relu(W1 x + b1); the next tile's inputs are fetched meanwhile
+        if (pt == 0) {
+            pending = -1;
             const bool have_w = weights_ready || mbar_wait(&sm.mbar_w, 0, a.wait_ns);
             tc_after_sync();
-            if (have_w) {
-                tc_mma(tmem, smem_desc(sx, 128, 2 * 128), smem_desc(sw + WC_W1 * 2, 128, 2 * 128), 0u);
-                tc_commit(&sm.mbar[wg]);
+            if (have_w && in_ok) {
+                if (ti + stride < n_tiles) {
+                    load_tile_inputs(P, ib ^ 1, ti + stride, a);
+                    pending = ib ^ 1;
+                    pending_parity = uint32_t((k + 1) >> 1) & 1u;
+                }
+                tc_mma(tmem, smem_desc(smem_addr(P.xb[ib]), 128, 2 * 128), smem_desc(sw + WC_W1 * 2, 128, 2 * 128), 0u);
+                tc_commit(&sm.mbar[p]);
             } else {
                 *abort_flag = 1;
                 atomicOr(a.status, 1);
-                mbar_arrive(&sm.mbar[wg]);  // release the group's waiters
+                mbar_arrive(&sm.mbar[p]);  // release the pipeline's waiters
             }
         }
         weights_ready = true;
-        if (group_wait(sm, wg, phase, a)) tc_epilogue_relu(taddr, sm.bias[0], P.act, row, ws ? ws + WS_X + row * H : nullptr);
+        // meanwhile: this row's part of the pooling matrix and its race's 1 / n
+        float inv_n = 0.0f;
+        {
+            const int st = in_ok ? mt.row_state[row] : -1;
+            int r0 = 0, r1 = 0;
+            if (st >= 0) {
+                r0 = mt.state_row0[st];
+                r1 = mt.state_row0[st + 1];
+                inv_n = 1.0f / float(r1 - r0);
+            }
+            tc_store_pool_row(ts, r0, r1, c0);
+            tmem_wait_st();
+        }
+        if (group_wait(sm, p, phase, a)) tc_epilogue_relu(td, sm.bias[0], P.act, row, ws ? ws + WS_X + row * H : nullptr, c0);
         fence_async_smem();
         tc_before_sync();
         sync();
@@ -673,17 +809,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
 
         // layers 2 and 3: h = relu(W h_prev + b), in place
         for (int l = 1; l <= 2; ++l) {
-            if (ltid == 0) {
+            if (pt == 0) {
                 tc_after_sync();
                 const uint32_t wl = sw + uint32_t(l == 1 ? WC_W2 : WC_W3) * 2;
 #pragma unroll
                 for (int ks = 0; ks < H / 16; ++ks)
                     tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128), smem_desc(wl + ks * 256, 128, 16 * 128),
                            ks > 0 ? 1u : 0u);
-                tc_commit(&sm.mbar[wg]);
+                tc_commit(&sm.mbar[p]);
             }
-            if (group_wait(sm, wg, phase, a))
-                tc_epilogue_relu(taddr, sm.bias[l], P.act, row, ws ? ws + WS_X + l * WS_H + row * H : nullptr);
+            if (group_wait(sm, p, phase, a))
+                tc_epilogue_relu(td, sm.bias[l], P.act, row, ws ? ws + WS_X + l * WS_H + row * H : nullptr, c0);
             fence_async_smem();
             tc_before_sync();
             sync();
@@ -691,71 +827,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
         }
         if (*abort_flag) break;
 
-        // head, first half: h3 . W4[:, 0:128]^T
-        if (ltid == 0) {
+        // pooled sums S . h3: A = S from tensor memory, B = h3^T, i.e. the activation tile read
+        // as an MN-major operand (core matrices 16 B apart along N, 2048 B apart along K)
+        if (pt == 0) {
+            tc_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < TILE / 16; ++ks)
+                tc_mma_ta(tmem, tmem + H + ks * 8, smem_desc(sact + ks * 4096, 2048, 128), kIdescBmn, ks > 0 ? 1u : 0u);
+            tc_commit(&sm.mbar[p]);
+        }
+        if (group_wait(sm, p, phase, a)) tc_epilogue_pool(td, tg, inv_n, c0);
+        tmem_wait_st();
+        tc_before_sync();
+        sync();
+        if (*abort_flag) break;
+
+        // head: h3 . W4[:, 0:128]^T + g . W4[:, 128:256]^T; u = relu(. + b4), logit = w5 . u + b5
+        if (pt == 0) {
             tc_after_sync();
 #pragma unroll
             for (int ks = 0; ks < H / 16; ++ks)
                 tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128), smem_desc(sw + WC_W4 * 2 + ks * 256, 128, 32 * 128),
                        ks > 0 ? 1u : 0u);
-            tc_commit(&sm.mbar[wg]);
+#pragma unroll
+            for (int ks = 0; ks < H / 16; ++ks)
+                tc_mma_ta(tmem, tmem + H + H / 2 + ks * 8, smem_desc(sw + WC_W4 * 2 + (H / 16 + ks) * 256, 128, 32 * 128),
+                          kIdesc, 1u);
+            tc_commit(&sm.mbar[p]);
         }
-        if (group_wait(sm, wg, phase, a)) tc_pool_inplace(P.act, P.m, t.ns, ltid);
+        if (group_wait(sm, p, phase, a))
+            P.logit_part[ch][row] =
+                tc_epilogue_head(td, sm.bias[3], sm.w5, ws ? ws + WS_X + 3 * WS_H + row * H : nullptr, c0);
         fence_async_smem();
         tc_before_sync();
         sync();
         if (*abort_flag) break;
-
-        // head, second half: + g . W4[:, 128:256]^T; u = relu(. + b4), logit = w5 . u + b5
-        if (ltid == 0) {
-            tc_after_sync();
-#pragma unroll
-            for (int ks = 0; ks < H / 16; ++ks)
-                tc_mma(tmem, smem_desc(sact + ks * 256, 128, 16 * 128),
-                       smem_desc(sw + WC_W4 * 2 + (H / 16 + ks) * 256, 128, 32 * 128), 1u);
-            tc_commit(&sm.mbar[wg]);
-        }
-        float logit = 0.0f;
-        if (group_wait(sm, wg, phase, a))
-            logit = tc_epilogue_head(taddr, sm.bias[3], sm.w5, ws ? ws + WS_X + 3 * WS_H + row * H : nullptr) + sm.b5;
-        P.logit[row] = logit;
-        tc_before_sync();
-        sync();
-        if (*abort_flag) break;
-
-        // softmax over each race's rows; training: d loss / d logit and the loss
-        if (ltid < t.ns) {
-            const int r0 = P.m.state_row0[ltid], r1 = P.m.state_row0[ltid + 1];
-            const int base = a.b.race_off[P.m.state_race[ltid]];
-            float mx = -INFINITY;
-            for (int q = r0; q < r1; ++q) mx = fmaxf(mx, P.logit[q]);
-            float sum = 0.0f;
-            for (int q = r0; q < r1; ++q) sum += expf(P.logit[q] - mx);
-            const float lsum = logf(sum);
-            float tsum = 0.0f, lossv = 0.0f;
-            if (a.train)
-                for (int q = r0; q < r1; ++q) tsum += a.target[base + (q - r0)];
-            for (int q = r0; q < r1; ++q) {
-                const float lq = P.logit[q] - mx - lsum;  // log q
-                const float qv = expf(lq);
-                if (a.probs) a.probs[base + (q - r0)] = qv;
-                if (a.train) {
-                    const float tv = a.target[base + (q - r0)];
-                    a.ws_dlogit[size_t(ti) * TILE + q] = (qv * tsum - tv) * a.inv_races;
-                    lossv -= tv * lq;
-                }
-            }
-            if (a.train && a.loss_acc) atomicAdd(a.loss_acc, lossv * a.inv_races);
-        }
-        if (a.train && ltid >= t.nrows) a.ws_dlogit[size_t(ti) * TILE + ltid] = 0.0f;
-        sync();
+        if (ch == 0) a.logits[size_t(ti) * TILE + row] = P.logit_part[0][row] + P.logit_part[1][row] + sm.b5;
     }
+    // a copy still in flight after an abort: wait for it before the block's memory goes
+    if (pt == 0 && pending >= 0) mbar_wait(&P.mbar_in[pending], pending_parity, a.wait_ns);
+    if (tid == 0 && !weights_ready) mbar_wait(&sm.mbar_w, 0, a.wait_ns);
     // every product this block issued has been waited for (or its wait gave up)
     tc_before_sync();
     __syncthreads();
     if (warp == 0) {
         tc_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(2 * H) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(4 * H) : "memory");
+    }
+}
+
+// softmax over each race's logits (one warp per tile, one lane per race); training: the loss
+// and d loss / d logit per tile row (zero on padding rows)
+__global__ void sg_softmax(SgArgs a, int n_tiles)
+{
+    const int ti = int((blockIdx.x * size_t(blockDim.x) + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (ti >= n_tiles) return;
+    const TileMeta &mt = a.meta[ti];
+    const int ns = mt.ns;
+    const float *lg = a.logits + size_t(ti) * TILE;
+    float lossv = 0.0f;
+    for (int st = lane; st < ns; st += 32) {
+        const int r0 = mt.state_row0[st], r1 = mt.state_row0[st + 1];
+        const int base = a.b.race_off[mt.state_race[st]];
+        float mx = -INFINITY;
+        for (int q = r0; q < r1; ++q) mx = fmaxf(mx, lg[q]);
+        float sum = 0.0f;
+        for (int q = r0; q < r1; ++q) sum += expf(lg[q] - mx);
+        const float lsum = logf(sum);
+        float tsum = 0.0f;
+        if (a.train)
+            for (int q = r0; q < r1; ++q) tsum += a.target[base + (q - r0)];
+        for (int q = r0; q < r1; ++q) {
+            const float lq = lg[q] - mx - lsum;  // log q
+            const float qv = expf(lq);
+            if (a.probs) a.probs[base + (q - r0)] = qv;
+            if (a.train) {
+                const float tv = a.target[base + (q - r0)];
+                a.ws_dlogit[size_t(ti) * TILE + q] = (qv * tsum - tv) * a.inv_races;
+                lossv -= tv * lq;
+            }
+        }
+    }
+    if (a.train) {
+        for (int q = mt.nrows + lane; q < TILE; q += 32) a.ws_dlogit[size_t(ti) * TILE + q] = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lossv += __shfl_xor_sync(0xffffffffu, lossv, o);
+        if (lane == 0 && a.loss_acc) atomicAdd(a.loss_acc, lossv * a.inv_races);
     }
 }
 
@@ -793,7 +950,7 @@ __device__ __forceinline__ void relu_grad_store(float (&acc)[16][4], const bf16 
 
 __global__ void __launch_bounds__(NTHREADS, 1) sg_backward(SgArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     BwdSmem &sm = *reinterpret_cast<BwdSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = warp * 16;
@@ -1001,6 +1158,13 @@ struct bbe_surrogate {
     bf16 *wb = nullptr;                                                // bfloat16 copy
     bf16 *wc = nullptr;                                                // canonical W1..W4 image
     int *d_status = nullptr;                                           // bounded-wait status word
+    // forward scratch: per-tile features, race layout records and logits
+    unsigned char *d_xbuf = nullptr;
+    size_t xbuf_cap = 0;
+    TileMeta *d_meta = nullptr;
+    size_t meta_cap = 0;
+    float *d_logits = nullptr;
+    size_t logits_cap = 0;
     int64_t step = 0;
     // training plan state
     uint64_t epoch = 0;
@@ -1041,19 +1205,6 @@ bbe_status ensure_attrs()
     SG_TRY(cudaFuncSetAttribute(sg_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
     SG_TRY(cudaFuncSetAttribute(sg_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bwd_smem())));
     done = true;
-    return BBE_OK;
-}
-
-// persistent forward over n_tiles tiles: two tile pipelines per block, at most one block per SM
-bbe_status launch_forward(const SgArgs &a, int64_t n_tiles, cudaStream_t st)
-{
-    if (n_tiles <= 0) return BBE_OK;
-    int dev = 0, sms = 0;
-    SG_TRY(cudaGetDevice(&dev));
-    SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n_tiles + 1) / 2, sms));
-    sg_forward_tc<<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
-    SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
 
@@ -1115,6 +1266,31 @@ SgArgs base_args(const bbe_surrogate *s, const bbe_batch *b)
     return a;
 }
 
+// forward over n_tiles tiles of a.tiles/a.order: features (one block per tile), the
+// persistent tensor-core kernel (two tile pipelines per block, at most one block per SM), softmax
+bbe_status launch_forward(bbe_surrogate *s, SgArgs a, int64_t n_tiles, cudaStream_t st)
+{
+    if (n_tiles <= 0) return BBE_OK;
+    bbe_status e;
+    if ((e = ensure_buf(s->d_xbuf, s->xbuf_cap, size_t(n_tiles) * TILE * KIN * sizeof(bf16)))) return e;
+    if ((e = ensure_buf(s->d_meta, s->meta_cap, size_t(n_tiles)))) return e;
+    if ((e = ensure_buf(s->d_logits, s->logits_cap, size_t(n_tiles) * TILE))) return e;
+    a.xbuf = s->d_xbuf;
+    a.meta = s->d_meta;
+    a.logits = s->d_logits;
+    int dev = 0, sms = 0;
+    SG_TRY(cudaGetDevice(&dev));
+    SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n_tiles + 1) / 2, sms));
+    sg_prep<<<unsigned(n_tiles), TILE, 0, st>>>(a);
+    SG_TRY(cudaGetLastError());
+    sg_forward_tc<<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
+    SG_TRY(cudaGetLastError());
+    sg_softmax<<<unsigned((n_tiles + 7) / 8), 256, 0, st>>>(a, int(n_tiles));
+    SG_TRY(cudaGetLastError());
+    return BBE_OK;
+}
+
 // upload order + tiles (synchronous on the stream: the host vectors are temporaries)
 bbe_status upload_plan(bbe_surrogate *s, const std::vector<int32_t> &order, const std::vector<SgTile> &tiles,
                        cudaStream_t st)
@@ -1146,7 +1322,7 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.ws_dlogit = s->ws_dlogit;
     a.train = 1;
     SG_TRY(cudaMemsetAsync(s->grad, 0, N_PARAMS * sizeof(float), st));
-    if ((e = launch_forward(a, nt, st))) return e;
+    if ((e = launch_forward(s, a, nt, st))) return e;
     sg_backward<<<unsigned(nt), NTHREADS, bwd_smem(), st>>>(a);
     SG_TRY(cudaGetLastError());
     return BBE_OK;
@@ -1259,7 +1435,7 @@ bbe_status upload_params(bbe_surrogate *s, const float *host)
 void free_surrogate(bbe_surrogate *s)
 {
     for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->wc,
-                    (void *)s->d_status, (void *)s->d_tiles,
+                    (void *)s->d_status, (void *)s->d_xbuf, (void *)s->d_meta, (void *)s->d_logits, (void *)s->d_tiles,
                     (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
                     (void *)s->d_iorder})
         if (p) cudaFree(p);
@@ -1278,7 +1454,7 @@ bbe_status forward_all(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     SgArgs a = base_args(s, b);
     a.probs = probs;
     a.train = 0;
-    return launch_forward(a, int64_t(tiles.size()), st);
+    return launch_forward(s, a, int64_t(tiles.size()), st);
 }
 
 }  // namespace
@@ -1467,7 +1643,7 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         a.order = s->d_iorder;
         a.probs = probs;
         a.train = 0;
-        if ((e = launch_forward(a, s->iplan_tiles, st))) return e;
+        if ((e = launch_forward(s, a, s->iplan_tiles, st))) return e;
     }
     const std::vector<int32_t> &mc = s->iplan_mc;
     const std::vector<uint8_t> &flag = s->iplan_flag;
