@@ -16,6 +16,7 @@ range of race ids (weak scaling, no data-path collective); rank 0 prints one JSO
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -254,6 +255,12 @@ def run_reference(args, rank, world):
 # algorithmic FLOPs per competitor row of the surrogate network (one forward pass):
 # 2 x (5*128 + 128*128 + 128*128 + 256*128 + 128)
 SURROGATE_FWD_FLOPS_PER_ROW = 2 * (5 * 128 + 2 * 128 * 128 + 256 * 128 + 128)
+# Monte Carlo budget of a query: about what plain Monte Carlo needs for a 0.01 max-abs error
+# over 1e4 states (4.5 sigma of a binomial proportion at p = 1/2)
+QUERY_ROLLOUTS = 50000
+# confidence gate of the surrogate: races whose runner-up network probability exceeds this go to
+# Monte Carlo (threshold chosen on held-out states of seeds 300 and 301)
+GATE_RUNNER_UP = 1e-3
 
 
 def run_surrogate(mode: str, dev, stream) -> dict:
@@ -311,42 +318,81 @@ def run_surrogate(mode: str, dev, stream) -> dict:
                    train_states_per_s=nsteps * B / out["train_s"],
                    train_tflops=3 * SURROGATE_FWD_FLOPS_PER_ROW * rows / out["train_s"] / 1e12)
         tb.close()
-        # held-out error against 1e5-rollout Monte Carlo
-        ho = W.uneven_batch(seed=300, n_races=10000, rollouts=100000)
+        # Held-out error against 1e5-rollout Monte Carlo on states the gate threshold was not
+        # chosen on.  Queries carry the deployment budget (5e4 rollouts, what plain Monte Carlo
+        # needs for a 0.01 max-abs error) and another Philox seed than the reference.
+        ho = W.uneven_batch(seed=302, n_races=10000, rollouts=100000)
         hb = bbe.Batch(ho, stream=stream)
         hc = torch.empty(ho.n_total, dtype=torch.int32, device=dev)
         hp = torch.empty(ho.n_total, dtype=torch.float32, device=dev)
         hs = torch.empty(ho.n_races, dtype=torch.int64, device=dev)
         timed(lambda: (hb.rollout(hc, hs, stream=stream), hb.win_probs(hc, hp, stream=stream)))
-        q = torch.empty_like(hp)
-        used = torch.empty(ho.n_races, dtype=torch.uint8, device=dev)
-        bbe.bbe_surrogate_infer(s, hb.handle, q, used, stream=stream)
-        stream.synchronize()
-        P, Q = hp.cpu().numpy().astype(np.float64), q.cpu().numpy().astype(np.float64)
-        err = np.abs(P - Q)
-        kl = np.where(P > 0, P * (np.log(np.maximum(P, 1e-30)) - np.log(np.maximum(Q, 1e-30))), 0.0)
+        P = hp.cpu().numpy().astype(np.float64)
         mc_cs_per_rollout = float((ho.sizes() * hs.cpu().numpy()).sum()) / float(ho.rollouts.sum())
-        out["heldout"] = {"states": ho.n_races, "reference_rollouts": 100000, "max_abs": float(err.max()),
-                          "mean_abs": float(err.mean()), "p99_abs": float(np.quantile(err, 0.99)),
-                          "kl_mean": float(np.add.reduceat(kl, ho.race_off[:-1]).mean()),
-                          "kl_max": float(np.add.reduceat(kl, ho.race_off[:-1]).max()),
-                          "used_mc": int(used.cpu().numpy().sum())}
         hb.close()
-        # C4: 1e6 queries drawn as in the uneven workload
-        qrb = W.uneven_batch(seed=400, n_races=1_000_000, rollouts=10000)
+        hq = dataclasses.replace(ho, rollouts=np.full(ho.n_races, QUERY_ROLLOUTS, np.int64), seed=303)
+        qb = bbe.Batch(hq, stream=stream)
+        q = torch.empty(ho.n_total, dtype=torch.float32, device=dev)
+        used = torch.empty(ho.n_races, dtype=torch.uint8, device=dev)
+
+        def errors(Q):
+            err = np.abs(P - Q)
+            kl = np.where(P > 0, P * (np.log(np.maximum(P, 1e-30)) - np.log(np.maximum(Q, 1e-30))), 0.0)
+            klr = np.add.reduceat(kl, ho.race_off[:-1])
+            return {"max_abs": float(err.max()), "mean_abs": float(err.mean()), "p99_abs": float(np.quantile(err, 0.99)),
+                    "kl_mean": float(klr.mean()), "kl_max": float(klr.max())}
+
+        held = {"states": ho.n_races, "reference_rollouts": 100000, "query_rollouts": QUERY_ROLLOUTS}
+        bbe.bbe_surrogate_set_gate(s, 1.0)
+        bbe.bbe_surrogate_infer(s, qb.handle, q, used, stream=stream)
+        stream.synchronize()
+        held["network"] = errors(q.cpu().numpy().astype(np.float64))
+        held["network"]["used_mc"] = int(used.cpu().numpy().sum())
+        bbe.bbe_surrogate_set_gate(s, GATE_RUNNER_UP)
+        bbe.bbe_surrogate_infer(s, qb.handle, q, used, stream=stream)
+        stream.synchronize()
+        held["gated"] = errors(q.cpu().numpy().astype(np.float64))
+        u = used.cpu().numpy()
+        held["gated"].update(runner_up_max=GATE_RUNNER_UP, gated=int((u == 2).sum()), out_of_range=int((u == 1).sum()))
+        mcq_c = torch.empty(ho.n_total, dtype=torch.int32, device=dev)
+        mcq_p = torch.empty(ho.n_total, dtype=torch.float32, device=dev)
+        qb.rollout(mcq_c, stream=stream)
+        qb.win_probs(mcq_c, mcq_p, stream=stream)
+        stream.synchronize()
+        held["mc_at_query_rollouts"] = errors(mcq_p.cpu().numpy().astype(np.float64))
+        out["heldout"] = held
+        qb.close()
+        # C4: 1e6 queries drawn as in the uneven workload, network alone and gated
+        qrb = W.uneven_batch(seed=400, n_races=1_000_000 if full else 100_000, rollouts=QUERY_ROLLOUTS)
         t0 = time.perf_counter()
         qb = bbe.Batch(qrb, stream=stream)
         out["query_stage_s"] = time.perf_counter() - t0
         qp = torch.empty(qrb.n_total, dtype=torch.float32, device=dev)
         qu = torch.empty(qrb.n_races, dtype=torch.uint8, device=dev)
-        bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)  # plans once per batch
-        ts = [timed(lambda: bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)) for _ in range(3)]
-        t_inf = min(ts)
         qrows = float(qrb.n_total)
+        bbe.bbe_surrogate_set_gate(s, 1.0)
+        bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)  # plans once per batch
+        t_inf = min(timed(lambda: bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream)) for _ in range(3))
         out["infer"] = {"states": qrb.n_races, "s": t_inf, "win_prob_vectors_per_s": qrb.n_races / t_inf,
                         "used_mc": int(qu.cpu().numpy().sum()),
                         "tflops": SURROGATE_FWD_FLOPS_PER_ROW * qrows / t_inf / 1e12}
+        bbe.bbe_surrogate_set_gate(s, GATE_RUNNER_UP)
+        t_g = timed(lambda: bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream))
+        u = qu.cpu().numpy()
+        out["infer_gated"] = {"states": qrb.n_races, "s": t_g, "win_prob_vectors_per_s": qrb.n_races / t_g,
+                              "runner_up_max": GATE_RUNNER_UP, "gated": int((u == 2).sum()),
+                              "out_of_range": int((u == 1).sum()), "fallback_rollouts": QUERY_ROLLOUTS}
         qb.close()
+        # plain Monte Carlo at the query budget on a 20,000-query sample of the same stream
+        ms = qrb.slice(0, 20000)
+        with bbe.Batch(ms, stream=stream) as mb:
+            mcnt = torch.empty(ms.n_total, dtype=torch.int32, device=dev)
+            mstp = torch.empty(ms.n_races, dtype=torch.int64, device=dev)
+            mpr = torch.empty(ms.n_total, dtype=torch.float32, device=dev)
+            t_ms = timed(lambda: (mb.rollout(mcnt, mstp, stream=stream), mb.win_probs(mcnt, mpr, stream=stream)))
+        out["mc_at_query_rollouts"] = {"states": ms.n_races, "s": t_ms, "win_prob_vectors_per_s": ms.n_races / t_ms,
+                                       "rollouts": QUERY_ROLLOUTS}
+        out["gain_gated_vs_mc_at_query_rollouts"] = out["infer_gated"]["win_prob_vectors_per_s"] / (ms.n_races / t_ms)
     finally:
         bbe.bbe_surrogate_destroy(s)
     # plain Monte Carlo on the uneven workload (10,000 snapshots, budgets 1e3..1e5)
@@ -362,7 +408,7 @@ def run_surrogate(mode: str, dev, stream) -> dict:
     mc_rate = u.n_races / t_mc
     # Monte Carlo at the surrogate's mean-abs error: E|N(0, p(1-p)/R)| = sqrt(2 p (1-p) / (pi R))
     sq = float(np.mean(np.sqrt(P * (1 - P))))
-    r_match = 2.0 / np.pi * (sq / max(out["heldout"]["mean_abs"], 1e-12)) ** 2
+    r_match = 2.0 / np.pi * (sq / max(out["heldout"]["network"]["mean_abs"], 1e-12)) ** 2
     cs_per_s = mc_cs / t_mc
     mc_rate_matched = cs_per_s / (max(r_match, 1.0) * mc_cs_per_rollout)
     out["mc"] = {"workload": "uneven 10,000 snapshots, rollouts floor(10^U(3,5))", "win_prob_vectors_per_s": mc_rate,

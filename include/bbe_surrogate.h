@@ -81,15 +81,24 @@ BBE_API bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *stat
                                          void *cuda_stream);
 
 /* bbe_surrogate_infer -- win probabilities for every race of `states`: races inside the
- * training ranges get the network's output; every other race is simulated with plain Monte
- * Carlo (bbe_rollout_batch with the race's own rollout budget and stream id, so its
- * probabilities are exactly those of the Monte Carlo path).
+ * training ranges get the network's output unless the confidence gate (bbe_surrogate_set_gate)
+ * rejects it; every other race is simulated with plain Monte Carlo (bbe_rollout_batch with
+ * the race's own rollout budget and stream id, so its probabilities are exactly those of the
+ * Monte Carlo path).
  *   probs   device float[sum n], overwritten.
- *   used_mc device uint8[n_races] or NULL: 1 where the race fell back to Monte Carlo.
- * Synchronises cuda_stream when some race falls back.  Errors: BBE_ERR_ARG,
- * BBE_ERR_CUDA, BBE_ERR_RANGE (no training ranges recorded yet). */
+ *   used_mc device uint8[n_races] or NULL: 0 network, 1 Monte Carlo (outside the training
+ *           ranges), 2 Monte Carlo (rejected by the confidence gate).
+ * Synchronises cuda_stream when the gate is enabled or some race falls back.  Errors:
+ * BBE_ERR_ARG, BBE_ERR_CUDA, BBE_ERR_RANGE (no training ranges recorded yet). */
 BBE_API bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *states, float *probs, uint8_t *used_mc,
                                        void *cuda_stream);
+
+/* bbe_surrogate_set_gate -- confidence gate of bbe_surrogate_infer: a race whose network output
+ * has a second-largest probability above runner_up_max (a contest the network does not call
+ * with near-certainty) is simulated with plain Monte Carlo instead.  runner_up_max in [0, 1];
+ * values of 0.5 or more disable the gate (the default is 1).  Not stored in checkpoints.
+ * Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_surrogate_set_gate(bbe_surrogate *s, float runner_up_max);
 
 /* bbe_surrogate_status -- synchronise cuda_stream and report whether a kernel launched on
  * this handle gave up a bounded device wait since the last call (the flag is then cleared;

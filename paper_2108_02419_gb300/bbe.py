@@ -270,6 +270,7 @@ def _sg():
             "bbe_surrogate_forward": [vp, vp, vp, vp],
             "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
             "bbe_surrogate_status": [vp, vp],
+            "bbe_surrogate_set_gate": [vp, C.c_float],
             "bbe_surrogate_save": [vp, C.c_char_p],
             "bbe_surrogate_load": [C.POINTER(vp), C.c_char_p],
         }
@@ -328,6 +329,11 @@ def bbe_surrogate_forward(s: int, batch: int, probs, stream=None) -> None:
 def bbe_surrogate_infer(s: int, batch: int, probs, used_mc=None, stream=None) -> None:
     _check(_sg().bbe_surrogate_infer(s, batch, _ptr(probs, np.float32), _ptr(used_mc, np.uint8), _stream(stream)),
            "bbe_surrogate_infer")
+
+
+def bbe_surrogate_set_gate(s: int, runner_up_max: float) -> None:
+    """Send races whose second-largest network probability exceeds runner_up_max to Monte Carlo."""
+    _check(_sg().bbe_surrogate_set_gate(s, float(runner_up_max)), "bbe_surrogate_set_gate")
 
 
 def bbe_surrogate_status(s: int, stream=None) -> None:

@@ -1131,6 +1131,27 @@ __global__ void scatter_probs(const float *src, const int32_t *dst_index, float 
     if (i < n) dst[dst_index[i]] = src[i];
 }
 
+// confidence gate: flag[i] = 1 when the second-largest output probability of race races[i]
+// exceeds runner_up_max
+__global__ void sg_gate(const int32_t *race_off, const int32_t *races, int n, const float *probs, float runner_up_max,
+                        uint8_t *flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = races[i];
+    float m1 = -1.0f, m2 = -1.0f;
+    for (int c = race_off[r]; c < race_off[r + 1]; ++c) {
+        const float p = probs[c];
+        if (p > m1) {
+            m2 = m1;
+            m1 = p;
+        } else if (p > m2) {
+            m2 = p;
+        }
+    }
+    flag[i] = m2 > runner_up_max ? 1 : 0;
+}
+
 #define SG_TRY(expr)                                                                        \
     do {                                                                                    \
         cudaError_t e_ = (expr);                                                            \
@@ -1184,8 +1205,13 @@ struct bbe_surrogate {
     uint64_t ranges_version = 1;
     // inference plan cached per (batch, ranges): network races packed into tiles, fallback races
     uint64_t iplan_serial = 0, iplan_version = 0;
-    std::vector<int32_t> iplan_mc;
+    std::vector<int32_t> iplan_net;  // races the network answers (tile order)
+    std::vector<int32_t> iplan_mc;   // races outside the training ranges
     std::vector<uint8_t> iplan_flag;
+    // confidence gate: runner-up probability above which a race goes to Monte Carlo
+    float gate = 1.0f;
+    uint8_t *d_gate = nullptr;
+    size_t gate_cap = 0;
     int64_t iplan_tiles = 0;
     SgTile *d_itiles = nullptr;
     size_t itiles_cap = 0;
@@ -1437,7 +1463,7 @@ void free_surrogate(bbe_surrogate *s)
     for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->wc,
                     (void *)s->d_status, (void *)s->d_xbuf, (void *)s->d_meta, (void *)s->d_logits, (void *)s->d_tiles,
                     (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
-                    (void *)s->d_iorder})
+                    (void *)s->d_iorder, (void *)s->d_gate})
         if (p) cudaFree(p);
 }
 
@@ -1634,6 +1660,7 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         SG_TRY(cudaMemcpyAsync(s->d_itiles, tiles.data(), tiles.size() * sizeof(SgTile), cudaMemcpyHostToDevice, st));
         SG_TRY(cudaStreamSynchronize(st));
         s->iplan_tiles = int64_t(tiles.size());
+        s->iplan_net = std::move(net);
         s->iplan_serial = b->serial;
         s->iplan_version = s->ranges_version;
     }
@@ -1645,10 +1672,26 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         a.train = 0;
         if ((e = launch_forward(s, a, s->iplan_tiles, st))) return e;
     }
-    const std::vector<int32_t> &mc = s->iplan_mc;
-    const std::vector<uint8_t> &flag = s->iplan_flag;
+    std::vector<int32_t> mc = s->iplan_mc;
+    std::vector<uint8_t> flag = s->iplan_flag;
+    const int64_t n_net = int64_t(s->iplan_net.size());
+    if (s->gate < 0.5f && n_net > 0) {
+        // races the network does not call with near-certainty go to Monte Carlo as well
+        if ((e = ensure_buf(s->d_gate, s->gate_cap, size_t(n_net)))) return e;
+        sg_gate<<<unsigned((n_net + 255) / 256), 256, 0, st>>>(b->dev.race_off, s->d_iorder, int(n_net), probs, s->gate,
+                                                              s->d_gate);
+        SG_TRY(cudaGetLastError());
+        std::vector<uint8_t> g(size_t(n_net), 0);
+        SG_TRY(cudaMemcpyAsync(g.data(), s->d_gate, size_t(n_net), cudaMemcpyDeviceToHost, st));
+        SG_TRY(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < n_net; ++i)
+            if (g[size_t(i)]) {
+                mc.push_back(s->iplan_net[size_t(i)]);
+                flag[size_t(s->iplan_net[size_t(i)])] = 2;
+            }
+    }
     if (!mc.empty()) {
-        // plain Monte Carlo for the out-of-range races, with their own stream ids
+        // plain Monte Carlo for these races, with their own stream ids
         std::vector<int32_t> off(1, 0), ids;
         std::vector<float> L, d0, mu, sg, rho, P, th, pv;
         std::vector<int64_t> R;
@@ -1710,6 +1753,16 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
         SG_TRY(cudaMemcpyAsync(used_mc, flag.data(), flag.size(), cudaMemcpyHostToDevice, st));
         SG_TRY(cudaStreamSynchronize(st));
     }
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_set_gate(bbe_surrogate *s, float runner_up_max)
+{
+    if (!s || !(runner_up_max >= 0.0f && runner_up_max <= 1.0f)) {
+        bbe::set_error("bbe_surrogate_set_gate: surrogate is NULL or runner_up_max outside [0, 1]");
+        return BBE_ERR_ARG;
+    }
+    s->gate = runner_up_max;
     return BBE_OK;
 }
 

@@ -181,6 +181,40 @@ def test_infer_falls_back_to_exact_monte_carlo(bbe, tmp_path):
         bbe.bbe_surrogate_destroy(s)
 
 
+def test_confidence_gate_sends_uncertain_races_to_monte_carlo(bbe):
+    rb = W.uneven_batch(seed=54, n_races=600, n_lo=2, n_hi=10, rollouts=800)
+    s = bbe.bbe_surrogate_create(9)
+    try:
+        with bbe.Batch(rb) as b:
+            c, _ = b.rollout()
+            mc, _ = b.win_probs(c)
+            bbe.bbe_surrogate_train(s, b.handle, mc, batch_states=128, steps=30)
+            net = torch.empty_like(mc)
+            bbe.bbe_surrogate_forward(s, b.handle, net)  # the training states are all in range
+            out = torch.empty_like(mc)
+            used = torch.empty(rb.n_races, dtype=torch.uint8, device="cuda")
+            thr = 1e-3
+            bbe.bbe_surrogate_set_gate(s, thr)
+            bbe.bbe_surrogate_infer(s, b.handle, out, used)
+            gated = used.cpu().numpy()
+            bbe.bbe_surrogate_set_gate(s, 1.0)
+            bbe.bbe_surrogate_infer(s, b.handle, out2 := torch.empty_like(mc), used)
+            ungated = used.cpu().numpy()
+            torch.cuda.synchronize()
+            net, out, out2, mc = (t.cpu().numpy() for t in (net, out, out2, mc))
+        with pytest.raises(bbe.BbeError):
+            bbe.bbe_surrogate_set_gate(s, 1.5)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    assert np.all(ungated == 0) and np.array_equal(out2, net)
+    assert set(np.unique(gated)) <= {0, 2} and 0 < (gated == 2).sum() < rb.n_races
+    for r in range(rb.n_races):
+        a, e = rb.race_off[r], rb.race_off[r + 1]
+        runner_up = np.sort(net[a:e])[-2]
+        assert (gated[r] == 2) == (runner_up > np.float32(thr)), r
+        assert np.array_equal(out[a:e], mc[a:e] if gated[r] else net[a:e]), r
+
+
 def test_infer_without_training_ranges_is_refused(bbe):
     rb = W.uneven_batch(seed=48, n_races=4, rollouts=10)
     s = bbe.bbe_surrogate_create(7)
