@@ -60,7 +60,47 @@ def parse():
     ap.add_argument("--races", type=int, default=0, help="use only the first N races (profiling of a small case)")
     ap.add_argument("--surrogate", default="full", choices=["full", "small", "off"],
                     help="learned-surrogate leg: full = 2e6 training states x 1e4 rollouts, 20 epochs")
+    ap.add_argument("--surrogate-kernels", default="", choices=["", "forward", "train"],
+                    help="profiling aid: run only the surrogate's inference (3 calls) or 4 training steps of "
+                         "4096 races on the first --races uneven states (default 100000), print timings and exit")
     return ap.parse_args()
+
+
+def run_surrogate_kernels(mode: str, races: int) -> dict:
+    """The surrogate's kernels alone on a small uneven workload (for profiler captures)."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    n = races or 100_000
+    rb = W.uneven_batch(seed=400, n_races=n, rollouts=1000)
+    s = bbe.bbe_surrogate_create(1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"surrogate_kernels": mode, "races": n, "rows": rb.n_total}
+    try:
+        with bbe.Batch(rb) as b:
+            if mode == "forward":
+                p = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+                ms = []
+                for _ in range(3):
+                    ev[0].record()
+                    bbe.bbe_surrogate_forward(s, b.handle, p)
+                    ev[1].record()
+                    ev[1].synchronize()
+                    ms.append(ev[0].elapsed_time(ev[1]))
+                out["forward_ms"] = ms
+            else:
+                c, _ = b.rollout()
+                p, _ = b.win_probs(c)
+                ev[0].record()
+                bbe.bbe_surrogate_train(s, b.handle, p, batch_states=4096, steps=4)
+                ev[1].record()
+                ev[1].synchronize()
+                out["train_ms_per_step"] = ev[0].elapsed_time(ev[1]) / 4
+            bbe.bbe_surrogate_status(s)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    return out
 
 
 def make_workload(name: str, rank: int = 0, races: int = 0) -> W.RaceBatch:
@@ -556,6 +596,9 @@ def run_gpu(args, rank, world, dist):
 
 def main():
     args = parse()
+    if args.surrogate_kernels:
+        print(json.dumps(run_surrogate_kernels(args.surrogate_kernels, args.races)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
