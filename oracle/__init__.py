@@ -76,6 +76,10 @@ def lib():
             L.bbe_oracle_rollout.restype = C.c_int
             L.bbe_oracle_race_counts.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, i64, vp, vp]
             L.bbe_oracle_race_counts.restype = C.c_int
+            L.bbe_oracle_rollout_order.argtypes = [C.POINTER(_Race), u64, u32, u32, C.c_int, i64, vp, vp]
+            L.bbe_oracle_rollout_order.restype = C.c_int
+            L.bbe_oracle_race_places.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
+            L.bbe_oracle_race_places.restype = C.c_int
             L.bbe_oracle_win_probs.argtypes = [C.c_int, vp, i64, vp, vp]
             L.bbe_oracle_log_batch.argtypes = [vp, vp, i64]
             L.bbe_oracle_sincos2pi_batch.argtypes = [vp, vp, vp, i64]
@@ -154,6 +158,59 @@ def race_counts(race: dict, seed: int, r: int | None = None, R: int | None = Non
     steps = np.zeros(1, np.int64)
     st = lib().bbe_oracle_race_counts(C.byref(a.s), seed, r, k_begin, R, max_steps, _ptr(counts), _ptr(steps))
     return counts, int(steps[0]), int(st)
+
+
+def rollout_order(race: dict, seed: int, r: int, k: int, places: int, max_steps: int = MAX_STEPS_DEFAULT):
+    """One dry-run to the places-th finisher: (order int32 [places], steps, status)."""
+    a = _RaceArgs(race)
+    steps = np.zeros(1, np.int64)
+    order = np.full(race["n"], -1, np.int32)
+    st = lib().bbe_oracle_rollout_order(C.byref(a.s), seed, r, k, places, max_steps, _ptr(steps), _ptr(order))
+    return order[:places], int(steps[0]), int(st)
+
+
+def race_places(race: dict, seed: int, places: int, r: int | None = None, R: int | None = None, k_begin: int = 0,
+                max_steps: int = MAX_STEPS_DEFAULT):
+    """Place counts of one race: (counts int32 [n, places], steps_total, status)."""
+    a = _RaceArgs(race)
+    r = race["race_id"] if r is None else r
+    R = race["R"] if R is None else R
+    counts = np.zeros((race["n"], places), np.int32)
+    steps = np.zeros(1, np.int64)
+    st = lib().bbe_oracle_race_places(C.byref(a.s), seed, r, k_begin, R, places, max_steps, _ptr(counts), _ptr(steps))
+    return counts, int(steps[0]), int(st)
+
+
+def batch_places(batch, places: int, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,
+                 rollout_chunk: int = 2500):
+    """Place counts for the given races of a RaceBatch: (counts int32 [sum n, places] in the
+    order given, steps int64 [len(races)], status); rollout chunks run on a thread pool."""
+    races = list(range(batch.n_races)) if races is None else [int(x) for x in races]
+    threads = threads or os.cpu_count() or 1
+    tasks = []
+    for i, r in enumerate(races):
+        R = int(batch.rollouts[r])
+        for k0 in range(0, R, rollout_chunk):
+            tasks.append((i, r, k0, min(rollout_chunk, R - k0)))
+
+    def one(task):
+        i, r, k0, cnt = task
+        return race_places(batch.race(r), batch.seed, places, R=cnt, k_begin=k0, max_steps=max_steps)
+
+    if threads <= 1 or len(tasks) <= 1:
+        res = [one(t) for t in tasks]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(one, tasks))
+    per_race = [np.zeros((int(batch.race_off[r + 1] - batch.race_off[r]), places), np.int64) for r in races]
+    steps = np.zeros(len(races), np.int64)
+    status = 0
+    for (i, r, k0, cnt), (c, st, s) in zip(tasks, res):
+        per_race[i] += c
+        steps[i] += st
+        status = min(status, s)
+    counts = np.concatenate(per_race).astype(np.int32) if per_race else np.zeros((0, places), np.int32)
+    return counts, steps, status
 
 
 def batch_counts(batch, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,

@@ -301,6 +301,93 @@ int bbe_oracle_race_counts(const bbe_oracle_race *race, uint64_t seed, uint32_t 
     return status;
 }
 
+/* One rollout k of race r run until `places` competitors have crossed the line.  Section 3
+ * runs a race until its last competitor crosses and lets in-play betting stop earlier, for
+ * instance when the third-placed competitor crosses; place and each-way markets (Section 2)
+ * need the places.  Readings: every competitor keeps moving under Eq. 1 until the rollout
+ * ends, finished ones included (the rule names no exception); the competitors that cross in
+ * the same step are placed in order of their crossing time within the step,
+ * tau = (L - d) / S, equal tau: lower index first.  order[j] receives the competitor in place
+ * j for j < places (places <= n).  Returns 0, or BBE_ORACLE_STEP_LIMIT if max_steps steps pass
+ * first.  *steps receives the number of steps taken. */
+int bbe_oracle_rollout_order(const bbe_oracle_race *race, uint64_t seed, uint32_t r, uint32_t k,
+                             int places, int64_t max_steps, int64_t *steps, int32_t *order)
+{
+    int n = race->n;
+    float *buf = (float *)malloc(sizeof(float) * (size_t)n * 5);
+    int *finished = (int *)calloc((size_t)n, sizeof(int));
+    float *kr = buf, *prev = buf + n, *d = buf + 2 * n, *S = buf + 3 * n, *dn = buf + 4 * n;
+    float invL;
+    race_constants(race, kr, prev, &invL);
+    for (int c = 0; c < n; ++c) d[c] = race->d0[c];
+    int placed = 0, status = 0;
+    int64_t t = 0;
+    for (;;) {
+        if (t == max_steps) {
+            status = BBE_ORACLE_STEP_LIMIT;
+            break;
+        }
+        race_step(race, kr, invL, d, prev, seed, r, k, (uint32_t)t, S);
+        for (int c = 0; c < n; ++c) dn[c] = d[c] + S[c];
+        /* this step's new finishers, earliest crossing first */
+        for (;;) {
+            int best = -1;
+            float best_tau = 0.0f;
+            for (int c = 0; c < n; ++c) {
+                if (finished[c] || !(dn[c] >= race->L)) continue;
+                float tau = (race->L - d[c]) / S[c];
+                if (best < 0 || tau < best_tau) {
+                    best = c;
+                    best_tau = tau;
+                }
+            }
+            if (best < 0) break;
+            finished[best] = 1;
+            if (placed < places) order[placed] = best;
+            ++placed;
+        }
+        ++t;
+        if (placed >= places) break;
+        for (int c = 0; c < n; ++c) {
+            prev[c] = S[c];
+            d[c] = dn[c];
+        }
+    }
+    *steps = t;
+    free(finished);
+    free(buf);
+    return status;
+}
+
+/* Place counts of one race: R rollouts k = k_begin .. k_begin + R - 1, each run until
+ * min(places, n) competitors have crossed; counts[c * places + j] = rollouts in which c
+ * finished in place j (j = 0: the winner).  Returns 0, or BBE_ORACLE_STEP_LIMIT if some
+ * rollout hit max_steps (that rollout then counts for nobody). */
+int bbe_oracle_race_places(const bbe_oracle_race *race, uint64_t seed, uint32_t r,
+                           int64_t k_begin, int64_t R, int places, int64_t max_steps,
+                           int32_t *counts, int64_t *steps_total)
+{
+    int n = race->n;
+    int kk = places < n ? places : n;
+    int status = 0;
+    int64_t total = 0;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int i = 0; i < n * places; ++i) counts[i] = 0;
+    for (int64_t k = k_begin; k < k_begin + R; ++k) {
+        int64_t steps = 0;
+        int st = bbe_oracle_rollout_order(race, seed, r, (uint32_t)k, kk, max_steps, &steps, order);
+        total += steps;
+        if (st != 0) {
+            status = st;
+            continue;
+        }
+        for (int j = 0; j < kk; ++j) counts[order[j] * places + j] += 1;
+    }
+    if (steps_total) *steps_total = total;
+    free(order);
+    return status;
+}
+
 /* Frequentist win probabilities and decimal odds (Section 2: decimal odds are the
  * total returned per unit stake, so odds = 1/p): p_c = count_c / R. */
 void bbe_oracle_win_probs(int n, const int32_t *counts, int64_t R, float *probs, float *odds)

@@ -76,3 +76,52 @@ def exact_win_probs(L, d0, mu, sigma, P=None, theta=None, prev0=None, max_steps=
             break
     assert not states, "race did not end within max_steps"
     return win
+
+
+def exact_place_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, max_steps=200):
+    """Exact probability that competitor c finishes in place j (j < places) of a two-point
+    race, by the same enumeration: every competitor keeps moving under Eq. 1 until `places`
+    competitors have crossed; those crossing in one step are placed by their binary32
+    crossing time tau, then by index.  Returns an [n, places] array."""
+    n = len(d0)
+    P = [1.0] * n if P is None else list(P)
+    theta = [1.0] * n if theta is None else list(theta)
+    prev = [mu[c] * P[c] for c in range(n)] if prev0 is None else list(prev0)
+    for v in list(d0) + list(mu) + list(sigma) + P + theta + prev + [L]:
+        assert float(np.float32(v)) == v and (v * 2 ** 12) == int(v * 2 ** 12), "inputs must be small dyadics"
+    places = min(places, n)
+    states = {(tuple(float(x) for x in d0), tuple(float(x) for x in prev), ()): 1.0}
+    out = np.zeros((n, places))
+    for _ in range(max_steps):
+        nxt = defaultdict(float)
+        for (d, pv, order), mass in states.items():
+            fixed = {}
+            free = []
+            for c in range(n):
+                ip = _nearest_in_front(d, c)
+                if ip is not None and not (d[ip] - d[c] > theta[c]):
+                    fixed[c] = min(pv[c], pv[ip])
+                else:
+                    free.append(c)
+            share = mass / (2 ** len(free))
+            for signs in product((-1.0, 1.0), repeat=len(free)):
+                S = [0.0] * n
+                for c, v in fixed.items():
+                    S[c] = v
+                for c, z in zip(free, signs):
+                    S[c] = P[c] * (mu[c] + sigma[c] * z)
+                S = [s if s >= S_FLOOR else S_FLOOR for s in S]
+                dn = [d[c] + S[c] for c in range(n)]
+                new = [c for c in range(n) if c not in order and dn[c] >= L]
+                taus = sorted((np.float32(np.float32(L) - np.float32(d[c])) / np.float32(S[c]), c) for c in new)
+                o2 = order + tuple(c for _, c in taus)
+                if len(o2) >= places:
+                    for j in range(places):
+                        out[o2[j], j] += share
+                else:
+                    nxt[(tuple(dn), tuple(S), o2)] += share
+        states = nxt
+        if not states:
+            break
+    assert not states, "race did not end within max_steps"
+    return out

@@ -1,6 +1,7 @@
 """The oracle's pins catch plausible mistakes: each mutant below is a copy of
 oracle/bbe_oracle.c with one deliberate error (in the oracle, on the CPU); the pin suites
-(tests/test_oracle_rng.py, tests/test_oracle_race.py) must fail against every mutant."""
+(tests/test_oracle_rng.py, tests/test_oracle_race.py, tests/test_oracle_places.py) must fail against
+every mutant."""
 import os
 import subprocess
 import sys
@@ -32,6 +33,10 @@ MUTANTS = {
                                "        race_step(race, kr, invL, d, prev, seed, r, k, (uint32_t)t, S);\n        for (int c = 0; c < race->n; ++c) if (c == 0) d[c] += S[c];"),
     "floor_dropped": ("if (S_c < BBE_ORACLE_S_FLOOR) S_c = BBE_ORACLE_S_FLOOR;", ";"),
     "counter_word_swap": ("uint32_t ctr[4] = { k, t >> 2, c, r };", "uint32_t ctr[4] = { k, t >> 2, r, c };"),
+    "places_in_index_order": ("if (best < 0 || tau < best_tau) {", "if (best < 0) {"),
+    "finished_competitors_stop": ("        if (placed >= places) break;\n        for (int c = 0; c < n; ++c) {\n",
+                                  "        if (placed >= places) break;\n        for (int c = 0; c < n; ++c) {\n            if (finished[c]) continue;\n"),
+    "places_short_of_n": ("int kk = places < n ? places : n;", "int kk = places < n ? places : n - 1;"),
 }
 
 
@@ -46,6 +51,7 @@ def test_pins_catch_mutant(tmp_path, name):
     env = dict(os.environ, BBE_ORACLE_LIB=so)
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_race.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_places.py"),
                           os.path.join(ROOT, "tests", "test_oracle_rng.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"mutant {name} passed every pin:\n{res.stdout[-2000:]}"
