@@ -138,9 +138,34 @@ BBE_API bbe_status bbe_rollout_batch(bbe_batch *batch, int32_t *win_counts, int6
 BBE_API bbe_status bbe_win_probs(const bbe_batch *batch, const int32_t *win_counts, float *probs, float *odds,
                          void *cuda_stream);
 
+/* bbe_place_counts -- finishing places of every competitor (Section 3: a race runs until its
+ * last competitor crosses the line, and in-play betting may stop earlier, for instance when the
+ * third-placed competitor crosses; place and each-way markets, Section 2, need the places).
+ * Every rollout of race r runs until K = min(places, n_r) competitors have crossed.  Readings:
+ * all competitors keep moving under Eq. 1 until the rollout ends, finished ones included (they
+ * can still block); competitors crossing in the same step are placed by their crossing time
+ * within the step, tau = (L - d) / S, then by lower index.  Same random stream as
+ * bbe_rollout_batch, so place 0 is exactly its win count.
+ *   places        1 .. BBE_MAX_COMPETITORS.
+ *   place_counts  device int32[sum n * places], overwritten: [i * places + j] = rollouts in
+ *                 which competitor i finished in place j (0 = first); zero for j >= n_r.
+ *   steps_total   nullable device int64[n_races]: steps summed over the race's rollouts.
+ * Asynchronous on cuda_stream.  A rollout that reaches max_steps first counts for nobody and
+ * sets BBE_ERR_STEP_LIMIT in the batch status.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_place_counts(bbe_batch *batch, int32_t places, int32_t *place_counts, int64_t *steps_total,
+                                    void *cuda_stream);
+
+/* bbe_place_probs -- probability of finishing in the first `top` places (a place market
+ * paying on the first `top` places; top = 1 is the win probability):
+ *   probs[i] = (sum over j < top of place_counts[i * places + j]) / R_r.
+ * place_counts as written by bbe_place_counts with the same `places`; 1 <= top <= places.
+ * Asynchronous.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_place_probs(const bbe_batch *batch, int32_t places, const int32_t *place_counts, int32_t top,
+                                   float *probs, void *cuda_stream);
+
 /* bbe_batch_status -- synchronise cuda_stream and return the batch's device status from
- * the last bbe_rollout_batch: BBE_OK, BBE_ERR_STEP_LIMIT, or BBE_ERR_CUDA if the stream
- * reported an error. */
+ * the last bbe_rollout_batch or bbe_place_counts: BBE_OK, BBE_ERR_STEP_LIMIT, or
+ * BBE_ERR_CUDA if the stream reported an error. */
 BBE_API bbe_status bbe_batch_status(bbe_batch *batch, void *cuda_stream);
 
 /* bbe_batch_set_cfg / bbe_batch_get_cfg -- launch shape used by bbe_rollout_batch.

@@ -53,6 +53,8 @@ def lib():
             "bbe_race_init": [C.POINTER(vp), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, C.c_int, u32, vp],
             "bbe_rollout_batch": [vp, vp, vp, vp],
             "bbe_win_probs": [vp, vp, vp, vp, vp],
+            "bbe_place_counts": [vp, C.c_int32, vp, vp, vp],
+            "bbe_place_probs": [vp, C.c_int32, vp, C.c_int32, vp, vp],
             "bbe_batch_status": [vp, vp],
             "bbe_batch_set_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
@@ -131,6 +133,16 @@ def bbe_rollout_batch(batch: int, win_counts, steps_total=None, stream=None) -> 
 def bbe_win_probs(batch: int, win_counts, probs, odds=None, stream=None) -> None:
     _check(lib().bbe_win_probs(batch, _ptr(win_counts, np.int32), _ptr(probs, np.float32), _ptr(odds, np.float32),
                                _stream(stream)), "bbe_win_probs")
+
+
+def bbe_place_counts(batch: int, places: int, place_counts, steps_total=None, stream=None) -> None:
+    _check(lib().bbe_place_counts(batch, int(places), _ptr(place_counts, np.int32), _ptr(steps_total, np.int64),
+                                  _stream(stream)), "bbe_place_counts")
+
+
+def bbe_place_probs(batch: int, places: int, place_counts, top: int, probs, stream=None) -> None:
+    _check(lib().bbe_place_probs(batch, int(places), _ptr(place_counts, np.int32), int(top), _ptr(probs, np.float32),
+                                 _stream(stream)), "bbe_place_probs")
 
 
 def bbe_batch_status(batch: int, stream=None) -> None:
@@ -214,6 +226,24 @@ class Batch:
             odds = torch.empty_like(probs)
         bbe_win_probs(self.handle, counts, probs, odds, stream)
         return probs, odds
+
+    def places(self, places: int, counts=None, steps=None, stream=None):
+        """Place counts [sum n, places] (device int32) and steps per race (device int64)."""
+        import torch
+
+        if counts is None:
+            counts = torch.empty((self.rb.n_total, places), dtype=torch.int32, device="cuda")
+            steps = torch.empty(self.rb.n_races, dtype=torch.int64, device="cuda")
+        bbe_place_counts(self.handle, places, counts, steps, stream)
+        return counts, steps
+
+    def place_probs(self, counts, top: int, probs=None, stream=None):
+        import torch
+
+        if probs is None:
+            probs = torch.empty(self.rb.n_total, dtype=torch.float32, device=counts.device)
+        bbe_place_probs(self.handle, counts.shape[1], counts, top, probs, stream)
+        return probs
 
     def status(self, stream=None):
         bbe_batch_status(self.handle, stream)

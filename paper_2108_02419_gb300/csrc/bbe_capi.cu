@@ -402,7 +402,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
     add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4); add(n_races * 4);
     for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
-    add(4 * kGroups); add(4);
+    add(4 * (kGroups + 1)); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
@@ -419,7 +419,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
     float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
     float *d_prev = carve<float>(p, nt);
-    b->d_queue = carve<int32_t>(p, kGroups);
+    b->d_queue = carve<int32_t>(p, kGroups + 1);
     b->d_status = carve<int32_t>(p, 1);
     struct Up {
         void *dst;
@@ -489,6 +489,46 @@ bbe_status bbe_win_probs(const bbe_batch *b, const int32_t *win_counts, float *p
         return BBE_ERR_ARG;
     }
     BBE_CUDA_TRY(bbe::launch_win_probs(b->dev, win_counts, probs, odds, as_stream(cuda_stream)));
+    return BBE_OK;
+}
+
+bbe_status bbe_place_counts(bbe_batch *b, int32_t places, int32_t *place_counts, int64_t *steps_total,
+                            void *cuda_stream)
+{
+    if (!b || !place_counts) {
+        set_error("batch or place_counts is NULL");
+        return BBE_ERR_ARG;
+    }
+    if (places < 1 || places > BBE_MAX_COMPETITORS) {
+        set_error("places outside 1..BBE_MAX_COMPETITORS");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
+    if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(b->d_queue + kGroups, 0, sizeof(int32_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s));
+    bbe::RolloutLaunch l = make_launch(b, place_counts, steps_total, 0);
+    l.items = b->d_items;
+    l.n_items = b->n_items_v[0] + b->n_items_v[1] + b->n_items_v[2];
+    l.queue = b->d_queue + kGroups;
+    l.places = places;
+    BBE_CUDA_TRY(bbe::launch_places(l, b->num_sms, s));
+    return BBE_OK;
+}
+
+bbe_status bbe_place_probs(const bbe_batch *b, int32_t places, const int32_t *place_counts, int32_t top,
+                           float *probs, void *cuda_stream)
+{
+    if (!b || !place_counts || !probs) {
+        set_error("batch, place_counts or probs is NULL");
+        return BBE_ERR_ARG;
+    }
+    if (places < 1 || places > BBE_MAX_COMPETITORS || top < 1 || top > places) {
+        set_error("places outside 1..BBE_MAX_COMPETITORS or top outside 1..places");
+        return BBE_ERR_ARG;
+    }
+    BBE_CUDA_TRY(bbe::launch_place_probs(b->dev, places, place_counts, top, probs, as_stream(cuda_stream)));
     return BBE_OK;
 }
 

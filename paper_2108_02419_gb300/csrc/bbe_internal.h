@@ -45,6 +45,7 @@ struct RolloutLaunch {
     int32_t max_steps;
     int32_t grid, block;
     uint32_t round_key[20];  // Philox round keys (k0, k1) of rounds 0..9, from the seed
+    int32_t places;          // place-count kernel: places per competitor in `counts`
 };
 
 // Philox4x32-10 key schedule: round i uses (seed_lo + i * 0x9E3779B9, seed_hi + i * 0xBB67AE85).
@@ -65,6 +66,10 @@ cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStrea
 int rollout_resident_blocks(int dist, int slots_per_lane, int block);
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
                              cudaStream_t stream);
+// Place counts: every item of l.items (any slots-per-lane group), counts [n_total][l.places].
+cudaError_t launch_places(RolloutLaunch l, int num_sms, cudaStream_t stream);
+cudaError_t launch_place_probs(const DevBatch &b, int places, const int32_t *counts, int top, float *probs,
+                               cudaStream_t stream);
 
 void set_error(const std::string &msg);
 
@@ -97,7 +102,7 @@ struct bbe_batch {
     DevBatch dev{};
     WorkItem *d_items = nullptr;  // items grouped by slots per lane (1, 2, 4)
     int32_t n_items_v[3] = {0, 0, 0};  // item counts per group
-    int32_t *d_queue = nullptr;        // one queue head per group
+    int32_t *d_queue = nullptr;        // one queue head per group, then the place kernel's
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};
