@@ -459,6 +459,38 @@ def run_surrogate(mode: str, dev, stream) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------- place-count leg
+
+def run_places(dev, stream) -> dict:
+    """Finishing places (rollouts to the K-th finisher) on the uniform workload: K = 3 (a
+    three-place market) and K = 20 (the full order), next to the win counts (K = 1)."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rb = W.uniform_batch(seed=0)
+    out = {"workload": "uniform 4096 x 20, L 5000, 10,000 rollouts per race", "ops_per_competitor_step": ALG_OPS_PER_COMPETITOR_STEP}
+    peak = SMS * LANES_PER_SM * 2070e6
+    with bbe.Batch(rb, stream=stream) as b:
+        for K in (3, 20):
+            counts = torch.empty((rb.n_total, K), dtype=torch.int32, device=dev)
+            steps = torch.empty(rb.n_races, dtype=torch.int64, device=dev)
+            bbe.bbe_place_counts(b.handle, K, counts, steps, stream)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bbe.bbe_place_counts(b.handle, K, counts, steps, stream)
+            e1.record(stream)
+            e1.synchronize()
+            b.status(stream)
+            t = e0.elapsed_time(e1) / 1e3
+            cs = float((rb.sizes() * steps.cpu().numpy()).sum())
+            rate = cs / t
+            out[f"K{K}"] = {"s": t, "competitor_steps": cs, "competitor_steps_per_s": rate,
+                            "steps_per_rollout": cs / float(rb.n_total) / 10000.0,
+                            "alu_frac": rate * ALG_OPS_PER_COMPETITOR_STEP / peak}
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU leg
 
 def run_gpu(args, rank, world, dist):
@@ -578,6 +610,7 @@ def run_gpu(args, rank, world, dist):
     sur = None
     if rank == 0 and args.surrogate != "off" and not args.races:
         sur = run_surrogate(args.surrogate, dev, stream)
+    places = run_places(dev, stream) if rank == 0 and not args.races and args.workload == "uniform" else None
 
     cfg = workload_config(args.workload, rb)
     cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch_cfg,
@@ -589,7 +622,7 @@ def run_gpu(args, rank, world, dist):
             "win_prob_vectors_per_s": rb.n_races * world * args.steps / t_max,
             "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps, "surrogate": sur}
+            "gpu_launches": 2 * args.steps, "surrogate": sur, "places": places}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
