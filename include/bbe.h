@@ -163,6 +163,56 @@ BBE_API bbe_status bbe_place_counts(bbe_batch *batch, int32_t places, int32_t *p
 BBE_API bbe_status bbe_place_probs(const bbe_batch *batch, int32_t places, const int32_t *place_counts, int32_t top,
                                    float *probs, void *cuda_stream);
 
+/* bbe_race_trajectory -- one full run of every race of the batch: rollout k of the race's
+ * stream (the same stream as bbe_rollout_batch, so use a k outside the dry-runs' 0 .. R-1 for
+ * an independent "actual race"), every competitor moving under Eq. 1 until the last one has
+ * crossed the line (Section 3) or max_steps pass.  This is the race the bettors of Section 6
+ * watch and the space-time series its figure plots.
+ *   cap         rows recorded per race, >= 1.
+ *   positions   device float[sum n * cap]: race r's rows at race_off[r] * cap; row t
+ *               (t < min(n_steps[r], cap)) holds the n positions after step t.
+ *   step_sizes  nullable device float[sum n * cap], same layout: S_c(t) of step t.
+ *   n_steps     device int32[n_races]: steps until the last competitor crossed.
+ * Asynchronous; max_steps sets BBE_ERR_STEP_LIMIT in the batch status.  Errors: BBE_ERR_ARG,
+ * BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_race_trajectory(bbe_batch *batch, uint32_t k, int32_t cap, float *positions, float *step_sizes,
+                                       int32_t *n_steps, void *cuda_stream);
+
+/* bbe_snapshot_batch -- the rational bettors' dry-runs along a trajectory (Section 6: B bettors,
+ * each re-estimating the outcome with d dry-runs, RP(d) of Section 3, at every snapshot).
+ * Snapshot s is the state of race `race` of src after t_s = s * every steps (t_s = 0: src's
+ * own state; else the positions of row t_s - 1 and the step sizes of that row as previous
+ * steps), for every t_s whose state is recorded and has nobody across the line.  The new batch
+ * holds one race per (snapshot s, bettor b), in that order, with src's competitor parameters,
+ * seed and distribution, dry_runs rollouts and stream id race_id0 + s * bettors + b (choose
+ * race_id0 so that these ids differ from the ids src uses).  Run it with bbe_rollout_batch.
+ *   positions, step_sizes, n_steps, cap: as written by bbe_race_trajectory on src.
+ *   n_snapshots (host) receives the number of snapshots.
+ * Synchronous on cuda_stream (the trajectory rows are read back).  Errors: BBE_ERR_ARG,
+ * BBE_ERR_RANGE (no open snapshot, or more than 2^31 - 1 competitors), BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_snapshot_batch(bbe_batch **out, const bbe_batch *src, int32_t race, const float *positions,
+                                      const float *step_sizes, const int32_t *n_steps, int32_t cap, int32_t every,
+                                      int32_t bettors, int64_t dry_runs, uint32_t race_id0, int32_t *n_snapshots,
+                                      void *cuda_stream);
+
+/* bbe_bettor_predictions -- the rule-based bettors of Section 4 at the snapshots of
+ * bbe_snapshot_batch (t_s = s * every, s < n_snapshots), predicting the winner from the race so
+ * far.  predictions: device int32[n_snapshots * 4], per snapshot:
+ *   [0] LW     the leader (largest position; equal positions: lower index);
+ *   [1] UD     the second-placed competitor while its distance to the leader is below ud_gap,
+ *              else the leader;
+ *   [2] LinEx  each competitor's mean step over the last min(linex_window, t_s) steps (its
+ *              previous-step input at t_s = 0) taken as its speed for the rest of the race; the
+ *              least (L - d) / v, equal values: lower index;
+ *   [3] ZI     a uniformly drawn competitor: (w0 * n) >> 32, w0 the first Philox word of
+ *              counter (s, 0, 0, zi_stream) under src's seed.
+ * Binary32 round-to-nearest arithmetic in the written order; -1 for a snapshot past the
+ * recorded trajectory.  Asynchronous.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_bettor_predictions(const bbe_batch *src, int32_t race, const float *positions,
+                                          const float *step_sizes, const int32_t *n_steps, int32_t cap, int32_t every,
+                                          int32_t n_snapshots, int32_t linex_window, float ud_gap, uint32_t zi_stream,
+                                          int32_t *predictions, void *cuda_stream);
+
 /* bbe_batch_status -- synchronise cuda_stream and return the batch's device status from
  * the last bbe_rollout_batch or bbe_place_counts: BBE_OK, BBE_ERR_STEP_LIMIT, or
  * BBE_ERR_CUDA if the stream reported an error. */

@@ -80,6 +80,8 @@ def lib():
             L.bbe_oracle_rollout_order.restype = C.c_int
             L.bbe_oracle_race_places.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
             L.bbe_oracle_race_places.restype = C.c_int
+            L.bbe_oracle_trajectory.argtypes = [C.POINTER(_Race), u64, u32, u32, i64, vp, vp, vp, i64]
+            L.bbe_oracle_trajectory.restype = C.c_int
             L.bbe_oracle_win_probs.argtypes = [C.c_int, vp, i64, vp, vp]
             L.bbe_oracle_log_batch.argtypes = [vp, vp, i64]
             L.bbe_oracle_sincos2pi_batch.argtypes = [vp, vp, vp, i64]
@@ -158,6 +160,17 @@ def race_counts(race: dict, seed: int, r: int | None = None, R: int | None = Non
     steps = np.zeros(1, np.int64)
     st = lib().bbe_oracle_race_counts(C.byref(a.s), seed, r, k_begin, R, max_steps, _ptr(counts), _ptr(steps))
     return counts, int(steps[0]), int(st)
+
+
+def trajectory(race: dict, seed: int, r: int, k: int, max_steps: int = MAX_STEPS_DEFAULT, cap: int = 100000):
+    """A full run to the last finisher: (positions [steps, n], step sizes [steps, n], steps, status)."""
+    a = _RaceArgs(race)
+    steps = np.zeros(1, np.int64)
+    d = np.zeros((cap, race["n"]), np.float32)
+    s = np.zeros((cap, race["n"]), np.float32)
+    st = lib().bbe_oracle_trajectory(C.byref(a.s), seed, r, k, max_steps, _ptr(steps), _ptr(d), _ptr(s), cap)
+    T = int(steps[0])
+    return d[:min(T, cap)], s[:min(T, cap)], T, int(st)
 
 
 def rollout_order(race: dict, seed: int, r: int, k: int, places: int, max_steps: int = MAX_STEPS_DEFAULT):

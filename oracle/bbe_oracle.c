@@ -388,6 +388,49 @@ int bbe_oracle_race_places(const bbe_oracle_race *race, uint64_t seed, uint32_t 
     return status;
 }
 
+/* One full run of race r (rollout k of its stream): every competitor moves under Eq. 1 until
+ * the last one has crossed the line (Section 3) or max_steps steps pass; the space-time series
+ * of the race (Section 6 plots one).  For t < min(steps, cap): d_traj[t * n + c] = d_c after
+ * step t and s_traj[t * n + c] = S_c(t) (either may be NULL).  Returns 0, or
+ * BBE_ORACLE_STEP_LIMIT; *steps = steps taken. */
+int bbe_oracle_trajectory(const bbe_oracle_race *race, uint64_t seed, uint32_t r, uint32_t k, int64_t max_steps,
+                          int64_t *steps, float *d_traj, float *s_traj, int64_t cap)
+{
+    int n = race->n;
+    float *buf = (float *)malloc(sizeof(float) * (size_t)n * 5);
+    float *kr = buf, *prev = buf + n, *d = buf + 2 * n, *S = buf + 3 * n, *dn = buf + 4 * n;
+    float invL;
+    race_constants(race, kr, prev, &invL);
+    for (int c = 0; c < n; ++c) d[c] = race->d0[c];
+    int status = 0;
+    int64_t t = 0;
+    for (;;) {
+        if (t == max_steps) {
+            status = BBE_ORACLE_STEP_LIMIT;
+            break;
+        }
+        race_step(race, kr, invL, d, prev, seed, r, k, (uint32_t)t, S);
+        int all_in = 1;
+        for (int c = 0; c < n; ++c) {
+            dn[c] = d[c] + S[c];
+            if (!(dn[c] >= race->L)) all_in = 0;
+        }
+        if (t < cap) {
+            if (d_traj) memcpy(d_traj + t * n, dn, sizeof(float) * (size_t)n);
+            if (s_traj) memcpy(s_traj + t * n, S, sizeof(float) * (size_t)n);
+        }
+        for (int c = 0; c < n; ++c) {
+            prev[c] = S[c];
+            d[c] = dn[c];
+        }
+        ++t;
+        if (all_in) break;
+    }
+    *steps = t;
+    free(buf);
+    return status;
+}
+
 /* Frequentist win probabilities and decimal odds (Section 2: decimal odds are the
  * total returned per unit stake, so odds = 1/p): p_c = count_c / R. */
 void bbe_oracle_win_probs(int n, const int32_t *counts, int64_t R, float *probs, float *odds)

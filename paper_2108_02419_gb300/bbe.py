@@ -54,6 +54,11 @@ def lib():
             "bbe_rollout_batch": [vp, vp, vp, vp],
             "bbe_win_probs": [vp, vp, vp, vp, vp],
             "bbe_place_counts": [vp, C.c_int32, vp, vp, vp],
+            "bbe_race_trajectory": [vp, C.c_uint32, C.c_int32, vp, vp, vp, vp],
+            "bbe_snapshot_batch": [C.POINTER(vp), vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int64, C.c_uint32, C.POINTER(C.c_int32), vp],
+            "bbe_bettor_predictions": [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_float, C.c_uint32, vp, vp],
             "bbe_place_probs": [vp, C.c_int32, vp, C.c_int32, vp, vp],
             "bbe_batch_status": [vp, vp],
             "bbe_batch_set_cfg": [vp, C.POINTER(bbe_launch_cfg)],
@@ -143,6 +148,33 @@ def bbe_place_counts(batch: int, places: int, place_counts, steps_total=None, st
 def bbe_place_probs(batch: int, places: int, place_counts, top: int, probs, stream=None) -> None:
     _check(lib().bbe_place_probs(batch, int(places), _ptr(place_counts, np.int32), int(top), _ptr(probs, np.float32),
                                  _stream(stream)), "bbe_place_probs")
+
+
+def bbe_race_trajectory(batch: int, k: int, cap: int, positions, step_sizes, n_steps, stream=None) -> None:
+    _check(lib().bbe_race_trajectory(batch, int(k), int(cap), _ptr(positions, np.float32),
+                                     _ptr(step_sizes, np.float32), _ptr(n_steps, np.int32), _stream(stream)),
+           "bbe_race_trajectory")
+
+
+def bbe_snapshot_batch(src: int, race: int, positions, step_sizes, n_steps, cap: int, every: int, bettors: int,
+                       dry_runs: int, race_id0: int, stream=None):
+    """Returns (batch handle, number of snapshots)."""
+    h = C.c_void_p()
+    ns = C.c_int32(0)
+    _check(lib().bbe_snapshot_batch(C.byref(h), src, int(race), _ptr(positions, np.float32),
+                                    _ptr(step_sizes, np.float32), _ptr(n_steps, np.int32), int(cap), int(every),
+                                    int(bettors), int(dry_runs), int(race_id0) & 0xFFFFFFFF, C.byref(ns),
+                                    _stream(stream)), "bbe_snapshot_batch")
+    return h.value, int(ns.value)
+
+
+def bbe_bettor_predictions(src: int, race: int, positions, step_sizes, n_steps, cap: int, every: int,
+                           n_snapshots: int, linex_window: int, ud_gap: float, zi_stream: int, predictions,
+                           stream=None) -> None:
+    _check(lib().bbe_bettor_predictions(src, int(race), _ptr(positions, np.float32), _ptr(step_sizes, np.float32),
+                                        _ptr(n_steps, np.int32), int(cap), int(every), int(n_snapshots),
+                                        int(linex_window), float(ud_gap), int(zi_stream) & 0xFFFFFFFF,
+                                        _ptr(predictions, np.int32), _stream(stream)), "bbe_bettor_predictions")
 
 
 def bbe_batch_status(batch: int, stream=None) -> None:

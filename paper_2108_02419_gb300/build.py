@@ -29,6 +29,7 @@ UNITS = {
     "bbe_rollout.cu": ["--fmad=false"],
     "bbe_noalloc.cu": ["--fmad=false"],
     "bbe_places.cu": ["--fmad=false"],
+    "bbe_trajectory.cu": ["--fmad=false"],
     "bbe_surrogate.cu": [],
 }
 

@@ -10,8 +10,7 @@
 //
 // Layout: one competitor per lane (lane j of a segment holds competitor j for the whole
 // rollout; n <= 32), floor(32 / n) segments per warp, each running its own sequence of
-// rollouts of the warp's race.  i+ is found by a scan of the segment (n shuffles per step),
-// the four normals of a Philox block stay in the lane's registers, and when the rollout ends
+// rollouts of the warp's race; the step is bbe_lane.cuh's lane_step.  When the rollout ends
 // lane j of the segment adds one to the count of (competitor placed j-th, place j) in a
 // per-warp shared-memory table, flushed to global memory once per work item.  The step
 // arithmetic is the win kernel's operation for operation (binary32 round-to-nearest
@@ -21,7 +20,7 @@
 #include <cmath>
 
 #include "bbe_internal.h"
-#include "bbe_rng.cuh"
+#include "bbe_lane.cuh"
 
 namespace bbe {
 
@@ -35,27 +34,6 @@ struct PlaceStage {
     float d0[32], prev0[32];
     int cnt[32 * 32];  // [competitor][place] counts of the current work item
 };
-
-template <int DIST>
-__device__ __forceinline__ void draw_block(float (&zc)[4], int c, int t, uint32_t k, uint32_t rid,
-                                           const uint32_t (&rk)[20])
-{
-    const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, rk);
-    if (DIST == BBE_DIST_NORMAL) {
-        box_muller(wd.w0, wd.w1, zc[0], zc[1]);
-        box_muller(wd.w2, wd.w3, zc[2], zc[3]);
-    } else if (DIST == BBE_DIST_UNIFORM) {
-        zc[0] = uniform_z(wd.w0);
-        zc[1] = uniform_z(wd.w1);
-        zc[2] = uniform_z(wd.w2);
-        zc[3] = uniform_z(wd.w3);
-    } else {
-        zc[0] = two_point_z(wd.w0);
-        zc[1] = two_point_z(wd.w1);
-        zc[2] = two_point_z(wd.w2);
-        zc[3] = two_point_z(wd.w3);
-    }
-}
 
 template <int DIST>
 __global__ void __launch_bounds__(256) place_kernel(RolloutLaunch l)
@@ -95,8 +73,11 @@ __global__ void __launch_bounds__(256) place_kernel(RolloutLaunch l)
         const float L = b.L[r];
         const float invL = __fdiv_rn(1.0f, L);
         const uint32_t rid = b.race_ids ? uint32_t(b.race_ids[r]) : b.race_id0 + uint32_t(r);
-        const float4 q = lane_used ? st.pq[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float kr = lane_used ? st.kr[c] : 0.0f;
+        LaneComp cp{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (lane_used) {
+            const float4 q = st.pq[c];
+            cp = LaneComp{q.x, q.y, q.z, q.w, st.kr[c]};
+        }
         const int kend = w.k_begin + w.k_count;
         int k = w.k_begin + seg;
         bool active = lane_used && k < kend;
@@ -110,28 +91,9 @@ __global__ void __launch_bounds__(256) place_kernel(RolloutLaunch l)
 
         while (__any_sync(kFull, active)) {
             const bool running = active;
-            // i+: the nearest competitor strictly in front, lowest index among equal positions
-            float fd = INFINITY, fp = 0.0f;
-            bool hf = false;
-            for (int j = 0; j < n; ++j) {
-                const int src = lane_used ? segbase + j : lane;
-                const float dj = __shfl_sync(kFull, d, src);
-                const float pj = __shfl_sync(kFull, prev, src);
-                if (dj > d && dj < fd) {
-                    fd = dj;
-                    fp = pj;
-                    hf = true;
-                }
-            }
-            if (running && (t & 3) == 0) draw_block<DIST>(zc, c, t, uint32_t(k), rid, l.round_key);
-            const int ph = t & 3;
-            const float z = ph == 0 ? zc[0] : (ph == 1 ? zc[1] : (ph == 2 ? zc[2] : zc[3]));
-            // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
-            const float Rc = __fmaf_rn(kr, __fmaf_rn(d, invL, -0.5f), 1.0f);
-            const bool blocked = hf && !(__fsub_rn(fd, d) > q.w);
-            float S = blocked ? __fmul_rn(Rc, fminf(prev, fp)) : __fmul_rn(__fmul_rn(Rc, q.z), __fmaf_rn(q.y, z, q.x));
-            S = fmaxf(S, kStepFloor);
+            const float S = lane_step<DIST>(d, prev, cp, n, segbase, lane_used, running, c, t, uint32_t(k), rid, invL, zc,
+                                            l.round_key);
             const float dn = __fadd_rn(d, S);
             bool fin = running && !aborted && !finished && dn >= L;
             // this step's finishers of each segment, earliest crossing first
