@@ -491,6 +491,82 @@ def run_places(dev, stream) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------- bettor-population leg
+
+def run_population(dev, stream, bettors: int = 1000, dry_runs: int = 50) -> dict:
+    """Section 6's use case on the single-race workload (5 competitors, L 2000): one actual race
+    (a full trajectory), and at every step until the first competitor crosses, `bettors` RP(d)
+    bettors with d = dry_runs dry-runs each on their own streams, plus the rule-based bettors'
+    predictions; timed end to end on the device (trajectory, snapshot batch, dry-runs, odds,
+    predictions)."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rb = W.single_race_start(seed=0)
+    cap, every, k_actual, id0 = 1024, 1, 1 << 30, 1 << 20
+    out = {"workload": "single race, 5 competitors, L 2000; snapshots every step until the first finisher",
+           "bettors": bettors, "dry_runs": dry_runs}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with bbe.Batch(rb, stream=stream) as b:
+        pos = torch.empty(rb.n_total * cap, dtype=torch.float32, device=dev)
+        stp = torch.empty_like(pos)
+        ns = torch.empty(rb.n_races, dtype=torch.int32, device=dev)
+        for rep in range(2):  # the first pass warms up
+            t0 = time.perf_counter()
+            ev[0].record(stream)
+            bbe.bbe_race_trajectory(b.handle, k_actual, cap, pos, stp, ns, stream)
+            h, n_snap = bbe.bbe_snapshot_batch(b.handle, 0, pos, stp, ns, cap, every, bettors, dry_runs, id0, stream)
+            try:
+                nc = n_snap * bettors * rb.n_total
+                counts = torch.empty(nc, dtype=torch.int32, device=dev)
+                steps = torch.empty(n_snap * bettors, dtype=torch.int64, device=dev)
+                probs = torch.empty(nc, dtype=torch.float32, device=dev)
+                odds = torch.empty(nc, dtype=torch.float32, device=dev)
+                e2 = torch.cuda.Event(enable_timing=True)
+                e3 = torch.cuda.Event(enable_timing=True)
+                e2.record(stream)
+                bbe.bbe_rollout_batch(h, counts, steps, stream)
+                e3.record(stream)
+                bbe.bbe_win_probs(h, counts, probs, odds, stream)
+                pred = torch.empty(n_snap * 4, dtype=torch.int32, device=dev)
+                bbe.bbe_bettor_predictions(b.handle, 0, pos, stp, ns, cap, every, n_snap, 10, 3.0, 77, pred, stream)
+                ev[1].record(stream)
+                ev[1].synchronize()
+                wall = time.perf_counter() - t0
+                bbe.bbe_batch_status(h, stream)
+            finally:
+                bbe.bbe_destroy_batch(h)
+        t_all = ev[0].elapsed_time(ev[1]) / 1e3
+        t_dry = e2.elapsed_time(e3) / 1e3
+        cs = float(steps.sum().item()) * rb.n_total
+        T = int(ns[0].item())
+        P = pos[:T * rb.n_total].view(T, rb.n_total).cpu().numpy()
+        S = stp[:T * rb.n_total].view(T, rb.n_total).cpu().numpy()
+        cnt = counts.view(n_snap, bettors, rb.n_total).cpu().numpy()
+        pr = pred.view(n_snap, 4).cpu().numpy()
+    # the actual winner: first step across the line, then the crossing time within it
+    prev = np.vstack([rb.d0[None, :], P[:-1]])
+    cross = [int(np.argmax(P[:, c] >= rb.L[0])) for c in range(rb.n_total)]
+    tau = [np.float32(np.float32(rb.L[0]) - prev[cross[c], c]) / S[cross[c], c] for c in range(rb.n_total)]
+    winner = min(range(rb.n_total), key=lambda c: (cross[c], tau[c], c))
+    rp_pick = cnt.argmax(axis=2)                  # each bettor's favourite at each snapshot
+    pooled = cnt.sum(axis=1) / float(bettors * dry_runs)  # all bettors' dry-runs pooled
+    out.update({
+        "snapshots": n_snap, "actual_race_steps": T, "actual_winner": winner,
+        "dry_runs_total": n_snap * bettors * dry_runs,
+        "s_end_to_end_device": t_all, "s_wall": wall, "s_dry_runs": t_dry,
+        "dry_runs_per_s": n_snap * bettors * dry_runs / t_dry,
+        "competitor_steps_per_s": cs / t_dry,
+        "bettor_updates_per_s_end_to_end": n_snap * bettors / t_all,
+        "pick_is_winner": {"RP(d) bettor": float((rp_pick == winner).mean()),
+                           "pooled dry-runs": float((pooled.argmax(axis=1) == winner).mean()),
+                           "LW": float((pr[:, 0] == winner).mean()), "UD(3)": float((pr[:, 1] == winner).mean()),
+                           "LinEx(10)": float((pr[:, 2] == winner).mean()), "ZI": float((pr[:, 3] == winner).mean())},
+    })
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU leg
 
 def run_gpu(args, rank, world, dist):
@@ -611,6 +687,7 @@ def run_gpu(args, rank, world, dist):
     if rank == 0 and args.surrogate != "off" and not args.races:
         sur = run_surrogate(args.surrogate, dev, stream)
     places = run_places(dev, stream) if rank == 0 and not args.races and args.workload == "uniform" else None
+    population = run_population(dev, stream) if rank == 0 and not args.races else None
 
     cfg = workload_config(args.workload, rb)
     cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch_cfg,
@@ -622,7 +699,8 @@ def run_gpu(args, rank, world, dist):
             "win_prob_vectors_per_s": rb.n_races * world * args.steps / t_max,
             "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps, "surrogate": sur, "places": places}
+            "gpu_launches": 2 * args.steps, "surrogate": sur, "places": places,
+            "population": population}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
