@@ -28,7 +28,6 @@ UNITS = {
     "bbe_capi.cu": ["--fmad=false"],
     "bbe_rollout.cu": ["--fmad=false"],
     "bbe_noalloc.cu": ["--fmad=false"],
-    "bbe_places.cu": ["--fmad=false"],
     "bbe_trajectory.cu": ["--fmad=false"],
     "bbe_surrogate.cu": [],
 }

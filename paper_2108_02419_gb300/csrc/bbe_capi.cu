@@ -402,7 +402,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
     add((n_races + 1) * 4); add(n_races * 4); add(n_races * 8); add(size_t(nt) * 4); add(n_races * 4);
     for (int i = 0; i < 7; ++i) add(size_t(nt) * 4);
-    add(4 * (kGroups + 1)); add(4);
+    add(4 * kGroups); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
@@ -419,7 +419,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_d0 = carve<float>(p, nt), *d_mu = carve<float>(p, nt), *d_sigma = carve<float>(p, nt);
     float *d_rho = carve<float>(p, nt), *d_P = carve<float>(p, nt), *d_theta = carve<float>(p, nt);
     float *d_prev = carve<float>(p, nt);
-    b->d_queue = carve<int32_t>(p, kGroups + 1);
+    b->d_queue = carve<int32_t>(p, kGroups);
     b->d_status = carve<int32_t>(p, 1);
     struct Up {
         void *dst;
@@ -506,14 +506,16 @@ bbe_status bbe_place_counts(bbe_batch *b, int32_t places, int32_t *place_counts,
     cudaStream_t s = as_stream(cuda_stream);
     BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
     if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));
-    BBE_CUDA_TRY(cudaMemsetAsync(b->d_queue + kGroups, 0, sizeof(int32_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, kGroups * sizeof(int32_t), s));
     BBE_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s));
-    bbe::RolloutLaunch l = make_launch(b, place_counts, steps_total, 0);
-    l.items = b->d_items;
-    l.n_items = b->n_items_v[0] + b->n_items_v[1] + b->n_items_v[2];
-    l.queue = b->d_queue + kGroups;
-    l.places = places;
-    BBE_CUDA_TRY(bbe::launch_places(l, b->num_sms, s));
+    for (int g = kGroups - 1; g >= 0; --g) {
+        if (b->n_items_v[g] == 0) continue;
+        bbe::RolloutLaunch l = make_launch(b, place_counts, steps_total, g);
+        l.places = places;
+        const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block);
+        l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
+        BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
+    }
     return BBE_OK;
 }
 

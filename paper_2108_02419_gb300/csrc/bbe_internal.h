@@ -66,8 +66,9 @@ cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStrea
 int rollout_resident_blocks(int dist, int slots_per_lane, int block);
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
                              cudaStream_t stream);
-// Place counts: every item of l.items (any slots-per-lane group), counts [n_total][l.places].
-cudaError_t launch_places(RolloutLaunch l, int num_sms, cudaStream_t stream);
+// The rollout kernel in place mode: counts [n_total][l.places], rollouts to the K-th finisher.
+cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
+int place_resident_blocks(int dist, int slots_per_lane, int block);
 cudaError_t launch_place_probs(const DevBatch &b, int places, const int32_t *counts, int top, float *probs,
                                cudaStream_t stream);
 
@@ -102,7 +103,7 @@ struct bbe_batch {
     DevBatch dev{};
     WorkItem *d_items = nullptr;  // items grouped by slots per lane (1, 2, 4)
     int32_t n_items_v[3] = {0, 0, 0};  // item counts per group
-    int32_t *d_queue = nullptr;        // one queue head per group, then the place kernel's
+    int32_t *d_queue = nullptr;        // one queue head per group
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};

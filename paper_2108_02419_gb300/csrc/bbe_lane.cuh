@@ -1,12 +1,12 @@
-// bbe_lane.cuh -- one step of Eq. 1 in the one-competitor-per-lane layout, shared by the
-// place-count and trajectory kernels.
+// bbe_lane.cuh -- one step of Eq. 1 in the one-competitor-per-lane layout (the trajectory
+// kernel: one rollout per race, so the rank-ordered slots of the rollout kernel do not pay).
 //
 // A race of n competitors occupies a segment of n lanes (lane segbase + c holds competitor c
 // for the whole rollout).  i+ (the nearest competitor strictly in front, lowest index among
 // equal positions) is found by a scan of the segment; the four normals of the current Philox
 // block (counter (k, t >> 2, c, race id)) are kept in the lane's registers.  The arithmetic
-// is the win kernel's, operation for operation: binary32 round-to-nearest intrinsics, and the
-// including translation units are compiled with --fmad=false.
+// is the rollout kernel's, operation for operation: binary32 round-to-nearest intrinsics, and
+// the including translation unit is compiled with --fmad=false.
 #pragma once
 
 #include "bbe_internal.h"

@@ -13,7 +13,11 @@
 // lane).  Finishing is detected with a ballot; the winner (least within-step crossing time,
 // lowest index on ties) comes from the ballot mask, or from a shuffle reduction when several
 // cross in the same step.  Each slot counts the wins of the competitor that starts every
-// rollout in it; the counts are reduced once per work item.
+// rollout in it; the counts are reduced once per work item.  The same kernel in place mode
+// runs every rollout to the K-th finisher (include/bbe.h: bbe_place_counts): finished
+// competitors keep moving in their rank slots, the finishers of a step are placed by repeated
+// argmin of (crossing time, index), the lane of place j records its competitor, and completed
+// rollouts are tallied in a per-warp [competitor][place] table in shared memory.
 //
 // The arithmetic is pinned to binary32 round-to-nearest with explicit intrinsics, and this
 // file is compiled with --fmad=false, so the counts are bit-identical to any
@@ -90,11 +94,17 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
     return z0;
 }
 
-template <int DIST, int V>
+// MODE 0: win counts (the rollout ends at the first finisher).  MODE 1: place counts (the
+// rollout ends when K = min(places, n) competitors have crossed; competitors past the line keep
+// moving and keep their rank slots; a competitor has finished exactly when its position is at
+// least L, since positions only grow).
+template <int DIST, int V, int MODE>
 __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
 {
     extern __shared__ WarpStage stage_all[];
     WarpStage &st = stage_all[threadIdx.x >> 5];
+    // place mode: a [competitor][place] count table per warp after the stages
+    int *cnt = MODE == 1 ? reinterpret_cast<int *>(stage_all + (blockDim.x >> 5)) + (threadIdx.x >> 5) * 1024 : nullptr;
     const DevBatch &b = l.b;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -138,6 +148,9 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             rank += (di < my_d0 || (di == my_d0 && i < lane)) ? 1 : 0;
         }
         if (lane < n) st.init_c[rank] = lane;
+        const int K = MODE == 1 ? min(l.places, n) : 1;
+        if (MODE == 1)
+            for (int i = lane; i < n * K; i += 32) cnt[i] = 0;
         __syncwarp();
 
         const float L = b.L[r];
@@ -160,6 +173,10 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         }
         long long steps = 0;
         bool hit_limit = false;
+        int placed = 0;      // place mode: competitors placed in the segment's current rollout
+        int my_ord[V];       // place mode: competitor in place ql + m * nl
+#pragma unroll
+        for (int m = 0; m < V; ++m) my_ord[m] = 0;
 
         while (__any_sync(kFull, active)) {
             __syncwarp();  // z-cache writes of earlier steps are visible to every lane
@@ -302,68 +319,145 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
                 Sv = fmaxf(Sv, kStepFloor);
                 S[v] = Sv;
                 dn[v] = __fadd_rn(s[v].d, Sv);
-                fin[v] = running && valid[v] && !aborted && dn[v] >= L;
+                fin[v] = running && valid[v] && !aborted && dn[v] >= L && (MODE == 0 || s[v].d < L);
                 any_fin |= fin[v];
             }
             // finish: least within-step crossing time, ties to the lowest competitor index
             bool seg_fin = false, seg_done = false;
-            if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
-                const unsigned amask = __ballot_sync(kFull, aborted);
-                unsigned fm[V];
-                int nfin = 0;
+            if constexpr (MODE == 0) {
+                if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
+                    const unsigned amask = __ballot_sync(kFull, aborted);
+                    unsigned fm[V];
+                    int nfin = 0;
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
-                    nfin += __popc(fm[v]);
-                }
-                seg_fin = nfin > 0;
-                seg_done = seg_fin || (amask & segmask) != 0u;
-                int wl = lane, wv = 0;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (fm[v] != 0u) {
-                        wl = __ffs(fm[v]) - 1;
-                        wv = v;
+                    for (int v = 0; v < V; ++v) {
+                        fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
+                        nfin += __popc(fm[v]);
                     }
+                    seg_fin = nfin > 0;
+                    seg_done = seg_fin || (amask & segmask) != 0u;
+                    int wl = lane, wv = 0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (fm[v] != 0u) {
+                            wl = __ffs(fm[v]) - 1;
+                            wv = v;
+                        }
+                    }
+                    if (__any_sync(kFull, nfin > 1)) {
+                        float best = INFINITY;
+                        int bestc = 1 << 30, bl = wl, bv = wv;
+                        for (int j = 0; j < nl; ++j) {
+                            const int src = lane_used ? segbase + j : lane;
+#pragma unroll
+                            for (int u = 0; u < V; ++u) {
+                                const float tau = fin[u] ? __fdiv_rn(__fsub_rn(L, s[u].d), S[u]) : INFINITY;
+                                const float tj = __shfl_sync(kFull, tau, src);
+                                const int cj = __shfl_sync(kFull, s[u].c, src);
+                                if (tj < best || (tj == best && tj < INFINITY && cj < bestc)) {
+                                    best = tj;
+                                    bestc = cj;
+                                    bl = src;
+                                    bv = u;
+                                }
+                            }
+                        }
+                        if (nfin > 1) {
+                            wl = bl;
+                            wv = bv;
+                        }
+                    }
+                    int cw = 0;
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        const int cu = __shfl_sync(kFull, s[u].c, wl);
+                        cw = wv == u ? cu : cw;
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
                 }
-                if (__any_sync(kFull, nfin > 1)) {
-                    float best = INFINITY;
-                    int bestc = 1 << 30, bl = wl, bv = wv;
-                    for (int j = 0; j < nl; ++j) {
-                        const int src = lane_used ? segbase + j : lane;
+
+            } else {
+                // place this step's new finishers of each segment, earliest crossing first
+                if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
+                    const unsigned amask = __ballot_sync(kFull, aborted);
+                    for (;;) {
+                        unsigned fm[V];
+                        int nfin = 0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
+                            nfin += __popc(fm[v]);
+                        }
+                        if (!__any_sync(kFull, nfin > 0)) break;
+                        int wl = lane, wv = 0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            if (fm[v] != 0u) {
+                                wl = __ffs(fm[v]) - 1;
+                                wv = v;
+                            }
+                        }
+                        if (__any_sync(kFull, nfin > 1)) {
+                            float best = INFINITY;
+                            int bestc = 1 << 30, bl = wl, bv = wv;
+                            for (int j = 0; j < nl; ++j) {
+                                const int src = lane_used ? segbase + j : lane;
+#pragma unroll
+                                for (int u = 0; u < V; ++u) {
+                                    const float tau = fin[u] ? __fdiv_rn(__fsub_rn(L, s[u].d), S[u]) : INFINITY;
+                                    const float tj = __shfl_sync(kFull, tau, src);
+                                    const int cj = __shfl_sync(kFull, s[u].c, src);
+                                    if (tj < best || (tj == best && tj < INFINITY && cj < bestc)) {
+                                        best = tj;
+                                        bestc = cj;
+                                        bl = src;
+                                        bv = u;
+                                    }
+                                }
+                            }
+                            if (nfin > 1) {
+                                wl = bl;
+                                wv = bv;
+                            }
+                        }
+                        int cw = 0;
 #pragma unroll
                         for (int u = 0; u < V; ++u) {
-                            const float tau = fin[u] ? __fdiv_rn(__fsub_rn(L, s[u].d), S[u]) : INFINITY;
-                            const float tj = __shfl_sync(kFull, tau, src);
-                            const int cj = __shfl_sync(kFull, s[u].c, src);
-                            if (tj < best || (tj == best && tj < INFINITY && cj < bestc)) {
-                                best = tj;
-                                bestc = cj;
-                                bl = src;
-                                bv = u;
+                            const int cu = __shfl_sync(kFull, s[u].c, wl);
+                            cw = wv == u ? cu : cw;
+                        }
+                        if (nfin > 0) {
+#pragma unroll
+                            for (int m = 0; m < V; ++m)
+                                if (placed == ql + m * nl) my_ord[m] = cw;
+                            ++placed;
+                            if (lane == wl) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    if (v == wv) fin[v] = false;
                             }
                         }
                     }
-                    if (nfin > 1) {
-                        wl = bl;
-                        wv = bv;
-                    }
+                    seg_fin = placed >= K;
+                    seg_done = seg_fin || (amask & segmask) != 0u;
                 }
-                int cw = 0;
-#pragma unroll
-                for (int u = 0; u < V; ++u) {
-                    const int cu = __shfl_sync(kFull, s[u].c, wl);
-                    cw = wv == u ? cu : cw;
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
             }
 
             // advance, or start the segment's next rollout
             if (active) {
                 if (running) {
                     if (seg_done) {
+                        if constexpr (MODE == 1) {
+                            // one count per place of a completed rollout (a cut-off one counts for nobody)
+#pragma unroll
+                            for (int m = 0; m < V; ++m) {
+                                const int j = ql + m * nl;
+                                if (seg_fin && j < K) atomicAdd(&cnt[my_ord[m] * K + j], 1);
+                            }
+                            placed = 0;
+                        }
                         steps += seg_fin ? (t + 1) : t;
                         hit_limit |= !seg_fin;
                         k += nseg;
@@ -394,12 +488,21 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
             ++gstep;
 
         }
-        // one reduction per work item: wins of each home competitor summed over segments
+        if constexpr (MODE == 0) {
+            // one reduction per work item: wins of each home competitor summed over segments
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            int total = 0;
-            for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
-            if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
+            for (int v = 0; v < V; ++v) {
+                int total = 0;
+                for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
+                if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
+            }
+        } else {
+            // one flush of the place table per work item
+            __syncwarp();
+            for (int i = lane; i < n * K; i += 32) {
+                const int c = cnt[i];
+                if (c != 0) atomicAdd(&l.counts[(off + i / K) * l.places + i % K], c);
+            }
         }
         unsigned long long stp = (lane_used && ql == 0) ? (unsigned long long)steps : 0ull;
         for (int o = 16; o > 0; o >>= 1) stp += __shfl_xor_sync(kFull, stp, o);
@@ -419,33 +522,50 @@ __global__ void win_probs_kernel(DevBatch b, const int32_t *__restrict__ counts,
     if (odds) odds[i] = __fdiv_rn(1.0f, p);
 }
 
-template <int V>
+// probs[i] = (sum of place counts of competitor i over places 0 .. top-1) / R of its race
+__global__ void place_probs_kernel(DevBatch b, int places, const int32_t *__restrict__ counts, int top,
+                                   float *__restrict__ probs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n_total) return;
+    int64_t s = 0;
+    for (int j = 0; j < top; ++j) s += counts[int64_t(i) * places + j];
+    probs[i] = __fdiv_rn(__ll2float_rn(s), __ll2float_rn(b.R[b.comp_race[i]]));
+}
+
+template <int MODE>
+size_t stage_bytes(int block)
+{
+    return size_t(block / 32) * (sizeof(WarpStage) + (MODE == 1 ? 1024 * sizeof(int) : 0));
+}
+
+template <int V, int MODE>
 cudaError_t launch_v(const RolloutLaunch &l, cudaStream_t stream)
 {
-    const size_t smem = size_t(l.block / 32) * sizeof(WarpStage);
+    const size_t smem = stage_bytes<MODE>(l.block);
     switch (l.b.dist) {
-    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL, V><<<l.grid, l.block, smem, stream>>>(l); break;
-    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM, V><<<l.grid, l.block, smem, stream>>>(l); break;
-    default: rollout_kernel<BBE_DIST_TWO_POINT, V><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
+    default: rollout_kernel<BBE_DIST_TWO_POINT, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
     }
     return cudaGetLastError();
 }
 
-template <int V>
+template <int V, int MODE>
 int resident_v(int dist, int block)
 {
-    const size_t smem = size_t(block / 32) * sizeof(WarpStage);
+    const size_t smem = stage_bytes<MODE>(block);
     int nb = 0;
     cudaError_t e;
     switch (dist) {
     case BBE_DIST_NORMAL:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL, V>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL, V, MODE>, block, smem);
         break;
     case BBE_DIST_UNIFORM:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM, V>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM, V, MODE>, block, smem);
         break;
     default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT, V>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT, V, MODE>, block, smem);
         break;
     }
     return e == cudaSuccess ? nb : 1;
@@ -456,19 +576,46 @@ int resident_v(int dist, int block)
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
     switch (slots_per_lane) {
-    case 4: return launch_v<4>(l, stream);
-    case 2: return launch_v<2>(l, stream);
-    default: return launch_v<1>(l, stream);
+    case 4: return launch_v<4, 0>(l, stream);
+    case 2: return launch_v<2, 0>(l, stream);
+    default: return launch_v<1, 0>(l, stream);
     }
 }
 
 int rollout_resident_blocks(int dist, int slots_per_lane, int block)
 {
     switch (slots_per_lane) {
-    case 4: return resident_v<4>(dist, block);
-    case 2: return resident_v<2>(dist, block);
-    default: return resident_v<1>(dist, block);
+    case 4: return resident_v<4, 0>(dist, block);
+    case 2: return resident_v<2, 0>(dist, block);
+    default: return resident_v<1, 0>(dist, block);
     }
+}
+
+cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
+{
+    switch (slots_per_lane) {
+    case 4: return launch_v<4, 1>(l, stream);
+    case 2: return launch_v<2, 1>(l, stream);
+    default: return launch_v<1, 1>(l, stream);
+    }
+}
+
+int place_resident_blocks(int dist, int slots_per_lane, int block)
+{
+    switch (slots_per_lane) {
+    case 4: return resident_v<4, 1>(dist, block);
+    case 2: return resident_v<2, 1>(dist, block);
+    default: return resident_v<1, 1>(dist, block);
+    }
+}
+
+cudaError_t launch_place_probs(const DevBatch &b, int places, const int32_t *counts, int top, float *probs,
+                               cudaStream_t stream)
+{
+    const int threads = 256;
+    const int blocks = (b.n_total + threads - 1) / threads;
+    if (blocks > 0) place_probs_kernel<<<blocks, threads, 0, stream>>>(b, places, counts, top, probs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *probs, float *odds,
