@@ -163,6 +163,24 @@ BBE_API bbe_status bbe_place_counts(bbe_batch *batch, int32_t places, int32_t *p
 BBE_API bbe_status bbe_place_probs(const bbe_batch *batch, int32_t places, const int32_t *place_counts, int32_t top,
                                    float *probs, void *cuda_stream);
 
+/* bbe_preference_coefficients -- the preference coefficients P_c of Eq. 1 from vectors
+ * (Section 3: P_c(f_r, p_c) in [0, 1] reduces c's stochastic step by an amount that depends on
+ * the mismatch between the race's factors f_r, such as wet or dry going, and the competitor's
+ * preferred values p_c; the paper gives no formula).  This library's law:
+ *   P_c = prod over factors k in order of (1 - w_k * min(1, |f_r,k - p_c,k|)),
+ * binary32 round-to-nearest, each product and difference rounded once.  With weights in [0, 1]
+ * the result lies in [0, 1]: 1 for a perfect match, 0 for a full mismatch on a factor of weight 1.
+ * Pass the result as bbe_race_init's pref argument.
+ *   race_off     device int32[n_races + 1], CSR over competitors (n_competitors = race_off[n_races]).
+ *   factors      device float[n_races * n_factors], row-major.
+ *   preferences  device float[n_competitors * n_factors], row-major.
+ *   weights      device float[n_factors].
+ *   P            device float[n_competitors], overwritten.
+ * Asynchronous.  Errors: BBE_ERR_ARG (a NULL pointer, n_races < 1, n_factors < 1), BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_preference_coefficients(int32_t n_races, const int32_t *race_off, int32_t n_competitors,
+                                               int32_t n_factors, const float *factors, const float *preferences,
+                                               const float *weights, float *P, void *cuda_stream);
+
 /* bbe_race_trajectory -- one full run of every race of the batch: rollout k of the race's
  * stream (the same stream as bbe_rollout_batch, so use a k outside the dry-runs' 0 .. R-1 for
  * an independent "actual race"), every competitor moving under Eq. 1 until the last one has

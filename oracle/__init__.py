@@ -82,6 +82,7 @@ def lib():
             L.bbe_oracle_race_places.restype = C.c_int
             L.bbe_oracle_trajectory.argtypes = [C.POINTER(_Race), u64, u32, u32, i64, vp, vp, vp, i64]
             L.bbe_oracle_trajectory.restype = C.c_int
+            L.bbe_oracle_preference.argtypes = [C.c_int, vp, C.c_int, vp, vp, vp, vp]
             L.bbe_oracle_win_probs.argtypes = [C.c_int, vp, i64, vp, vp]
             L.bbe_oracle_log_batch.argtypes = [vp, vp, i64]
             L.bbe_oracle_sincos2pi_batch.argtypes = [vp, vp, vp, i64]
@@ -259,6 +260,19 @@ def batch_counts(batch, races=None, threads: int | None = None, max_steps: int =
         status = min(status, s)
     counts = np.concatenate(per_race).astype(np.int32) if per_race else np.zeros(0, np.int32)
     return counts, steps, status
+
+
+def preference(race_off, factors, prefs, weights) -> np.ndarray:
+    """P per competitor from factor vectors [n_races, F], preference vectors [sum n, F] and weights [F]."""
+    off = np.ascontiguousarray(race_off, np.int32)
+    f = np.ascontiguousarray(factors, np.float32)
+    p = np.ascontiguousarray(prefs, np.float32)
+    w = np.ascontiguousarray(weights, np.float32)
+    F = w.size
+    assert f.shape == (off.size - 1, F) and p.shape == (int(off[-1]), F)
+    out = np.empty(int(off[-1]), np.float32)
+    lib().bbe_oracle_preference(off.size - 1, _ptr(off), F, _ptr(f), _ptr(p), _ptr(w), _ptr(out))
+    return out
 
 
 def win_probs(counts, R: int):

@@ -431,6 +431,28 @@ int bbe_oracle_trajectory(const bbe_oracle_race *race, uint64_t seed, uint32_t r
     return status;
 }
 
+/* Preference coefficients P_c(f_r, p_c) of Eq. 1 from factor and preference vectors
+ * (Section 3: a coefficient in [0, 1] that reduces the step by an amount depending on the
+ * mismatch between the race's factors f_r and the competitor's preferences p_c; the paper gives
+ * no formula).  Reading: P_c = prod_i (1 - w_i * min(1, |f_r,i - p_c,i|)), i = 0 .. F-1 in order,
+ * binary32, with weights w_i in [0, 1], so a perfect match gives 1 and a full mismatch on a
+ * factor of weight 1 gives 0.  factors [n_races][F], prefs [sum n][F], P [sum n]. */
+void bbe_oracle_preference(int n_races, const int32_t *race_off, int F, const float *factors, const float *prefs,
+                           const float *weights, float *P)
+{
+    for (int r = 0; r < n_races; ++r) {
+        for (int c = race_off[r]; c < race_off[r + 1]; ++c) {
+            float p = 1.0f;
+            for (int i = 0; i < F; ++i) {
+                float m = fabsf(factors[r * F + i] - prefs[c * F + i]);
+                if (m > 1.0f) m = 1.0f;
+                p = p * (1.0f - weights[i] * m);
+            }
+            P[c] = p;
+        }
+    }
+}
+
 /* Frequentist win probabilities and decimal odds (Section 2: decimal odds are the
  * total returned per unit stake, so odds = 1/p): p_c = count_c / R. */
 void bbe_oracle_win_probs(int n, const int32_t *counts, int64_t R, float *probs, float *odds)

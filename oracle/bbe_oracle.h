@@ -47,6 +47,8 @@ int bbe_oracle_race_places(const bbe_oracle_race *race, uint64_t seed, uint32_t 
                            int32_t *counts, int64_t *steps_total);
 int bbe_oracle_trajectory(const bbe_oracle_race *race, uint64_t seed, uint32_t r, uint32_t k, int64_t max_steps,
                           int64_t *steps, float *d_traj, float *s_traj, int64_t cap);
+void bbe_oracle_preference(int n_races, const int32_t *race_off, int F, const float *factors, const float *prefs,
+                           const float *weights, float *P);
 void bbe_oracle_win_probs(int n, const int32_t *counts, int64_t R, float *probs, float *odds);
 void bbe_oracle_log_batch(const float *x, float *y, int64_t n);
 void bbe_oracle_sincos2pi_batch(const uint32_t *m24, float *s, float *c, int64_t n);

@@ -55,6 +55,7 @@ def lib():
             "bbe_win_probs": [vp, vp, vp, vp, vp],
             "bbe_place_counts": [vp, C.c_int32, vp, vp, vp],
             "bbe_race_trajectory": [vp, C.c_uint32, C.c_int32, vp, vp, vp, vp],
+            "bbe_preference_coefficients": [C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp],
             "bbe_snapshot_batch": [C.POINTER(vp), vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32,
                                    C.c_int64, C.c_uint32, C.POINTER(C.c_int32), vp],
             "bbe_bettor_predictions": [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -148,6 +149,14 @@ def bbe_place_counts(batch: int, places: int, place_counts, steps_total=None, st
 def bbe_place_probs(batch: int, places: int, place_counts, top: int, probs, stream=None) -> None:
     _check(lib().bbe_place_probs(batch, int(places), _ptr(place_counts, np.int32), int(top), _ptr(probs, np.float32),
                                  _stream(stream)), "bbe_place_probs")
+
+
+def bbe_preference_coefficients(n_races: int, race_off, n_competitors: int, n_factors: int, factors, preferences,
+                                weights, P, stream=None) -> None:
+    _check(lib().bbe_preference_coefficients(int(n_races), _ptr(race_off, np.int32), int(n_competitors),
+                                             int(n_factors), _ptr(factors, np.float32), _ptr(preferences, np.float32),
+                                             _ptr(weights, np.float32), _ptr(P, np.float32), _stream(stream)),
+           "bbe_preference_coefficients")
 
 
 def bbe_race_trajectory(batch: int, k: int, cap: int, positions, step_sizes, n_steps, stream=None) -> None:

@@ -519,6 +519,46 @@ bbe_status bbe_place_counts(bbe_batch *b, int32_t places, int32_t *place_counts,
     return BBE_OK;
 }
 
+namespace {
+// P_c = prod_i (1 - w_i min(1, |f_r,i - p_c,i|)), one thread per competitor; its race by binary
+// search of race_off
+__global__ void preference_kernel(int n_races, const int32_t *__restrict__ race_off, int F,
+                                  const float *__restrict__ factors, const float *__restrict__ prefs,
+                                  const float *__restrict__ weights, float *__restrict__ P)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= race_off[n_races]) return;
+    int lo = 0, hi = n_races;  // race_off[lo] <= i < race_off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (race_off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    float p = 1.0f;
+    for (int k = 0; k < F; ++k) {
+        const float m = fminf(fabsf(__fsub_rn(factors[size_t(lo) * F + k], prefs[size_t(i) * F + k])), 1.0f);
+        p = __fmul_rn(p, __fsub_rn(1.0f, __fmul_rn(weights[k], m)));
+    }
+    P[i] = p;
+}
+}  // namespace
+
+bbe_status bbe_preference_coefficients(int32_t n_races, const int32_t *race_off, int32_t n_competitors,
+                                       int32_t n_factors, const float *factors, const float *preferences,
+                                       const float *weights, float *P, void *cuda_stream)
+{
+    if (n_races < 1 || n_competitors < 0 || n_factors < 1 || !race_off || !factors || !preferences || !weights || !P) {
+        set_error("bbe_preference_coefficients: bad arguments");
+        return BBE_ERR_ARG;
+    }
+    if (n_competitors == 0) return BBE_OK;
+    const int threads = 256;
+    preference_kernel<<<unsigned((n_competitors + threads - 1) / threads), threads, 0, as_stream(cuda_stream)>>>(
+        n_races, race_off, n_factors, factors, preferences, weights, P);
+    BBE_CUDA_TRY(cudaGetLastError());
+    return BBE_OK;
+}
+
 bbe_status bbe_place_probs(const bbe_batch *b, int32_t places, const int32_t *place_counts, int32_t top,
                            float *probs, void *cuda_stream)
 {

@@ -104,3 +104,36 @@ def test_bad_arguments(bbe):
         with pytest.raises(bbe.BbeError) as ei:
             bbe.bbe_race_trajectory(b.handle, 0, 0, pos, stp, ns)
         assert ei.value.status == -1
+
+
+def test_preference_coefficients_match_oracle(bbe):
+    rng = np.random.default_rng(12)
+    sizes = rng.integers(1, 25, 300)
+    off = np.zeros(sizes.size + 1, np.int32)
+    off[1:] = np.cumsum(sizes)
+    F = 6
+    f = rng.uniform(0, 1, (sizes.size, F)).astype(np.float32)
+    p = rng.uniform(-0.5, 1.5, (int(off[-1]), F)).astype(np.float32)
+    w = rng.uniform(0, 1, F).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
+    bbe.bbe_preference_coefficients(sizes.size, dev(off), int(off[-1]), F, dev(f), dev(p), dev(w), P)
+    torch.cuda.synchronize()
+    assert np.array_equal(P.cpu().numpy(), oracle.preference(off, f, p, w))
+    # the coefficients drive Eq. 1 through bbe_race_init's preference input
+    rb = W.uneven_batch(seed=62, n_races=sizes.size, n_lo=1, n_hi=24, rollouts=200, rem_lo=100.0, rem_hi=600.0)
+    rb = W.from_arrays(rb.sizes(), rb.L, rb.rollouts, rb.d0, rb.mu, rb.sigma, rb.rho, seed=5)
+    off2 = rb.race_off
+    f2 = rng.uniform(0, 1, (rb.n_races, F)).astype(np.float32)
+    p2 = rng.uniform(0, 1, (rb.n_total, F)).astype(np.float32)
+    P2 = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+    bbe.bbe_preference_coefficients(rb.n_races, dev(off2), rb.n_total, F, dev(f2), dev(p2), dev(w), P2)
+    rb.P = P2.cpu().numpy()
+    with bbe.Batch(rb) as b:
+        counts, steps = b.rollout()
+        b.status()
+        counts, steps = counts.cpu().numpy(), steps.cpu().numpy()
+    races = [0, 7, rb.n_races - 1]
+    want_c, want_s, _ = oracle.batch_counts(rb, races=races)
+    got = np.concatenate([counts[off2[r]:off2[r + 1]] for r in races])
+    assert np.array_equal(got, want_c) and np.array_equal(steps[races], want_s)
