@@ -63,7 +63,34 @@ def parse():
     ap.add_argument("--surrogate-kernels", default="", choices=["", "forward", "train"],
                     help="profiling aid: run only the surrogate's inference (3 calls) or 4 training steps of "
                          "4096 races on the first --races uneven states (default 100000), print timings and exit")
+    ap.add_argument("--place-kernels", type=int, default=0, metavar="K",
+                    help="profiling aid: run place counts to the K-th finisher on the --workload batch "
+                         "(first --races races), print timings and exit")
     return ap.parse_args()
+
+
+def run_place_kernels(args) -> dict:
+    """Place counts alone (for profiler captures): one warm-up pass, one timed pass."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rb = make_workload(args.workload, 0, args.races)
+    K = args.place_kernels
+    with bbe.Batch(rb) as b:
+        counts = torch.empty((rb.n_total, K), dtype=torch.int32, device="cuda")
+        steps = torch.empty(rb.n_races, dtype=torch.int64, device="cuda")
+        bbe.bbe_place_counts(b.handle, K, counts, steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bbe.bbe_place_counts(b.handle, K, counts, steps)
+        e1.record()
+        e1.synchronize()
+        b.status()
+        cs = float((rb.sizes() * steps.cpu().numpy()).sum())
+    t = e0.elapsed_time(e1) / 1e3
+    return {"place_kernels": K, "workload": args.workload, "races": rb.n_races, "s": t,
+            "competitor_steps_per_s": cs / t}
 
 
 def run_surrogate_kernels(mode: str, races: int) -> dict:
@@ -709,6 +736,9 @@ def main():
     args = parse()
     if args.surrogate_kernels:
         print(json.dumps(run_surrogate_kernels(args.surrogate_kernels, args.races)))
+        return
+    if args.place_kernels:
+        print(json.dumps(run_place_kernels(args)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
