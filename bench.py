@@ -626,6 +626,8 @@ def run_gpu(args, rank, world, dist):
     batch.status(stream)
     units_per_step = competitor_steps(rb, steps_t.cpu().numpy())
     rollouts_per_step = int(rb.rollouts.sum())
+    # kernels of one step: the rollout pass's persistent launches plus the win-probability kernel
+    launches_per_step = bbe.bbe_batch_launches(batch.handle) + 1
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -726,7 +728,7 @@ def run_gpu(args, rank, world, dist):
             "win_prob_vectors_per_s": rb.n_races * world * args.steps / t_max,
             "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps, "surrogate": sur, "places": places,
+            "gpu_launches": launches_per_step * args.steps, "surrogate": sur, "places": places,
             "population": population}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -248,6 +248,11 @@ BBE_API bbe_status bbe_batch_get_cfg(const bbe_batch *batch, bbe_launch_cfg *cfg
  * BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_batch_autotune(bbe_batch *batch, int32_t *win_counts, double budget_ms, void *cuda_stream);
 
+/* bbe_batch_launches -- rollout-kernel launches of one bbe_rollout_batch or bbe_place_counts
+ * call on this batch (one persistent launch per group of races with the same competitors per
+ * lane, 1 to 3).  Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_batch_launches(const bbe_batch *batch, int32_t *kernels_per_pass);
+
 /* bbe_batch_info -- sizes of a staged batch (any output pointer may be NULL). */
 BBE_API bbe_status bbe_batch_info(const bbe_batch *batch, int32_t *n_races, int64_t *n_competitors,
                           int64_t *total_rollouts, int32_t *max_competitors);

@@ -66,6 +66,7 @@ def lib():
             "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_autotune": [vp, vp, C.c_double, vp],
             "bbe_batch_info": [vp, vp, vp, vp, vp],
+            "bbe_batch_launches": [vp, vp],
             "bbe_rollout_noalloc": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, C.c_int, u32, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -212,6 +213,12 @@ def bbe_batch_info(batch: int) -> dict:
     nr, nc, tr, mx = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
     _check(lib().bbe_batch_info(batch, C.byref(nr), C.byref(nc), C.byref(tr), C.byref(mx)), "bbe_batch_info")
     return dict(n_races=nr.value, n_competitors=nc.value, total_rollouts=tr.value, max_competitors=mx.value)
+
+
+def bbe_batch_launches(batch: int) -> int:
+    k = C.c_int32()
+    _check(lib().bbe_batch_launches(batch, C.byref(k)), "bbe_batch_launches")
+    return k.value
 
 
 def bbe_destroy_batch(batch: int) -> None:

@@ -691,6 +691,18 @@ bbe_status bbe_batch_info(const bbe_batch *b, int32_t *n_races, int64_t *n_compe
     return BBE_OK;
 }
 
+bbe_status bbe_batch_launches(const bbe_batch *b, int32_t *kernels_per_pass)
+{
+    if (!b || !kernels_per_pass) {
+        set_error("batch or kernels_per_pass is NULL");
+        return BBE_ERR_ARG;
+    }
+    int32_t k = 0;
+    for (int g = 0; g < kGroups; ++g) k += b->n_items_v[g] > 0 ? 1 : 0;
+    *kernels_per_pass = k;
+    return BBE_OK;
+}
+
 void bbe_destroy_batch(bbe_batch *b)
 {
     if (!b) return;
