@@ -6,9 +6,9 @@
 //   forward   Y[rows][out] = X[rows][in] . W[out][in]^T on the fifth-generation tensor cores
 //             (tcgen05.mma, bfloat16 operands in shared memory, float32 accumulators in
 //             tensor memory), persistent blocks with the weights resident (sg_forward_tc).
-//   backward  dX = dY . W,   dW += dY^T . X  with mma.sync m16n8k16 (one 8-warp block per
-//             tile, warp w owns rows 16w..16w+15, operands loaded with ldmatrix, float32
-//             accumulators in registers, dW added to the float32 gradient with vector atomics).
+//   backward  dX = dY . W per tile (sg_backward_chain) and dW = dY^T . X accumulated over
+//             tiles in tensor memory, split over blocks and reduced in a fixed order
+//             (sg_backward_wgrad, sg_reduce_grad), also on tcgen05.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -34,7 +34,6 @@ constexpr int FIN = 14;       // input features in use (raw and derived)
 constexpr int RAW = 5;        // raw per-competitor quantities (range-checked at inference)
 constexpr int TILE = 128;     // rows per tile
 constexpr int MAX_STATES = 64;
-constexpr int NTHREADS = 256;
 constexpr float L_SCALE = 5000.0f;
 
 // flat parameter layout (floats)
@@ -62,13 +61,20 @@ constexpr int TC_THREADS = 512;                  // forward: two tile pipelines 
 constexpr int TC_PIPE = 256;                     // threads of one pipeline
 constexpr long long kWaitNs = 2000000000LL;      // limit of every device-side wait (2 s)
 
-// shared-memory row strides (bf16 elements): +8 keeps ldmatrix rows on distinct banks
-constexpr int LD_H = H + 8;      // 136
-constexpr int LD_2H = 2 * H + 8; // 264
-
-// per-tile training workspace (global memory)
-constexpr size_t WS_X = size_t(TILE) * KIN;   // bf16
-constexpr size_t WS_H = size_t(TILE) * H;     // bf16, one per h1, h2, h3, u
+// Training workspace of one tile (global memory, bytes).  Every [128][128] bfloat16 block is in
+// the canonical activation layout (8-row x 16-byte core matrices, row-group stride 2048 B), so
+// the backward kernels move each block with one bulk copy and read it as a tensor-core operand.
+constexpr size_t WS_BLOCK = size_t(TILE) * H * 2;           // 32 KB
+constexpr size_t WS_MASK = size_t(TILE) * (H / 32) * 4;      // 2 KB: ReLU mask bits, [row][4 words]
+constexpr size_t WS_H1 = 0;                                  // h1, h2, h3, g, u
+constexpr size_t WS_U = 4 * WS_BLOCK;
+constexpr size_t WS_G = 3 * WS_BLOCK;
+constexpr size_t WS_M = 5 * WS_BLOCK;                        // masks of h1, h2, h3, u (> 0)
+constexpr size_t WS_DU = WS_M + 4 * WS_MASK;                 // du, da3, da2, da1 (backward)
+constexpr size_t WS_DA3 = WS_DU + WS_BLOCK;
+constexpr size_t WS_DA2 = WS_DA3 + WS_BLOCK;
+constexpr size_t WS_DA1 = WS_DA2 + WS_BLOCK;
+constexpr size_t WS_TILE = WS_DA1 + WS_BLOCK;                // 303,104 bytes
 
 struct SgTile {
     int32_t s0;     // first position in the order array
@@ -99,7 +105,9 @@ struct SgArgs {
     float inv_races;       // 1 / races in the step
     float *loss_acc;       // training: mean loss accumulator (device scalar) or null
     float *grad;           // training: float32 gradient (flat layout)
-    bf16 *ws;              // training workspace, tile-major
+    unsigned char *ws;     // training workspace, WS_TILE bytes per tile
+    float *partial;        // backward: per-block weight-gradient partials [2][groups][N_PARAMS]
+    int32_t wgroups;       // backward: blocks per weight-gradient group
     float *ws_dlogit;      // training: d loss / d logit per tile row
     int train;
     unsigned char *xbuf;   // forward: per-tile features, canonical operand layout (TILE * KIN bf16)
@@ -109,122 +117,11 @@ struct SgArgs {
     long long wait_ns;     // limit of each wait
 };
 
-// ------------------------------------------------------------------ tensor-core helpers
+// ------------------------------------------------------------------ helpers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int NT>
-__device__ __forceinline__ void zero_acc(float (&acc)[NT][4])
-{
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-}
-
-// acc[16 rows][8*NT] += dY[16 rows][N] . W[N][8*NT]   (W: [reduction][out] block of [out..][in])
-template <int NT, int N>
-__device__ __forceinline__ void gemm_dyW(float (&acc)[NT][4], const bf16 *dY, int ldy, const bf16 *W, int ldw,
-                                         int lane)
-{
-#pragma unroll 2
-    for (int n0 = 0; n0 < N; n0 += 16) {
-        uint32_t a[4];
-        ldsm_x4(a, dY + (lane & 15) * ldy + n0 + (lane >> 4) * 8);
-#pragma unroll
-        for (int j = 0; j < NT; j += 2) {
-            const int mi = lane >> 3;
-            uint32_t bq[4];
-            ldsm_x4_t(bq, W + (n0 + (lane & 7) + (mi & 1) * 8) * ldw + j * 8 + (mi >> 1) * 8);
-            mma16816(acc[j], a, bq[0], bq[1]);
-            mma16816(acc[j + 1], a, bq[2], bq[3]);
-        }
-    }
-}
-
-// acc[16 outs (n0..n0+15)][8*NT] += sum over the tile's 128 rows of dY[row][n] X[row][k]
-template <int NT>
-__device__ __forceinline__ void gemm_dyT_x(float (&acc)[NT][4], const bf16 *dY, int ldy, int n0, const bf16 *X,
-                                           int ldx, int lane)
-{
-    const int mi = lane >> 3;
-#pragma unroll 2
-    for (int m0 = 0; m0 < TILE; m0 += 16) {
-        uint32_t a[4];
-        ldsm_x4_t(a, dY + (m0 + (lane & 7) + (mi >> 1) * 8) * ldy + n0 + (mi & 1) * 8);
-#pragma unroll
-        for (int j = 0; j < NT; j += 2) {
-            uint32_t bq[4];
-            ldsm_x4_t(bq, X + (m0 + (lane & 7) + (mi & 1) * 8) * ldx + j * 8 + (mi >> 1) * 8);
-            mma16816(acc[j], a, bq[0], bq[1]);
-            mma16816(acc[j + 1], a, bq[2], bq[3]);
-        }
-    }
-}
-
-// copy a [128][K] bf16 matrix (row stride K in global) into shared memory with stride ld
-template <int K>
-__device__ __forceinline__ void load_rows(bf16 *dst, int ld, const bf16 *src, int tid)
-{
-    constexpr int VPR = K / 8;  // 16-byte vectors per row
-    for (int i = tid; i < TILE * VPR; i += NTHREADS) {
-        const int r = i / VPR, v = i - r * VPR;
-        *reinterpret_cast<uint4 *>(dst + r * ld + v * 8) = *reinterpret_cast<const uint4 *>(src + size_t(r) * K + v * 8);
-    }
-}
-
-// gradient of a [128 outs][K] block: accumulator rows n0 + g (+8), columns j*8 + 2t (+1)
-template <int NT>
-__device__ __forceinline__ void atomic_add_block(float *g, int ldg, int n0, int col0, const float (&acc)[NT][4],
-                                                 int lane)
-{
-    const int gr = lane >> 2, tc = (lane & 3) * 2;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        atomicAdd(reinterpret_cast<float2 *>(g + (n0 + gr) * ldg + col0 + j * 8 + tc), make_float2(acc[j][0], acc[j][1]));
-        atomicAdd(reinterpret_cast<float2 *>(g + (n0 + gr + 8) * ldg + col0 + j * 8 + tc),
-                  make_float2(acc[j][2], acc[j][3]));
-    }
-}
-
-// column sums of a warp's 16 rows (values v[j][0..3] as in the accumulator layout), added to g
-template <int NT>
-__device__ __forceinline__ void atomic_add_colsum(float *g, const float (&v)[NT][4], int lane)
-{
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        float s0 = v[j][0] + v[j][2], s1 = v[j][1] + v[j][3];
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (lane < 4) atomicAdd(reinterpret_cast<float2 *>(g + j * 8 + lane * 2), make_float2(s0, s1));
-    }
 }
 
 // ------------------------------------------------------------------ tile bookkeeping
@@ -338,24 +235,6 @@ __device__ void tile_features(float (&f)[KIN], FeatScratch &fs, const SgArgs &a,
         f[11] = fminf(gb, 100.0f) / 10.0f;
         f[12] = (ia >= 0 && vc > fs.v[ia]) ? fminf(ga / (vc - fs.v[ia]) / fs.T[tid], 2.0f) / 2.0f : 1.0f;
         f[13] = (ib >= 0 && fs.v[ib] > vc) ? fminf(gb / (fs.v[ib] - vc) / fs.T[ib], 2.0f) / 2.0f : 1.0f;
-    }
-}
-
-// mean over each race's rows of h (bf16, stride ldh) into g (bf16, stride ldg, per row), as
-// bfloat16(sum x (1/n)) like the forward kernel; padding rows get zeros so that nothing
-// undefined reaches a matrix product
-__device__ void pool_context(bf16 *g, int ldg, const bf16 *h, int ldh, const RowMap &m, int ns, int tid)
-{
-    if (tid < H) {
-        const int col = tid;
-        for (int s = 0; s < ns; ++s) {
-            const int r0 = m.state_row0[s], r1 = m.state_row0[s + 1];
-            float sum = 0.0f;
-            for (int row = r0; row < r1; ++row) sum += __bfloat162float(h[row * ldh + col]);
-            const bf16 gv = __float2bfloat16_rn(sum * (1.0f / float(r1 - r0)));
-            for (int row = r0; row < r1; ++row) g[row * ldg + col] = gv;
-        }
-        for (int row = m.state_row0[ns]; row < TILE; ++row) g[row * ldg + col] = __float2bfloat16_rn(0.0f);
     }
 }
 
@@ -531,20 +410,32 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
 }
 
 // Epilogues.  Two threads share a tile row (its TMEM lane): thread half ch handles the 64
-// accumulator columns [64 ch, 64 ch + 64).
+// accumulator columns [64 ch, 64 ch + 64).  In training the activations also go to the
+// workspace block (same canonical offsets) and their ReLU masks (bit c mod 32 of word c / 32 of
+// the row: activation c > 0) to the mask block.
 
-// bias + ReLU -> bfloat16 into the canonical activation tile and, when training, into the
-// workspace row
-__device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
-                                                 bf16 *ws_row, int c0)
+// byte offset of row `row` in a canonical [128][128] activation block; chunk c (8 columns) is at
+// + c * 128
+__device__ __forceinline__ uint32_t act_row(int row) { return uint32_t((row >> 3) * 2048 + (row & 7) * 16); }
+
+// mask bits of a bfloat16 pair from cvt.rn.relu (the values are +0 or positive)
+__device__ __forceinline__ uint32_t pos_bits(uint32_t pk)
 {
-    unsigned char *arow = act + (row >> 3) * 2048 + (row & 7) * 16;
+    return ((pk & 0xFFFFu) != 0u ? 1u : 0u) | ((pk >> 16) != 0u ? 2u : 0u);
+}
+
+// bias + ReLU -> bfloat16 into the canonical activation tile (and the workspace block and mask)
+__device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
+                                                 unsigned char *ws_blk, uint32_t *ws_mask, int c0)
+{
+    unsigned char *arow = act + act_row(row);
 #pragma unroll
     for (int cb = c0; cb < c0 + 64; cb += 32) {
         uint32_t r[32];
         tmem_ld16<0>(r, taddr + cb);
         tmem_ld16<16>(r, taddr + cb + 16);
         tmem_wait_ld();
+        uint32_t bits = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t pk[4];
@@ -552,16 +443,20 @@ __device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bi
             for (int e = 0; e < 4; ++e) {
                 const int j = q * 8 + 2 * e;
                 pk[e] = relu_bf16x2(__uint_as_float(r[j]) + bias[cb + j], __uint_as_float(r[j + 1]) + bias[cb + j + 1]);
+                bits |= pos_bits(pk[e]) << j;
             }
             const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             *reinterpret_cast<uint4 *>(arow + ((cb >> 3) + q) * 128) = v;
-            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + cb + q * 8) = v;
+            if (ws_blk) *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) = v;
         }
+        if (ws_mask) ws_mask[row * 4 + (cb >> 5)] = bits;
     }
 }
 
-// head: u = bfloat16(relu(acc + b4)) (workspace row when training); returns this half's w5 . u
-__device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, bf16 *ws_row, int c0)
+// head: u = bfloat16(relu(acc + b4)) (workspace block and mask when training); returns this
+// half's w5 . u
+__device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, int row,
+                                                  unsigned char *ws_blk, uint32_t *ws_mask, int c0)
 {
     float s = 0.0f;
 #pragma unroll
@@ -570,6 +465,7 @@ __device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b
         tmem_ld16<0>(r, taddr + cb);
         tmem_ld16<16>(r, taddr + cb + 16);
         tmem_wait_ld();
+        uint32_t bits = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t pk[4];
@@ -578,9 +474,13 @@ __device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b
                 const int j = q * 8 + 2 * e;
                 pk[e] = relu_bf16x2(__uint_as_float(r[j]) + b4[cb + j], __uint_as_float(r[j + 1]) + b4[cb + j + 1]);
                 s += __uint_as_float(pk[e] << 16) * w5[cb + j] + __uint_as_float(pk[e] & 0xFFFF0000u) * w5[cb + j + 1];
+                bits |= pos_bits(pk[e]) << j;
             }
-            if (ws_row) *reinterpret_cast<uint4 *>(ws_row + cb + q * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            if (ws_blk)
+                *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
+        if (ws_mask) ws_mask[row * 4 + (cb >> 5)] = bits;
     }
     return s;
 }
@@ -604,8 +504,10 @@ __device__ __forceinline__ void tc_store_pool_row(uint32_t taddr_s, int r0, int 
 }
 
 // pooled sums (TMEM accumulator columns [c0, c0 + 64)) -> g = bfloat16(sum x inv_n) -> 32
-// TMEM columns of bfloat16 pairs, the A operand of the head's second product
-__device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t taddr_g, float inv_n, int c0)
+// TMEM columns of bfloat16 pairs, the A operand of the head's second product (and the
+// workspace block when training)
+__device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t taddr_g, float inv_n, int row,
+                                                 unsigned char *ws_blk, int c0)
 {
 #pragma unroll
     for (int cb = c0; cb < c0 + 64; cb += 32) {
@@ -618,6 +520,12 @@ __device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t tadd
         for (int j = 0; j < 16; ++j)
             g[j] = pack_bf16x2(__uint_as_float(r[2 * j]) * inv_n, __uint_as_float(r[2 * j + 1]) * inv_n);
         tmem_st16<0>(taddr_g + cb / 2, g);
+        if (ws_blk) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) =
+                    make_uint4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+        }
     }
 }
 
@@ -665,7 +573,7 @@ __device__ __forceinline__ void load_tile_inputs(TcPipe &P, int i, int ti, const
 }
 
 // Tile features and race layout (one 128-thread block per tile): x in the canonical operand
-// layout (and row-major into the training workspace), the tile's race layout record.
+// layout (also the training pass's x), the tile's race layout record.
 __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
 {
     __shared__ RowMap m;
@@ -682,11 +590,6 @@ __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
     unsigned char *xt = a.xbuf + size_t(ti) * (TILE * KIN * 2);
     *reinterpret_cast<uint4 *>(xt + canon_off(tid, 0, KIN)) = lo;
     *reinterpret_cast<uint4 *>(xt + canon_off(tid, 8, KIN)) = hi;
-    if (a.train) {
-        bf16 *wx = a.ws + size_t(ti) * (WS_X + 4 * WS_H) + tid * KIN;
-        *reinterpret_cast<uint4 *>(wx) = lo;
-        *reinterpret_cast<uint4 *>(wx + 8) = hi;
-    }
     TileMeta &mt = a.meta[ti];
     if (tid == 0) {
         mt.ns = t.ns;
@@ -765,7 +668,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
             *abort_flag = 1;
             atomicOr(a.status, 1);
         }
-        bf16 *ws = a.train ? a.ws + size_t(ti) * (WS_X + 4 * WS_H) : nullptr;
+        unsigned char *ws = a.train ? a.ws + size_t(ti) * WS_TILE : nullptr;
+        uint32_t *wsm = ws ? reinterpret_cast<uint32_t *>(ws + WS_M) : nullptr;  // masks of h1, h2, h3, u
         const TileMeta &mt = P.mt[ib];
 
         // layer 1: h1 = relu(W1 x + b1); the next tile's inputs are fetched meanwhile
@@ -801,7 +705,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
             tc_store_pool_row(ts, r0, r1, c0);
             tmem_wait_st();
         }
-        if (group_wait(sm, p, phase, a)) tc_epilogue_relu(td, sm.bias[0], P.act, row, ws ? ws + WS_X + row * H : nullptr, c0);
+        if (group_wait(sm, p, phase, a))
+            tc_epilogue_relu(td, sm.bias[0], P.act, row, ws ? ws + WS_H1 : nullptr, wsm, c0);
         fence_async_smem();
         tc_before_sync();
         sync();
@@ -819,7 +724,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
                 tc_commit(&sm.mbar[p]);
             }
             if (group_wait(sm, p, phase, a))
-                tc_epilogue_relu(td, sm.bias[l], P.act, row, ws ? ws + WS_X + l * WS_H + row * H : nullptr, c0);
+                tc_epilogue_relu(td, sm.bias[l], P.act, row, ws ? ws + WS_H1 + l * WS_BLOCK : nullptr,
+                                 wsm ? wsm + l * (WS_MASK / 4) : nullptr, c0);
             fence_async_smem();
             tc_before_sync();
             sync();
@@ -836,7 +742,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
                 tc_mma_ta(tmem, tmem + H + ks * 8, smem_desc(sact + ks * 4096, 2048, 128), kIdescBmn, ks > 0 ? 1u : 0u);
             tc_commit(&sm.mbar[p]);
         }
-        if (group_wait(sm, p, phase, a)) tc_epilogue_pool(td, tg, inv_n, c0);
+        if (group_wait(sm, p, phase, a)) tc_epilogue_pool(td, tg, inv_n, row, ws ? ws + WS_G : nullptr, c0);
         tmem_wait_st();
         tc_before_sync();
         sync();
@@ -857,7 +763,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
         }
         if (group_wait(sm, p, phase, a))
             P.logit_part[ch][row] =
-                tc_epilogue_head(td, sm.bias[3], sm.w5, ws ? ws + WS_X + 3 * WS_H + row * H : nullptr, c0);
+                tc_epilogue_head(td, sm.bias[3], sm.w5, row, ws ? ws + WS_U : nullptr, wsm ? wsm + 3 * (WS_MASK / 4) : nullptr,
+                                 c0);
         fence_async_smem();
         tc_before_sync();
         sync();
@@ -916,163 +823,492 @@ __global__ void sg_softmax(SgArgs a, int n_tiles)
     }
 }
 
-// ------------------------------------------------------------------ backward
+// ------------------------------------------------------------------ backward (tcgen05)
+//
+// Two persistent kernels and a reduction.  The forward pass of a training step leaves, per tile,
+// h1, h2, h3, g and u in the canonical activation layout, the ReLU masks of h1, h2, h3 and u as
+// bits, and d loss / d logit per row.
+//   sg_backward_chain   one 256-thread block per SM, W2, W3, W4 resident in shared memory,
+//                       the tile's masks and d logit by bulk copy (double-buffered):
+//                         du  = dlogit w5 [u > 0]                         (CUDA cores)
+//                         dz  = du . W4          (tcgen05, N = 256: W4 read as an MN-major B)
+//                         pooled context gradient S . dz_g (S, the race indicator, in TMEM;
+//                             dz_g rounded to bfloat16 in shared memory as an MN-major B)
+//                         da3 = (dz_h + pooled / n) [h3 > 0]
+//                         da2 = (da3 . W3) [h2 > 0],  da1 = (da2 . W2) [h1 > 0]
+//                       du, da3, da2, da1 go to the workspace in bfloat16.
+//   sg_backward_wgrad   split-K over tiles: block group 0 accumulates dW4 = du^T [h3 ; g], the
+//                       b4 gradient (du^T . 1) and the w5 gradient (u^T . dlogit, dlogit split
+//                       into two bfloat16 parts) in tensor memory over its tiles; group 1
+//                       dW3 = da3^T h2, dW2 = da2^T h1, dW1 = da1^T x and the b3, b2, b1
+//                       gradients.  The transposed operands are the workspace blocks read as
+//                       MN-major operands.  Each block writes its partial sums once.
+//   sg_reduce_grad      the float32 gradient = sum of the blocks' partials in block order.
+// The b5 gradient (sum of d logit) is added by the chain kernel.
 
-struct BwdSmem {
-    bf16 w[TILE * LD_2H];
-    bf16 dy[TILE * LD_H];
-    bf16 x[TILE * LD_2H];
-    float dg[MAX_STATES * H];
-    float dlogit[TILE];
-    RowMap m;
-};
-
-// mask by (act > 0), column sums into the bias gradient, bfloat16 into dst (this warp's rows)
-__device__ __forceinline__ void relu_grad_store(float (&acc)[16][4], const bf16 *act, int lda, bf16 *dst, int ldd,
-                                                float *gbias, int row0, const RowMap &m, int lane)
+// instruction descriptor with M = 128, N = n, bfloat16 in, float32 out; a_mn / b_mn: MN-major
+__host__ __device__ constexpr uint32_t idesc_of(int n, int a_mn, int b_mn)
 {
-    const int gr = lane >> 2, tc = (lane & 3) * 2;
-    const bool lo_ok = m.row_race[row0 + gr] >= 0, hi_ok = m.row_race[row0 + gr + 8] >= 0;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int col = j * 8 + tc;
-        const __nv_bfloat162 al = *reinterpret_cast<const __nv_bfloat162 *>(act + (row0 + gr) * lda + col);
-        const __nv_bfloat162 ah = *reinterpret_cast<const __nv_bfloat162 *>(act + (row0 + gr + 8) * lda + col);
-        acc[j][0] = (lo_ok && __low2float(al) > 0.0f) ? acc[j][0] : 0.0f;
-        acc[j][1] = (lo_ok && __high2float(al) > 0.0f) ? acc[j][1] : 0.0f;
-        acc[j][2] = (hi_ok && __low2float(ah) > 0.0f) ? acc[j][2] : 0.0f;
-        acc[j][3] = (hi_ok && __high2float(ah) > 0.0f) ? acc[j][3] : 0.0f;
-        *reinterpret_cast<__nv_bfloat162 *>(dst + (row0 + gr) * ldd + col) = __floats2bfloat162_rn(acc[j][0], acc[j][1]);
-        *reinterpret_cast<__nv_bfloat162 *>(dst + (row0 + gr + 8) * ldd + col) = __floats2bfloat162_rn(acc[j][2], acc[j][3]);
-    }
-    atomic_add_colsum(gbias, acc, lane);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a_mn) << 15) | (uint32_t(b_mn) << 16) |
+           (uint32_t(n >> 3) << 17) | (uint32_t(TILE >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) sg_backward(SgArgs a)
+// D (+)= A . B^T with both operands in shared memory and an explicit instruction descriptor
+__device__ __forceinline__ void tc_mma_d(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+struct __align__(16) BcIn {
+    uint32_t mask[4][TILE][4];  // masks of h1, h2, h3, u
+    float dlogit[TILE];
+    TileMeta mt;
+};
+static_assert(sizeof(BcIn) % 16 == 0 && sizeof(BcIn) == 4 * WS_MASK + TILE * 4 + sizeof(TileMeta), "chain inputs");
+
+struct BcSmem {
+    unsigned char w4[H * 2 * H * 2];  // canonical W4, W3, W2 (rows = outputs)
+    unsigned char w3[H * H * 2];
+    unsigned char w2[H * H * 2];
+    unsigned char buf[TILE * H * 2];  // du, then dz_g, da3, da2 (canonical activation layout)
+    BcIn in[2];
+    float w5[H];
+    int abort;
+    uint32_t tmem_base;
+    unsigned long long mbar_w, mbar, mbar_in[2];
+};
+static_assert(sizeof(BcSmem) <= 227 * 1024, "chain shared memory");
+
+__device__ __forceinline__ void load_chain_inputs(BcSmem &sm, int i, int ti, const SgArgs &a)
+{
+    mbar_expect_tx(&sm.mbar_in[i], uint32_t(sizeof(BcIn)));
+    bulk_g2s(sm.in[i].mask, a.ws + size_t(ti) * WS_TILE + WS_M, uint32_t(4 * WS_MASK), &sm.mbar_in[i]);
+    bulk_g2s(sm.in[i].dlogit, a.ws_dlogit + size_t(ti) * TILE, TILE * 4, &sm.mbar_in[i]);
+    bulk_g2s(&sm.in[i].mt, a.meta + ti, uint32_t(sizeof(TileMeta)), &sm.mbar_in[i]);
+}
+
+// wait for the block's product; a timeout flags the block and the launch
+__device__ __forceinline__ bool block_wait(unsigned long long *bar, uint32_t &phase, int *abort, const SgArgs &a)
+{
+    const bool done = __all_sync(0xffffffffu, mbar_wait(bar, phase, a.wait_ns));
+    phase ^= 1u;
+    if (!done) {
+        *reinterpret_cast<volatile int *>(abort) = 1;
+        atomicOr(a.status, 1);
+    }
+    tc_after_sync();
+    return done;
+}
+
+// 32 float32 accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr)
+{
+    tmem_ld16<0>(r, taddr);
+    tmem_ld16<16>(r, taddr + 16);
+    tmem_wait_ld();
+}
+
+__global__ void __launch_bounds__(256, 1) sg_backward_chain(SgArgs a, int n_tiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    BwdSmem &sm = *reinterpret_cast<BwdSmem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int row0 = warp * 16;
-    const SgTile t = a.tiles[blockIdx.x];
-    build_rowmap(sm.m, a, t, tid, BlockSync{});
-    const bf16 *ws = a.ws + size_t(blockIdx.x) * (WS_X + 4 * WS_H);
-    const bf16 *ws_x = ws, *ws_h1 = ws + WS_X, *ws_h2 = ws_h1 + WS_H, *ws_h3 = ws_h2 + WS_H, *ws_u = ws_h3 + WS_H;
-    float *g = a.grad;
-    if (tid < TILE) sm.dlogit[tid] = a.ws_dlogit[size_t(blockIdx.x) * TILE + tid];
-    for (int i = tid; i < MAX_STATES * H; i += NTHREADS) sm.dg[i] = 0.0f;
-    load_rows<H>(sm.x, LD_2H, ws_u, tid);
+    BcSmem &sm = *reinterpret_cast<BcSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = (warp & 3) * 32 + lane;  // TMEM lane = tile row
+    const int c0 = (warp >> 2) * 64;         // this thread's 64 columns
+    volatile int *abort_flag = &sm.abort;
+    if (tid == 0) {
+        mbar_init(&sm.mbar_w, 1);
+        mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.mbar_in[0], 1);
+        mbar_init(&sm.mbar_in[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sm.abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem_base)),
+                     "r"(4 * H)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid < H) sm.w5[tid] = a.wf[OFF_W5 + tid];
+    tc_before_sync();
     __syncthreads();
-    // head: du = dlogit w5 [u > 0]; d w5 = sum dlogit u; d b4 = sum du; d b5 = sum dlogit
-    {
-        const int col = tid & (H - 1), half = tid >> 7;
-        const float w5c = a.wf[OFF_W5 + col];
-        float sdu = 0.0f, sw5 = 0.0f;
-        for (int row = half * 64; row < half * 64 + 64; ++row) {
-            const float u = __bfloat162float(sm.x[row * LD_2H + col]);
-            const float dl = sm.dlogit[row];
-            const float du = u > 0.0f ? dl * w5c : 0.0f;
-            sdu += du;
-            sw5 += dl * u;
-            sm.dy[row * LD_H + col] = __float2bfloat16_rn(du);
+    tc_after_sync();
+    const int first = blockIdx.x, stride = gridDim.x;
+    if (tid == 0) {
+        mbar_expect_tx(&sm.mbar_w, uint32_t((WC_ELEMS - WC_W2) * 2));
+        bulk_g2s(sm.w2, a.wc + WC_W2, (WC_W3 - WC_W2) * 2, &sm.mbar_w);
+        bulk_g2s(sm.w3, a.wc + WC_W3, (WC_W4 - WC_W3) * 2, &sm.mbar_w);
+        bulk_g2s(sm.w4, a.wc + WC_W4, (WC_ELEMS - WC_W4) * 2, &sm.mbar_w);
+        if (first < n_tiles) load_chain_inputs(sm, 0, first, a);
+    }
+    // tensor memory: dz [0, 256) (dz_h, dz_g), pooled [256, 384), S [384, 448)
+    const uint32_t tmem = sm.tmem_base;
+    const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
+    const uint32_t tdz = tmem + lane_off, tpool = tmem + 256 + lane_off, ts = tmem + 384 + lane_off;
+    const uint32_t sbuf = smem_addr(sm.buf);
+    unsigned char *brow = sm.buf + act_row(row);
+    uint32_t phase = 0;
+    bool weights_ready = false;
+    int pending = first < n_tiles ? 0 : -1;
+    uint32_t pending_parity = 0;
+
+    int k = 0;
+    for (int ti = first; ti < n_tiles; ti += stride, ++k) {
+        const int ib = k & 1;
+        const bool in_ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar_in[ib], uint32_t(k >> 1) & 1u, a.wait_ns));
+        if (!in_ok) {
+            *abort_flag = 1;
+            atomicOr(a.status, 1);
         }
-        atomicAdd(g + OFF_B4 + col, sdu);
-        atomicAdd(g + OFF_W5 + col, sw5);
+        const BcIn &in = sm.in[ib];
+        unsigned char *ws = a.ws + size_t(ti) * WS_TILE;
         if (tid == 0) {
-            float s = 0.0f;
-            for (int row = 0; row < TILE; ++row) s += sm.dlogit[row];
-            atomicAdd(g + OFF_B5, s);
+            pending = -1;
+            if (in_ok && ti + stride < n_tiles) {
+                load_chain_inputs(sm, ib ^ 1, ti + stride, a);
+                pending = ib ^ 1;
+                pending_parity = uint32_t((k + 1) >> 1) & 1u;
+            }
+            if (!weights_ready && !mbar_wait(&sm.mbar_w, 0, a.wait_ns)) {
+                *abort_flag = 1;
+                atomicOr(a.status, 1);
+            }
         }
-    }
-    __syncthreads();
-    // z = [h3 ; g] -> x
-    load_rows<H>(sm.x, LD_2H, ws_h3, tid);
-    __syncthreads();
-    pool_context(sm.x + H, LD_2H, sm.x, LD_2H, sm.m, t.ns, tid);
-    load_rows<2 * H>(sm.w, LD_2H, a.wb + OFF_W4, tid);
-    __syncthreads();
-    float acc[16][4];
-    // d W4 = du^T z  (two halves of z's columns)
-    for (int half = 0; half < 2; ++half) {
-        zero_acc(acc);
-        gemm_dyT_x<16>(acc, sm.dy, LD_H, row0, sm.x + half * H, LD_2H, lane);
-        atomic_add_block(g + OFF_W4, 2 * H, row0, half * H, acc, lane);
-    }
-    // dz = du W4: the context half, summed over each race's rows
-    {
-        zero_acc(acc);
-        gemm_dyW<16, H>(acc, sm.dy + row0 * LD_H, LD_H, sm.w + H, LD_2H, lane);
-        const int gr = lane >> 2, tc = (lane & 3) * 2;
-        const int rl = row0 + gr, rh = row0 + gr + 8;
-        const int sl = sm.m.row_race[rl] >= 0 ? sm.m.row_state[rl] : -1;
-        const int sh = sm.m.row_race[rh] >= 0 ? sm.m.row_state[rh] : -1;
+        weights_ready = true;
+        // this row's part of the race indicator S (zero row for padding) and its race's 1 / n
+        float inv_n = 0.0f;
+        {
+            const int st = in_ok ? in.mt.row_state[row] : -1;
+            int r0 = 0, r1 = 0;
+            if (st >= 0) {
+                r0 = in.mt.state_row0[st];
+                r1 = in.mt.state_row0[st + 1];
+                inv_n = 1.0f / float(r1 - r0);
+            }
+            tc_store_pool_row(ts, r0, r1, c0);
+            tmem_wait_st();
+        }
+        // du = dlogit w5 [u > 0]
+        {
+            const float dl = in.dlogit[row];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = j * 8 + tc;
-            if (sl >= 0) {
-                atomicAdd(&sm.dg[sl * H + col], acc[j][0]);
-                atomicAdd(&sm.dg[sl * H + col + 1], acc[j][1]);
-            }
-            if (sh >= 0) {
-                atomicAdd(&sm.dg[sh * H + col], acc[j][2]);
-                atomicAdd(&sm.dg[sh * H + col + 1], acc[j][3]);
-            }
-        }
-    }
-    __syncthreads();
-    // the h3 half plus the pooled context's share: dh3 = dz_h3 + (1/n) sum_race dz_g, masked
-    {
-        zero_acc(acc);
-        gemm_dyW<16, H>(acc, sm.dy + row0 * LD_H, LD_H, sm.w, LD_2H, lane);
-        const int gr = lane >> 2, tc = (lane & 3) * 2;
-        const int rl = row0 + gr, rh = row0 + gr + 8;
-        const int sl = sm.m.row_race[rl] >= 0 ? sm.m.row_state[rl] : -1;
-        const int sh = sm.m.row_race[rh] >= 0 ? sm.m.row_state[rh] : -1;
-        const float il = sl >= 0 ? 1.0f / float(sm.m.state_n[sl]) : 0.0f;
-        const float ih = sh >= 0 ? 1.0f / float(sm.m.state_n[sh]) : 0.0f;
+            for (int cb = c0; cb < c0 + 64; cb += 32) {
+                const uint32_t mu4 = in.mask[3][row][cb >> 5];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = j * 8 + tc;
-            if (sl >= 0) {
-                acc[j][0] += sm.dg[sl * H + col] * il;
-                acc[j][1] += sm.dg[sl * H + col + 1] * il;
-            }
-            if (sh >= 0) {
-                acc[j][2] += sm.dg[sh * H + col] * ih;
-                acc[j][3] += sm.dg[sh * H + col + 1] * ih;
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = q * 8 + 2 * e;
+                        const float lo = (mu4 >> j) & 1u ? __fmul_rn(dl, sm.w5[cb + j]) : 0.0f;
+                        const float hi = (mu4 >> (j + 1)) & 1u ? __fmul_rn(dl, sm.w5[cb + j + 1]) : 0.0f;
+                        pk[e] = pack_bf16x2(lo, hi);
+                    }
+                    const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4 *>(brow + ((cb >> 3) + q) * 128) = v;
+                    *reinterpret_cast<uint4 *>(ws + WS_DU + act_row(row) + ((cb >> 3) + q) * 128) = v;
+                }
             }
         }
-        __syncthreads();  // every warp has read du (dW4 above and both dz halves) before dh3 replaces it
-        relu_grad_store(acc, sm.x, LD_2H, sm.dy, LD_H, g + OFF_B3, row0, sm.m, lane);
-    }
-    __syncthreads();
-    // layers 3, 2: dW = dh^T a_prev, dh_prev = (dh W) [a_prev > 0]
-    const bf16 *prev_act[2] = {ws_h2, ws_h1};
-    const int offw[2] = {OFF_W3, OFF_W2};
-    const int offb[2] = {OFF_B2, OFF_B1};
-    for (int l = 0; l < 2; ++l) {
-        load_rows<H>(sm.x, LD_2H, prev_act[l], tid);
-        load_rows<H>(sm.w, LD_H, a.wb + offw[l], tid);
+        if (tid == 0 && in_ok) {
+            float sdl = 0.0f;
+            for (int q = 0; q < TILE; ++q) sdl += in.dlogit[q];
+            atomicAdd(a.grad + OFF_B5, sdl);
+        }
+        fence_async_smem();
+        tc_before_sync();
         __syncthreads();
-        zero_acc(acc);
-        gemm_dyT_x<16>(acc, sm.dy, LD_H, row0, sm.x, LD_2H, lane);
-        atomic_add_block(g + offw[l], H, row0, 0, acc, lane);
-        zero_acc(acc);
-        gemm_dyW<16, H>(acc, sm.dy + row0 * LD_H, LD_H, sm.w, LD_H, lane);
-        __syncthreads();  // every warp has read dh before it is replaced
-        relu_grad_store(acc, sm.x, LD_2H, sm.dy, LD_H, g + offb[l], row0, sm.m, lane);
+        if (*abort_flag) break;
+
+        // dz = du . W4 (B = W4 read MN-major: rows = outputs are the reduction, inputs the N side)
+        if (tid == 0) {
+            tc_after_sync();
+            const uint32_t w4 = smem_addr(sm.w4);
+#pragma unroll
+            for (int ks = 0; ks < H / 16; ++ks)
+                tc_mma_d(tmem, smem_desc(sbuf + ks * 256, 128, 16 * 128), smem_desc(w4 + ks * 8192, 4096, 128),
+                         idesc_of(2 * H, 0, 1), ks > 0 ? 1u : 0u);
+            tc_commit(&sm.mbar);
+        }
+        if (block_wait(&sm.mbar, phase, &sm.abort, a)) {
+            // dz_g -> bfloat16 over du (the product has read it)
+#pragma unroll
+            for (int cb = c0; cb < c0 + 64; cb += 32) {
+                uint32_t r[32];
+                tmem_ld32(r, tdz + H + cb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(brow + ((cb >> 3) + q) * 128) =
+                        make_uint4(pack_bf16x2(__uint_as_float(r[8 * q]), __uint_as_float(r[8 * q + 1])),
+                                   pack_bf16x2(__uint_as_float(r[8 * q + 2]), __uint_as_float(r[8 * q + 3])),
+                                   pack_bf16x2(__uint_as_float(r[8 * q + 4]), __uint_as_float(r[8 * q + 5])),
+                                   pack_bf16x2(__uint_as_float(r[8 * q + 6]), __uint_as_float(r[8 * q + 7])));
+            }
+        }
+        fence_async_smem();
+        tc_before_sync();
         __syncthreads();
+        if (*abort_flag) break;
+
+        // per-race sums of dz_g: S . dz_g (A = S in tensor memory, B = dz_g^T read MN-major)
+        if (tid == 0) {
+            tc_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < TILE / 16; ++ks)
+                tc_mma_ta(tmem + 256, tmem + 384 + ks * 8, smem_desc(sbuf + ks * 4096, 2048, 128), kIdescBmn,
+                          ks > 0 ? 1u : 0u);
+            tc_commit(&sm.mbar);
+        }
+        if (block_wait(&sm.mbar, phase, &sm.abort, a)) {
+            // da3 = (dz_h + pooled / n) [h3 > 0]
+#pragma unroll
+            for (int cb = c0; cb < c0 + 64; cb += 32) {
+                uint32_t rz[32], rp[32];
+                tmem_ld32(rz, tdz + cb);
+                tmem_ld32(rp, tpool + cb);
+                const uint32_t m3 = in.mask[2][row][cb >> 5];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = q * 8 + 2 * e;
+                        const float lo = (m3 >> j) & 1u ? __fmaf_rn(__uint_as_float(rp[j]), inv_n, __uint_as_float(rz[j])) : 0.0f;
+                        const float hi = (m3 >> (j + 1)) & 1u
+                                             ? __fmaf_rn(__uint_as_float(rp[j + 1]), inv_n, __uint_as_float(rz[j + 1]))
+                                             : 0.0f;
+                        pk[e] = pack_bf16x2(lo, hi);
+                    }
+                    const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4 *>(brow + ((cb >> 3) + q) * 128) = v;
+                    *reinterpret_cast<uint4 *>(ws + WS_DA3 + act_row(row) + ((cb >> 3) + q) * 128) = v;
+                }
+            }
+        }
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        if (*abort_flag) break;
+
+        // da2 = (da3 . W3) [h2 > 0], then da1 = (da2 . W2) [h1 > 0]
+        for (int l = 0; l < 2; ++l) {
+            if (tid == 0) {
+                tc_after_sync();
+                const uint32_t wl = smem_addr(l == 0 ? sm.w3 : sm.w2);
+#pragma unroll
+                for (int ks = 0; ks < H / 16; ++ks)
+                    tc_mma_d(tmem, smem_desc(sbuf + ks * 256, 128, 16 * 128), smem_desc(wl + ks * 4096, 2048, 128),
+                             idesc_of(H, 0, 1), ks > 0 ? 1u : 0u);
+                tc_commit(&sm.mbar);
+            }
+            if (block_wait(&sm.mbar, phase, &sm.abort, a)) {
+#pragma unroll
+                for (int cb = c0; cb < c0 + 64; cb += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(r, tdz + cb);
+                    const uint32_t mk = in.mask[1 - l][row][cb >> 5];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = q * 8 + 2 * e;
+                            pk[e] = pack_bf16x2((mk >> j) & 1u ? __uint_as_float(r[j]) : 0.0f,
+                                                (mk >> (j + 1)) & 1u ? __uint_as_float(r[j + 1]) : 0.0f);
+                        }
+                        const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        if (l == 0) *reinterpret_cast<uint4 *>(brow + ((cb >> 3) + q) * 128) = v;
+                        *reinterpret_cast<uint4 *>(ws + (l == 0 ? WS_DA2 : WS_DA1) + act_row(row) + ((cb >> 3) + q) * 128) = v;
+                    }
+                }
+            }
+            fence_async_smem();
+            tc_before_sync();
+            __syncthreads();
+            if (*abort_flag) break;
+        }
+        if (*abort_flag) break;
     }
-    // d W1 = dh1^T x
-    for (int i = tid; i < TILE * (KIN / 8); i += NTHREADS) {
-        const int r = i / (KIN / 8), v = i - r * (KIN / 8);
-        *reinterpret_cast<uint4 *>(sm.x + r * LD_2H + v * 8) = *reinterpret_cast<const uint4 *>(ws_x + r * KIN + v * 8);
-    }
+    if (tid == 0 && pending >= 0) mbar_wait(&sm.mbar_in[pending], pending_parity, a.wait_ns);
+    if (tid == 0 && !weights_ready) mbar_wait(&sm.mbar_w, 0, a.wait_ns);
+    tc_before_sync();
     __syncthreads();
-    float acc1[2][4];
-    zero_acc(acc1);
-    gemm_dyT_x<2>(acc1, sm.dy, LD_H, row0, sm.x, LD_2H, lane);
-    atomic_add_block(g + OFF_W1, KIN, row0, 0, acc1, lane);
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(4 * H) : "memory");
+    }
+}
+
+struct BwSmem {
+    unsigned char blk[5][TILE * H * 2];  // group 0: du, h3, g, u; group 1: da3, h2, da2, h1, da1
+    unsigned char x[TILE * KIN * 2];     // group 1: x (canonical, K = 16)
+    unsigned char ones[16 * TILE * 2];   // B operand [16][128]: row 0 ones, the rest zeros
+    unsigned char dls[16 * TILE * 2];    // group 0: B operand, rows 0 and 1 the two bfloat16 parts of dlogit
+    float dlogit[TILE];
+    int abort;
+    uint32_t tmem_base;
+    unsigned long long mbar, mbar_in;
+};
+static_assert(sizeof(BwSmem) <= 227 * 1024, "weight-gradient shared memory");
+
+// byte offset of element (n, k) of a canonical K-major [16][128] operand
+__device__ __forceinline__ uint32_t nk_off(int n, int k) { return canon_off(n, k, TILE); }
+
+__global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tiles)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BwSmem &sm = *reinterpret_cast<BwSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int group = blockIdx.x / a.wgroups, cta = blockIdx.x % a.wgroups;
+    volatile int *abort_flag = &sm.abort;
+    if (tid == 0) {
+        mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.mbar_in, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sm.abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem_base)),
+                     "r"(4 * H)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // constant operands: ones in row 0, zeros elsewhere (rows 0 and 1 of dls are rewritten per tile)
+    for (int i = tid; i < 16 * TILE; i += 128) {
+        const int n = i / TILE, kk = i - n * TILE;
+        *reinterpret_cast<bf16 *>(sm.ones + nk_off(n, kk)) = __float2bfloat16_rn(n == 0 ? 1.0f : 0.0f);
+        *reinterpret_cast<bf16 *>(sm.dls + nk_off(n, kk)) = __float2bfloat16_rn(0.0f);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = sm.tmem_base;
+    const uint32_t s0 = smem_addr(sm.blk[0]), s1 = smem_addr(sm.blk[1]), s2 = smem_addr(sm.blk[2]);
+    const uint32_t s3 = smem_addr(sm.blk[3]), s4 = smem_addr(sm.blk[4]);
+    const uint32_t sx = smem_addr(sm.x), sones = smem_addr(sm.ones), sdls = smem_addr(sm.dls);
+    uint32_t phase = 0, in_phase = 0;
+    bool any = false;
+    for (int ti = cta; ti < n_tiles; ti += a.wgroups) {
+        const unsigned char *ws = a.ws + size_t(ti) * WS_TILE;
+        if (tid == 0) {
+            if (group == 0) {
+                mbar_expect_tx(&sm.mbar_in, uint32_t(4 * WS_BLOCK + TILE * 4));
+                bulk_g2s(sm.blk[0], ws + WS_DU, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[1], ws + WS_H1 + 2 * WS_BLOCK, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[2], ws + WS_G, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[3], ws + WS_U, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.dlogit, a.ws_dlogit + size_t(ti) * TILE, TILE * 4, &sm.mbar_in);
+            } else {
+                mbar_expect_tx(&sm.mbar_in, uint32_t(5 * WS_BLOCK + TILE * KIN * 2));
+                bulk_g2s(sm.blk[0], ws + WS_DA3, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[1], ws + WS_H1 + WS_BLOCK, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[2], ws + WS_DA2, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[3], ws + WS_H1, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.blk[4], ws + WS_DA1, uint32_t(WS_BLOCK), &sm.mbar_in);
+                bulk_g2s(sm.x, a.xbuf + size_t(ti) * (TILE * KIN * 2), TILE * KIN * 2, &sm.mbar_in);
+            }
+        }
+        if (!block_wait(&sm.mbar_in, in_phase, &sm.abort, a)) break;
+        if (group == 0) {
+            // d logit as two bfloat16 parts (hi + lo) in rows 0 and 1 of the B operand
+            const float dl = sm.dlogit[tid];
+            const bf16 hi = __float2bfloat16_rn(dl);
+            const bf16 lo = __float2bfloat16_rn(__fsub_rn(dl, __bfloat162float(hi)));
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(0, tid)) = hi;
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(1, tid)) = lo;
+            fence_async_smem();
+        }
+        tc_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc_after_sync();
+            const uint32_t amn = idesc_of(H, 1, 1), amn16 = idesc_of(16, 1, 0);
+#pragma unroll 1
+            for (int ks = 0; ks < TILE / 16; ++ks) {
+                const uint32_t acc = (any || ks > 0) ? 1u : 0u;
+                const uint32_t ko = uint32_t(ks) * 4096;  // 16 tile rows (the reduction) per step
+                const uint64_t ones = smem_desc(sones + ks * 256, 128, 16 * 128);
+                if (group == 0) {
+                    const uint64_t du = smem_desc(s0 + ko, 2048, 128);
+                    tc_mma_d(tmem, du, smem_desc(s1 + ko, 2048, 128), amn, acc);        // dW4[:, 0:128]
+                    tc_mma_d(tmem + 128, du, smem_desc(s2 + ko, 2048, 128), amn, acc);  // dW4[:, 128:256]
+                    tc_mma_d(tmem + 256, du, ones, amn16, acc);                          // b4
+                    tc_mma_d(tmem + 272, smem_desc(s3 + ko, 2048, 128), smem_desc(sdls + ks * 256, 128, 16 * 128), amn16,
+                             acc);                                                       // w5 (two parts)
+                } else {
+                    const uint64_t da3 = smem_desc(s0 + ko, 2048, 128), da2 = smem_desc(s2 + ko, 2048, 128);
+                    const uint64_t da1 = smem_desc(s4 + ko, 2048, 128);
+                    tc_mma_d(tmem, da3, smem_desc(s1 + ko, 2048, 128), amn, acc);        // dW3
+                    tc_mma_d(tmem + 128, da2, smem_desc(s3 + ko, 2048, 128), amn, acc);  // dW2
+                    tc_mma_d(tmem + 256, da1, smem_desc(sx + ks * 512, 256, 128), idesc_of(16, 1, 1), acc);  // dW1
+                    tc_mma_d(tmem + 272, da3, ones, amn16, acc);                          // b3
+                    tc_mma_d(tmem + 288, da2, ones, amn16, acc);                          // b2
+                    tc_mma_d(tmem + 304, da1, ones, amn16, acc);                          // b1
+                }
+            }
+            tc_commit(&sm.mbar);
+        }
+        any = true;
+        if (!block_wait(&sm.mbar, phase, &sm.abort, a)) break;  // the buffers are free again
+        tc_before_sync();
+        __syncthreads();
+        if (*abort_flag) break;
+    }
+    // this block's partial sums, one output row per thread (TMEM lane = output index)
+    if (any && !*abort_flag) {
+        const int j = (warp & 3) * 32 + (tid & 31);
+        const uint32_t tl = tmem + (uint32_t((warp & 3) * 32) << 16);
+        float *part = a.partial + (size_t(group) * a.wgroups + cta) * N_PARAMS;
+        uint32_t r[32];
+        if (group == 0) {
+            for (int c = 0; c < 2 * H; c += 32) {
+                tmem_ld32(r, tl + c);
+                for (int q = 0; q < 32; ++q) part[OFF_W4 + j * 2 * H + c + q] = __uint_as_float(r[q]);
+            }
+            tmem_ld32(r, tl + 256);
+            part[OFF_B4 + j] = __uint_as_float(r[0]);
+            part[OFF_W5 + j] = __fadd_rn(__uint_as_float(r[16]), __uint_as_float(r[17]));
+        } else {
+            for (int c = 0; c < H; c += 32) {
+                tmem_ld32(r, tl + c);
+                for (int q = 0; q < 32; ++q) part[OFF_W3 + j * H + c + q] = __uint_as_float(r[q]);
+                tmem_ld32(r, tl + 128 + c);
+                for (int q = 0; q < 32; ++q) part[OFF_W2 + j * H + c + q] = __uint_as_float(r[q]);
+            }
+            tmem_ld32(r, tl + 256);
+            for (int q = 0; q < KIN; ++q) part[OFF_W1 + j * KIN + q] = __uint_as_float(r[q]);
+            part[OFF_B3 + j] = __uint_as_float(r[16]);
+            tmem_ld32(r, tl + 288);
+            part[OFF_B2 + j] = __uint_as_float(r[0]);
+            part[OFF_B1 + j] = __uint_as_float(r[16]);
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(4 * H) : "memory");
+    }
+}
+
+// gradient[p] = sum over the owning group's blocks of their partials, in block order (b5 is
+// accumulated by the chain kernel and left alone)
+__global__ void sg_reduce_grad(float *grad, const float *partial, int wgroups)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N_PARAMS || p == OFF_B5) return;
+    const int group = (p >= OFF_W4 && p < OFF_B5) ? 0 : 1;
+    const float *src = partial + size_t(group) * wgroups * N_PARAMS + p;
+    float s = 0.0f;
+    for (int c = 0; c < wgroups; ++c) s += src[size_t(c) * N_PARAMS];
+    grad[p] = s;
 }
 
 // ------------------------------------------------------------------ optimizer
@@ -1197,9 +1433,11 @@ struct bbe_surrogate {
     size_t tiles_cap = 0;
     int32_t *d_order = nullptr;
     size_t order_cap = 0;
-    bf16 *ws = nullptr;
+    unsigned char *ws = nullptr;  // training workspace, WS_TILE bytes per tile
     float *ws_dlogit = nullptr;
     size_t ws_tiles = 0;
+    float *d_partial = nullptr;   // weight-gradient partials of the backward's blocks
+    size_t partial_cap = 0;
     float *d_loss = nullptr;
     SgRanges ranges;
     uint64_t ranges_version = 1;
@@ -1222,14 +1460,16 @@ struct bbe_surrogate {
 namespace {
 
 size_t fwd_smem() { return sizeof(TcSmem); }
-size_t bwd_smem() { return sizeof(BwdSmem); }
+size_t chain_smem() { return sizeof(BcSmem); }
+size_t wgrad_smem() { return sizeof(BwSmem); }
 
 bbe_status ensure_attrs()
 {
     static bool done = false;
     if (done) return BBE_OK;
     SG_TRY(cudaFuncSetAttribute(sg_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
-    SG_TRY(cudaFuncSetAttribute(sg_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bwd_smem())));
+    SG_TRY(cudaFuncSetAttribute(sg_backward_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(chain_smem())));
+    SG_TRY(cudaFuncSetAttribute(sg_backward_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wgrad_smem())));
     done = true;
     return BBE_OK;
 }
@@ -1272,7 +1512,7 @@ bbe_status ensure_ws(bbe_surrogate *s, size_t tiles)
     s->ws = nullptr;
     s->ws_dlogit = nullptr;
     s->ws_tiles = 0;
-    SG_TRY(cudaMalloc(&s->ws, tiles * (WS_X + 4 * WS_H) * sizeof(bf16)));
+    SG_TRY(cudaMalloc(&s->ws, tiles * WS_TILE));
     SG_TRY(cudaMalloc(&s->ws_dlogit, tiles * TILE * sizeof(float)));
     s->ws_tiles = tiles;
     return BBE_OK;
@@ -1294,7 +1534,7 @@ SgArgs base_args(const bbe_surrogate *s, const bbe_batch *b)
 
 // forward over n_tiles tiles of a.tiles/a.order: features (one block per tile), the
 // persistent tensor-core kernel (two tile pipelines per block, at most one block per SM), softmax
-bbe_status launch_forward(bbe_surrogate *s, SgArgs a, int64_t n_tiles, cudaStream_t st)
+bbe_status launch_forward(bbe_surrogate *s, SgArgs &a, int64_t n_tiles, cudaStream_t st)
 {
     if (n_tiles <= 0) return BBE_OK;
     bbe_status e;
@@ -1347,9 +1587,20 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.ws = s->ws;
     a.ws_dlogit = s->ws_dlogit;
     a.train = 1;
+    int dev = 0, sms = 0;
+    SG_TRY(cudaGetDevice(&dev));
+    SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // weight-gradient blocks per group: every block gets at least one tile
+    a.wgroups = int32_t(std::max<int64_t>(1, std::min<int64_t>(nt, std::max(1, sms / 2))));
+    if ((e = ensure_buf(s->d_partial, s->partial_cap, size_t(2) * a.wgroups * N_PARAMS))) return e;
+    a.partial = s->d_partial;
     SG_TRY(cudaMemsetAsync(s->grad, 0, N_PARAMS * sizeof(float), st));
     if ((e = launch_forward(s, a, nt, st))) return e;
-    sg_backward<<<unsigned(nt), NTHREADS, bwd_smem(), st>>>(a);
+    sg_backward_chain<<<unsigned(std::min<int64_t>(nt, sms)), 256, chain_smem(), st>>>(a, int(nt));
+    SG_TRY(cudaGetLastError());
+    sg_backward_wgrad<<<unsigned(2 * a.wgroups), 128, wgrad_smem(), st>>>(a, int(nt));
+    SG_TRY(cudaGetLastError());
+    sg_reduce_grad<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups);
     SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
@@ -1463,7 +1714,7 @@ void free_surrogate(bbe_surrogate *s)
     for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->wc,
                     (void *)s->d_status, (void *)s->d_xbuf, (void *)s->d_meta, (void *)s->d_logits, (void *)s->d_tiles,
                     (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
-                    (void *)s->d_iorder, (void *)s->d_gate})
+                    (void *)s->d_iorder, (void *)s->d_gate, (void *)s->d_partial})
         if (p) cudaFree(p);
 }
 
