@@ -1145,20 +1145,47 @@ __global__ void __launch_bounds__(256, 1) sg_backward_chain(SgArgs a, int n_tile
     }
 }
 
+constexpr uint32_t WS_HALF = uint32_t(WS_BLOCK / 2);  // 64 rows of a canonical block
+
 struct BwSmem {
-    unsigned char blk[5][TILE * H * 2];  // group 0: du, h3, g, u; group 1: da3, h2, da2, h1, da1
-    unsigned char x[TILE * KIN * 2];     // group 1: x (canonical, K = 16)
-    unsigned char ones[16 * TILE * 2];   // B operand [16][128]: row 0 ones, the rest zeros
+    // two slots, each one half (64 rows) of a tile: group 0 du, h3, g, u; group 1 da3, h2, da2,
+    // h1, da1; plus x (group 1) and d logit (group 0) of that half
+    unsigned char blk[2][5][WS_HALF];
+    unsigned char x[2][TILE * KIN];      // 64 rows of x (canonical, K = 16)
+    float dlogit[2][TILE / 2];
+    unsigned char ones[16 * TILE * 2];   // B operand [16][128 rows]: row 0 ones, the rest zeros
     unsigned char dls[16 * TILE * 2];    // group 0: B operand, rows 0 and 1 the two bfloat16 parts of dlogit
-    float dlogit[TILE];
     int abort;
     uint32_t tmem_base;
-    unsigned long long mbar, mbar_in;
+    unsigned long long mbar_mma[2], mbar_in[2];
 };
 static_assert(sizeof(BwSmem) <= 227 * 1024, "weight-gradient shared memory");
 
 // byte offset of element (n, k) of a canonical K-major [16][128] operand
 __device__ __forceinline__ uint32_t nk_off(int n, int k) { return canon_off(n, k, TILE); }
+
+// bulk copies of half u (tile a_tile, rows 64 part ..) into slot `slot`
+__device__ __forceinline__ void load_wgrad_half(BwSmem &sm, int slot, int group, int ti, int part, const SgArgs &a)
+{
+    const unsigned char *ws = a.ws + size_t(ti) * WS_TILE + size_t(part) * WS_HALF;
+    unsigned long long *bar = &sm.mbar_in[slot];
+    if (group == 0) {
+        mbar_expect_tx(bar, 4 * WS_HALF + TILE * 2);
+        bulk_g2s(sm.blk[slot][0], ws + WS_DU, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + 2 * WS_BLOCK, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][2], ws + WS_G, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][3], ws + WS_U, WS_HALF, bar);
+        bulk_g2s(sm.dlogit[slot], a.ws_dlogit + size_t(ti) * TILE + part * (TILE / 2), TILE * 2, bar);
+    } else {
+        mbar_expect_tx(bar, 5 * WS_HALF + TILE * KIN);
+        bulk_g2s(sm.blk[slot][0], ws + WS_DA3, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + WS_BLOCK, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][2], ws + WS_DA2, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][3], ws + WS_H1, WS_HALF, bar);
+        bulk_g2s(sm.blk[slot][4], ws + WS_DA1, WS_HALF, bar);
+        bulk_g2s(sm.x[slot], a.xbuf + size_t(ti) * (TILE * KIN * 2) + part * (TILE * KIN), TILE * KIN, bar);
+    }
+}
 
 __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tiles)
 {
@@ -1168,8 +1195,10 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
     const int group = blockIdx.x / a.wgroups, cta = blockIdx.x % a.wgroups;
     volatile int *abort_flag = &sm.abort;
     if (tid == 0) {
-        mbar_init(&sm.mbar, 1);
-        mbar_init(&sm.mbar_in, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.mbar_mma[i], 1);
+            mbar_init(&sm.mbar_in[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sm.abort = 0;
     }
@@ -1179,7 +1208,7 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // constant operands: ones in row 0, zeros elsewhere (rows 0 and 1 of dls are rewritten per tile)
+    // constant operands: ones in row 0, zeros elsewhere (rows 0 and 1 of dls are rewritten per half)
     for (int i = tid; i < 16 * TILE; i += 128) {
         const int n = i / TILE, kk = i - n * TILE;
         *reinterpret_cast<bf16 *>(sm.ones + nk_off(n, kk)) = __float2bfloat16_rn(n == 0 ? 1.0f : 0.0f);
@@ -1190,79 +1219,82 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = sm.tmem_base;
-    const uint32_t s0 = smem_addr(sm.blk[0]), s1 = smem_addr(sm.blk[1]), s2 = smem_addr(sm.blk[2]);
-    const uint32_t s3 = smem_addr(sm.blk[3]), s4 = smem_addr(sm.blk[4]);
-    const uint32_t sx = smem_addr(sm.x), sones = smem_addr(sm.ones), sdls = smem_addr(sm.dls);
-    uint32_t phase = 0, in_phase = 0;
-    bool any = false;
-    for (int ti = cta; ti < n_tiles; ti += a.wgroups) {
-        const unsigned char *ws = a.ws + size_t(ti) * WS_TILE;
-        if (tid == 0) {
-            if (group == 0) {
-                mbar_expect_tx(&sm.mbar_in, uint32_t(4 * WS_BLOCK + TILE * 4));
-                bulk_g2s(sm.blk[0], ws + WS_DU, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[1], ws + WS_H1 + 2 * WS_BLOCK, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[2], ws + WS_G, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[3], ws + WS_U, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.dlogit, a.ws_dlogit + size_t(ti) * TILE, TILE * 4, &sm.mbar_in);
-            } else {
-                mbar_expect_tx(&sm.mbar_in, uint32_t(5 * WS_BLOCK + TILE * KIN * 2));
-                bulk_g2s(sm.blk[0], ws + WS_DA3, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[1], ws + WS_H1 + WS_BLOCK, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[2], ws + WS_DA2, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[3], ws + WS_H1, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.blk[4], ws + WS_DA1, uint32_t(WS_BLOCK), &sm.mbar_in);
-                bulk_g2s(sm.x, a.xbuf + size_t(ti) * (TILE * KIN * 2), TILE * KIN * 2, &sm.mbar_in);
-            }
+    const uint32_t sones = smem_addr(sm.ones), sdls = smem_addr(sm.dls);
+    // this block's halves: u = 0 .. n_half-1 is half (u & 1) of its (u >> 1)-th tile
+    const int my_tiles = cta < n_tiles ? (n_tiles - 1 - cta) / a.wgroups + 1 : 0;
+    const int n_half = 2 * my_tiles;
+    uint32_t mma_phase[2] = {0u, 0u}, in_phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};          // issuing thread: a copy into the slot not yet waited for
+    uint32_t pend_parity[2] = {0u, 0u};     // and the phase it completes
+    if (tid == 0 && n_half > 0) {
+        load_wgrad_half(sm, 0, group, cta, 0, a);
+        pend[0] = true;
+        pend_parity[0] = in_phase[0];
+    }
+    int done_halves = 0;
+    for (int u = 0; u < n_half; ++u) {
+        const int slot = u & 1, part = u & 1;
+        // free the other slot (its product, half u - 1, has finished), then fetch half u + 1 into it
+        if (u >= 1 && !block_wait(&sm.mbar_mma[slot ^ 1], mma_phase[slot ^ 1], &sm.abort, a)) break;
+        if (tid == 0 && u + 1 < n_half) {
+            load_wgrad_half(sm, slot ^ 1, group, cta + ((u + 1) >> 1) * a.wgroups, (u + 1) & 1, a);
+            pend[slot ^ 1] = true;
+            pend_parity[slot ^ 1] = in_phase[slot ^ 1];
         }
-        if (!block_wait(&sm.mbar_in, in_phase, &sm.abort, a)) break;
-        if (group == 0) {
-            // d logit as two bfloat16 parts (hi + lo) in rows 0 and 1 of the B operand
-            const float dl = sm.dlogit[tid];
+        if (!block_wait(&sm.mbar_in[slot], in_phase[slot], &sm.abort, a)) break;
+        pend[slot] = false;
+        if (group == 0 && tid < TILE / 2) {
+            // d logit of these 64 rows as two bfloat16 parts (hi + lo) in rows 0 and 1 of dls
+            const float dl = sm.dlogit[slot][tid];
             const bf16 hi = __float2bfloat16_rn(dl);
             const bf16 lo = __float2bfloat16_rn(__fsub_rn(dl, __bfloat162float(hi)));
-            *reinterpret_cast<bf16 *>(sm.dls + nk_off(0, tid)) = hi;
-            *reinterpret_cast<bf16 *>(sm.dls + nk_off(1, tid)) = lo;
-            fence_async_smem();
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(0, part * 64 + tid)) = hi;
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(1, part * 64 + tid)) = lo;
         }
+        fence_async_smem();
         tc_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc_after_sync();
             const uint32_t amn = idesc_of(H, 1, 1), amn16 = idesc_of(16, 1, 0);
+            const uint32_t b0 = smem_addr(sm.blk[slot][0]), b1 = smem_addr(sm.blk[slot][1]);
+            const uint32_t b2 = smem_addr(sm.blk[slot][2]), b3 = smem_addr(sm.blk[slot][3]);
+            const uint32_t b4 = smem_addr(sm.blk[slot][4]), bx = smem_addr(sm.x[slot]);
 #pragma unroll 1
-            for (int ks = 0; ks < TILE / 16; ++ks) {
-                const uint32_t acc = (any || ks > 0) ? 1u : 0u;
-                const uint32_t ko = uint32_t(ks) * 4096;  // 16 tile rows (the reduction) per step
+            for (int kh = 0; kh < TILE / 32; ++kh) {  // 16 rows of the reduction per step
+                const int ks = part * (TILE / 32) + kh;  // the step within the tile (ones, dls)
+                const uint32_t acc = (u > 0 || kh > 0) ? 1u : 0u;
+                const uint32_t ko = uint32_t(kh) * 4096;
                 const uint64_t ones = smem_desc(sones + ks * 256, 128, 16 * 128);
                 if (group == 0) {
-                    const uint64_t du = smem_desc(s0 + ko, 2048, 128);
-                    tc_mma_d(tmem, du, smem_desc(s1 + ko, 2048, 128), amn, acc);        // dW4[:, 0:128]
-                    tc_mma_d(tmem + 128, du, smem_desc(s2 + ko, 2048, 128), amn, acc);  // dW4[:, 128:256]
+                    const uint64_t du = smem_desc(b0 + ko, 2048, 128);
+                    tc_mma_d(tmem, du, smem_desc(b1 + ko, 2048, 128), amn, acc);        // dW4[:, 0:128]
+                    tc_mma_d(tmem + 128, du, smem_desc(b2 + ko, 2048, 128), amn, acc);  // dW4[:, 128:256]
                     tc_mma_d(tmem + 256, du, ones, amn16, acc);                          // b4
-                    tc_mma_d(tmem + 272, smem_desc(s3 + ko, 2048, 128), smem_desc(sdls + ks * 256, 128, 16 * 128), amn16,
+                    tc_mma_d(tmem + 272, smem_desc(b3 + ko, 2048, 128), smem_desc(sdls + ks * 256, 128, 16 * 128), amn16,
                              acc);                                                       // w5 (two parts)
                 } else {
-                    const uint64_t da3 = smem_desc(s0 + ko, 2048, 128), da2 = smem_desc(s2 + ko, 2048, 128);
-                    const uint64_t da1 = smem_desc(s4 + ko, 2048, 128);
-                    tc_mma_d(tmem, da3, smem_desc(s1 + ko, 2048, 128), amn, acc);        // dW3
-                    tc_mma_d(tmem + 128, da2, smem_desc(s3 + ko, 2048, 128), amn, acc);  // dW2
-                    tc_mma_d(tmem + 256, da1, smem_desc(sx + ks * 512, 256, 128), idesc_of(16, 1, 1), acc);  // dW1
+                    const uint64_t da3 = smem_desc(b0 + ko, 2048, 128), da2 = smem_desc(b2 + ko, 2048, 128);
+                    const uint64_t da1 = smem_desc(b4 + ko, 2048, 128);
+                    tc_mma_d(tmem, da3, smem_desc(b1 + ko, 2048, 128), amn, acc);        // dW3
+                    tc_mma_d(tmem + 128, da2, smem_desc(b3 + ko, 2048, 128), amn, acc);  // dW2
+                    tc_mma_d(tmem + 256, da1, smem_desc(bx + kh * 512, 256, 128), idesc_of(16, 1, 1), acc);  // dW1
                     tc_mma_d(tmem + 272, da3, ones, amn16, acc);                          // b3
                     tc_mma_d(tmem + 288, da2, ones, amn16, acc);                          // b2
                     tc_mma_d(tmem + 304, da1, ones, amn16, acc);                          // b1
                 }
             }
-            tc_commit(&sm.mbar);
+            tc_commit(&sm.mbar_mma[slot]);
         }
-        any = true;
-        if (!block_wait(&sm.mbar, phase, &sm.abort, a)) break;  // the buffers are free again
-        tc_before_sync();
-        __syncthreads();
+        done_halves = u + 1;
         if (*abort_flag) break;
     }
-    // this block's partial sums, one output row per thread (TMEM lane = output index)
-    if (any && !*abort_flag) {
+    // the last product, then this block's partial sums, one output row per thread
+    bool ok = !*abort_flag;
+    if (ok && done_halves > 0) ok = block_wait(&sm.mbar_mma[(done_halves - 1) & 1], mma_phase[(done_halves - 1) & 1], &sm.abort, a);
+    for (int i = 0; i < 2; ++i)
+        if (tid == 0 && pend[i]) mbar_wait(&sm.mbar_in[i], pend_parity[i], a.wait_ns);
+    if (ok && done_halves == n_half && n_half > 0) {
         const int j = (warp & 3) * 32 + (tid & 31);
         const uint32_t tl = tmem + (uint32_t((warp & 3) * 32) << 16);
         float *part = a.partial + (size_t(group) * a.wgroups + cta) * N_PARAMS;
@@ -1570,6 +1602,24 @@ bbe_status upload_plan(bbe_surrogate *s, const std::vector<int32_t> &order, cons
     return BBE_OK;
 }
 
+// every buffer a training pass of up to max_nt tiles needs, allocated before the steps are
+// launched (a reallocation between launches would synchronise the device)
+bbe_status ensure_train_buffers(bbe_surrogate *s, int64_t max_nt)
+{
+    if (max_nt <= 0) return BBE_OK;
+    bbe_status e;
+    int dev = 0, sms = 0;
+    SG_TRY(cudaGetDevice(&dev));
+    SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if ((e = ensure_ws(s, size_t(max_nt)))) return e;
+    if ((e = ensure_buf(s->d_xbuf, s->xbuf_cap, size_t(max_nt) * TILE * KIN * sizeof(bf16)))) return e;
+    if ((e = ensure_buf(s->d_meta, s->meta_cap, size_t(max_nt)))) return e;
+    if ((e = ensure_buf(s->d_logits, s->logits_cap, size_t(max_nt) * TILE))) return e;
+    const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(max_nt, std::max(1, sms / 2)));
+    if ((e = ensure_buf(s->d_partial, s->partial_cap, size_t(2) * groups * N_PARAMS))) return e;
+    return BBE_OK;
+}
+
 // one training pass (forward + backward) over tiles [t0, t1) of the uploaded plan
 bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target, int64_t t0, int64_t t1,
                       int64_t races, float *loss_slot, cudaStream_t st)
@@ -1838,6 +1888,12 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
         s->cursor = 0;
     }
     if (loss_log) SG_TRY(cudaMemsetAsync(loss_log, 0, size_t(cfg->steps) * sizeof(float), st));
+    // plan every step of the call on the host first (per-epoch shuffle, tile packing), upload
+    // the plan once, then launch the steps back to back
+    std::vector<int32_t> all_order;
+    std::vector<SgTile> all_tiles;
+    std::vector<int64_t> tile_begin(size_t(cfg->steps) + 1, 0), races_in(size_t(cfg->steps), 0);
+    int64_t max_nt = 0;
     for (int32_t k = 0; k < cfg->steps; ++k) {
         if (s->epoch_order.empty() || s->cursor >= int64_t(s->epoch_order.size())) {
             s->epoch_order.resize(b->n_races);
@@ -1848,12 +1904,19 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
             s->cursor = 0;
         }
         const int64_t take = std::min<int64_t>(cfg->batch_states, int64_t(s->epoch_order.size()) - s->cursor);
-        std::vector<int32_t> order(s->epoch_order.begin() + s->cursor, s->epoch_order.begin() + s->cursor + take);
+        const int64_t base = int64_t(all_order.size());
+        all_order.insert(all_order.end(), s->epoch_order.begin() + s->cursor, s->epoch_order.begin() + s->cursor + take);
         s->cursor += take;
-        std::vector<SgTile> tiles;
-        pack_tiles(b->h_off, order.data(), take, 0, tiles);
-        if ((e = upload_plan(s, order, tiles, st))) return e;
-        if ((e = train_pass(s, b, target, 0, int64_t(tiles.size()), take, loss_log ? loss_log + k : nullptr, st)))
+        pack_tiles(b->h_off, all_order.data() + base, take, base, all_tiles);
+        tile_begin[size_t(k) + 1] = int64_t(all_tiles.size());
+        races_in[size_t(k)] = take;
+        max_nt = std::max<int64_t>(max_nt, tile_begin[size_t(k) + 1] - tile_begin[size_t(k)]);
+    }
+    if ((e = upload_plan(s, all_order, all_tiles, st))) return e;
+    if ((e = ensure_train_buffers(s, max_nt))) return e;
+    for (int32_t k = 0; k < cfg->steps; ++k) {
+        if ((e = train_pass(s, b, target, tile_begin[size_t(k)], tile_begin[size_t(k) + 1], races_in[size_t(k)],
+                            loss_log ? loss_log + k : nullptr, st)))
             return e;
         s->step += 1;
         const float c1 = 1.0f - std::pow(cfg->beta1, float(s->step));
