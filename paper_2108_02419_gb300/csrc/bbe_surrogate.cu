@@ -424,7 +424,8 @@ __device__ __forceinline__ uint32_t pos_bits(uint32_t pk)
     return ((pk & 0xFFFFu) != 0u ? 1u : 0u) | ((pk >> 16) != 0u ? 2u : 0u);
 }
 
-// bias + ReLU -> bfloat16 into the canonical activation tile (and the workspace block and mask)
+// bias + ReLU -> bfloat16 into the canonical activation tile (and, TRAIN, the workspace block and mask)
+template <bool TRAIN>
 __device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bias, unsigned char *act, int row,
                                                  unsigned char *ws_blk, uint32_t *ws_mask, int c0)
 {
@@ -443,18 +444,19 @@ __device__ __forceinline__ void tc_epilogue_relu(uint32_t taddr, const float *bi
             for (int e = 0; e < 4; ++e) {
                 const int j = q * 8 + 2 * e;
                 pk[e] = relu_bf16x2(__uint_as_float(r[j]) + bias[cb + j], __uint_as_float(r[j + 1]) + bias[cb + j + 1]);
-                bits |= pos_bits(pk[e]) << j;
+                if (TRAIN) bits |= pos_bits(pk[e]) << j;
             }
             const uint4 v = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             *reinterpret_cast<uint4 *>(arow + ((cb >> 3) + q) * 128) = v;
-            if (ws_blk) *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) = v;
+            if (TRAIN) *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) = v;
         }
-        if (ws_mask) ws_mask[row * 4 + (cb >> 5)] = bits;
+        if (TRAIN) ws_mask[row * 4 + (cb >> 5)] = bits;
     }
 }
 
 // head: u = bfloat16(relu(acc + b4)) (workspace block and mask when training); returns this
 // half's w5 . u
+template <bool TRAIN>
 __device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b4, const float *w5, int row,
                                                   unsigned char *ws_blk, uint32_t *ws_mask, int c0)
 {
@@ -474,13 +476,13 @@ __device__ __forceinline__ float tc_epilogue_head(uint32_t taddr, const float *b
                 const int j = q * 8 + 2 * e;
                 pk[e] = relu_bf16x2(__uint_as_float(r[j]) + b4[cb + j], __uint_as_float(r[j + 1]) + b4[cb + j + 1]);
                 s += __uint_as_float(pk[e] << 16) * w5[cb + j] + __uint_as_float(pk[e] & 0xFFFF0000u) * w5[cb + j + 1];
-                bits |= pos_bits(pk[e]) << j;
+                if (TRAIN) bits |= pos_bits(pk[e]) << j;
             }
-            if (ws_blk)
+            if (TRAIN)
                 *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) =
                     make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        if (ws_mask) ws_mask[row * 4 + (cb >> 5)] = bits;
+        if (TRAIN) ws_mask[row * 4 + (cb >> 5)] = bits;
     }
     return s;
 }
@@ -506,6 +508,7 @@ __device__ __forceinline__ void tc_store_pool_row(uint32_t taddr_s, int r0, int 
 // pooled sums (TMEM accumulator columns [c0, c0 + 64)) -> g = bfloat16(sum x inv_n) -> 32
 // TMEM columns of bfloat16 pairs, the A operand of the head's second product (and the
 // workspace block when training)
+template <bool TRAIN>
 __device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t taddr_g, float inv_n, int row,
                                                  unsigned char *ws_blk, int c0)
 {
@@ -520,7 +523,7 @@ __device__ __forceinline__ void tc_epilogue_pool(uint32_t taddr_d, uint32_t tadd
         for (int j = 0; j < 16; ++j)
             g[j] = pack_bf16x2(__uint_as_float(r[2 * j]) * inv_n, __uint_as_float(r[2 * j + 1]) * inv_n);
         tmem_st16<0>(taddr_g + cb / 2, g);
-        if (ws_blk) {
+        if (TRAIN) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 *reinterpret_cast<uint4 *>(ws_blk + act_row(row) + ((cb >> 3) + q) * 128) =
@@ -600,6 +603,7 @@ __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
     mt.row_state[tid] = int8_t(m.row_race[tid] >= 0 ? m.row_state[tid] : -1);
 }
 
+template <bool TRAIN>
 __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_tiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
             *abort_flag = 1;
             atomicOr(a.status, 1);
         }
-        unsigned char *ws = a.train ? a.ws + size_t(ti) * WS_TILE : nullptr;
+        unsigned char *ws = TRAIN ? a.ws + size_t(ti) * WS_TILE : nullptr;
         uint32_t *wsm = ws ? reinterpret_cast<uint32_t *>(ws + WS_M) : nullptr;  // masks of h1, h2, h3, u
         const TileMeta &mt = P.mt[ib];
 
@@ -706,7 +710,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
             tmem_wait_st();
         }
         if (group_wait(sm, p, phase, a))
-            tc_epilogue_relu(td, sm.bias[0], P.act, row, ws ? ws + WS_H1 : nullptr, wsm, c0);
+            tc_epilogue_relu<TRAIN>(td, sm.bias[0], P.act, row, ws ? ws + WS_H1 : nullptr, wsm, c0);
         fence_async_smem();
         tc_before_sync();
         sync();
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
                 tc_commit(&sm.mbar[p]);
             }
             if (group_wait(sm, p, phase, a))
-                tc_epilogue_relu(td, sm.bias[l], P.act, row, ws ? ws + WS_H1 + l * WS_BLOCK : nullptr,
+                tc_epilogue_relu<TRAIN>(td, sm.bias[l], P.act, row, ws ? ws + WS_H1 + l * WS_BLOCK : nullptr,
                                  wsm ? wsm + l * (WS_MASK / 4) : nullptr, c0);
             fence_async_smem();
             tc_before_sync();
@@ -742,7 +746,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
                 tc_mma_ta(tmem, tmem + H + ks * 8, smem_desc(sact + ks * 4096, 2048, 128), kIdescBmn, ks > 0 ? 1u : 0u);
             tc_commit(&sm.mbar[p]);
         }
-        if (group_wait(sm, p, phase, a)) tc_epilogue_pool(td, tg, inv_n, row, ws ? ws + WS_G : nullptr, c0);
+        if (group_wait(sm, p, phase, a)) tc_epilogue_pool<TRAIN>(td, tg, inv_n, row, ws ? ws + WS_G : nullptr, c0);
         tmem_wait_st();
         tc_before_sync();
         sync();
@@ -763,7 +767,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
         }
         if (group_wait(sm, p, phase, a))
             P.logit_part[ch][row] =
-                tc_epilogue_head(td, sm.bias[3], sm.w5, row, ws ? ws + WS_U : nullptr, wsm ? wsm + 3 * (WS_MASK / 4) : nullptr,
+                tc_epilogue_head<TRAIN>(td, sm.bias[3], sm.w5, row, ws ? ws + WS_U : nullptr, wsm ? wsm + 3 * (WS_MASK / 4) : nullptr,
                                  c0);
         fence_async_smem();
         tc_before_sync();
@@ -1499,7 +1503,8 @@ bbe_status ensure_attrs()
 {
     static bool done = false;
     if (done) return BBE_OK;
-    SG_TRY(cudaFuncSetAttribute(sg_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
+    SG_TRY(cudaFuncSetAttribute(sg_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
+    SG_TRY(cudaFuncSetAttribute(sg_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem())));
     SG_TRY(cudaFuncSetAttribute(sg_backward_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(chain_smem())));
     SG_TRY(cudaFuncSetAttribute(sg_backward_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wgrad_smem())));
     done = true;
@@ -1582,7 +1587,10 @@ bbe_status launch_forward(bbe_surrogate *s, SgArgs &a, int64_t n_tiles, cudaStre
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n_tiles + 1) / 2, sms));
     sg_prep<<<unsigned(n_tiles), TILE, 0, st>>>(a);
     SG_TRY(cudaGetLastError());
-    sg_forward_tc<<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
+    if (a.train)
+        sg_forward_tc<true><<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
+    else
+        sg_forward_tc<false><<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
     SG_TRY(cudaGetLastError());
     sg_softmax<<<unsigned((n_tiles + 7) / 8), 256, 0, st>>>(a, int(n_tiles));
     SG_TRY(cudaGetLastError());
