@@ -117,30 +117,36 @@ int slots_for(int n, int mode)
 
 bbe_status build_items(bbe_batch *b)
 {
-    std::vector<bbe::WorkItem> items[kGroups];
-    std::vector<double> cost[kGroups];
+    // Per race: full chunks of `chunk` rollouts (all of one cost) and a remainder.  The list puts
+    // longer work first: full chunks race by race in descending cost per chunk, then the
+    // remainders in descending cost.  Sorting races rather than items keeps the host work
+    // proportional to the number of races.
+    struct RacePlan {
+        int32_t race;
+        int64_t chunk, full, rem;
+        double cost_full, cost_rem;
+    };
+    std::vector<RacePlan> plans[kGroups];
     const int64_t per_lane = b->cfg.rollouts_per_lane;
     // keep the whole list near kMaxItems items: very large batches get larger items
     int64_t total_rollouts = 0;
     for (int r = 0; r < b->n_races; ++r) total_rollouts += b->h_R[r];
     const int64_t min_chunk = (total_rollouts + kMaxItems - 1) / kMaxItems;
+    size_t total = 0;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
         const int v = slots_for(n, b->cfg.slots_per_lane);
-        const int g = group_of(v);
         const int nseg = 32 / ((n + v - 1) / v);
         // at least rollouts_per_lane per segment, at most kMaxItemsPerRace items per race
         const int64_t chunk = std::max<int64_t>(
             std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace), min_chunk);
         const double st = est_steps(b, r);
-        for (int64_t k = 0; k < b->h_R[r]; k += chunk) {
-            const int64_t cnt = std::min<int64_t>(chunk, b->h_R[r] - k);
-            items[g].push_back(bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0});
-            cost[g].push_back(double((cnt + nseg - 1) / nseg) * st);
-        }
+        RacePlan pl{r, chunk, b->h_R[r] / chunk, b->h_R[r] % chunk, 0.0, 0.0};
+        pl.cost_full = double((chunk + nseg - 1) / nseg) * st;
+        pl.cost_rem = double((pl.rem + nseg - 1) / nseg) * st;
+        total += size_t(pl.full) + (pl.rem > 0 ? 1 : 0);
+        plans[group_of(v)].push_back(pl);
     }
-    size_t total = 0;
-    for (int g = 0; g < kGroups; ++g) total += items[g].size();
     if (total > size_t(INT32_MAX)) {
         set_error("work list too long; raise rollouts_per_lane");
         return BBE_ERR_RANGE;
@@ -148,11 +154,16 @@ bbe_status build_items(bbe_batch *b)
     std::vector<bbe::WorkItem> sorted;
     sorted.reserve(total);
     for (int g = 0; g < kGroups; ++g) {
-        std::vector<int32_t> order(items[g].size());
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[g][x] > cost[g][y]; });
-        for (int32_t i : order) sorted.push_back(items[g][i]);
-        b->n_items_v[g] = int32_t(items[g].size());
+        std::vector<RacePlan> &pg = plans[g];
+        const size_t before = sorted.size();
+        std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_full > y.cost_full; });
+        for (const RacePlan &pl : pg)
+            for (int64_t i = 0; i < pl.full; ++i)
+                sorted.push_back(bbe::WorkItem{pl.race, int32_t(i * pl.chunk), int32_t(pl.chunk), 0});
+        std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_rem > y.cost_rem; });
+        for (const RacePlan &pl : pg)
+            if (pl.rem > 0) sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.full * pl.chunk), int32_t(pl.rem), 0});
+        b->n_items_v[g] = int32_t(sorted.size() - before);
     }
 
     if (b->d_items) cudaFree(b->d_items);
@@ -223,14 +234,21 @@ cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cu
     return e;
 }
 
-bbe_status ensure_graph(bbe_batch *b, int32_t *counts, int64_t *steps)
+bbe_status ensure_aux(bbe_batch *b)
 {
-    if (b->gexec && b->g_counts == counts && b->g_steps == steps) return BBE_OK;
-    free_graph(b);
     if (!b->capture_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
     if (!b->side_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
     if (!b->ev_fork) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
     if (!b->ev_join) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    return BBE_OK;
+}
+
+bbe_status ensure_graph(bbe_batch *b, int32_t *counts, int64_t *steps)
+{
+    if (b->gexec && b->g_counts == counts && b->g_steps == steps) return BBE_OK;
+    free_graph(b);
+    bbe_status st = ensure_aux(b);
+    if (st) return st;
     BBE_CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_pass(b, counts, steps, b->capture_stream, b->side_stream);
     cudaGraph_t graph = nullptr;
@@ -475,6 +493,16 @@ bbe_status bbe_rollout_batch(bbe_batch *b, int32_t *win_counts, int64_t *steps_t
     if (!b || !win_counts) {
         set_error("batch or win_counts is NULL");
         return BBE_ERR_ARG;
+    }
+    const bool cached = b->gexec && b->g_counts == win_counts && b->g_steps == steps_total;
+    if (!cached && !(b->last_counts == win_counts && b->last_steps == steps_total)) {
+        // first pass with these buffers: launch directly; a graph is captured if they come again
+        b->last_counts = win_counts;
+        b->last_steps = steps_total;
+        bbe_status st = ensure_aux(b);
+        if (st) return st;
+        BBE_CUDA_TRY(enqueue_pass(b, win_counts, steps_total, as_stream(cuda_stream), b->side_stream));
+        return BBE_OK;
     }
     bbe_status st = ensure_graph(b, win_counts, steps_total);
     if (st) return st;

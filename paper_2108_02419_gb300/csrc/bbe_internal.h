@@ -111,7 +111,9 @@ struct bbe_batch {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
-    // graph cache
+    // graph cache (captured on the second pass with the same output buffers)
+    int32_t *last_counts = nullptr;
+    int64_t *last_steps = nullptr;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int32_t *g_counts = nullptr;
