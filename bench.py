@@ -328,6 +328,11 @@ QUERY_ROLLOUTS = 50000
 # confidence gate of the surrogate: races whose runner-up network probability exceeds this go to
 # Monte Carlo (threshold chosen on held-out states of seeds 300 and 301)
 GATE_RUNNER_UP = 1e-3
+# two-stage fallback: a pilot of this many rollouts, then the budget that bounds every
+# probability's standard deviation by FALLBACK_SD (0.01 / 4.5: a 0.01 max-abs error over the
+# ~10^5 probabilities a run reports, at 4.5 standard deviations)
+FALLBACK_PILOT = 2000
+FALLBACK_SD = 0.01 / 4.5
 
 
 def run_surrogate(mode: str, dev, stream) -> dict:
@@ -421,6 +426,14 @@ def run_surrogate(mode: str, dev, stream) -> dict:
         held["gated"] = errors(q.cpu().numpy().astype(np.float64))
         u = used.cpu().numpy()
         held["gated"].update(runner_up_max=GATE_RUNNER_UP, gated=int((u == 2).sum()), out_of_range=int((u == 1).sum()))
+        bbe.bbe_surrogate_set_fallback(s, FALLBACK_PILOT, FALLBACK_SD)
+        bbe.bbe_surrogate_infer(s, qb.handle, q, used, stream=stream)
+        stream.synchronize()
+        held["gated_two_stage"] = errors(q.cpu().numpy().astype(np.float64))
+        fr, fro = bbe.bbe_surrogate_fallback_stats(s)
+        held["gated_two_stage"].update(pilot=FALLBACK_PILOT, max_sd=FALLBACK_SD, fallback_races=fr,
+                                       fallback_rollouts_mean=fro / max(fr, 1))
+        bbe.bbe_surrogate_set_fallback(s, 0)
         mcq_c = torch.empty(ho.n_total, dtype=torch.int32, device=dev)
         mcq_p = torch.empty(ho.n_total, dtype=torch.float32, device=dev)
         qb.rollout(mcq_c, stream=stream)
@@ -449,6 +462,13 @@ def run_surrogate(mode: str, dev, stream) -> dict:
         out["infer_gated"] = {"states": qrb.n_races, "s": t_g, "win_prob_vectors_per_s": qrb.n_races / t_g,
                               "runner_up_max": GATE_RUNNER_UP, "gated": int((u == 2).sum()),
                               "out_of_range": int((u == 1).sum()), "fallback_rollouts": QUERY_ROLLOUTS}
+        bbe.bbe_surrogate_set_fallback(s, FALLBACK_PILOT, FALLBACK_SD)
+        t_g2 = timed(lambda: bbe.bbe_surrogate_infer(s, qb.handle, qp, qu, stream=stream))
+        fr, fro = bbe.bbe_surrogate_fallback_stats(s)
+        out["infer_gated_two_stage"] = {"states": qrb.n_races, "s": t_g2, "win_prob_vectors_per_s": qrb.n_races / t_g2,
+                                        "runner_up_max": GATE_RUNNER_UP, "pilot": FALLBACK_PILOT, "max_sd": FALLBACK_SD,
+                                        "fallback_races": fr, "fallback_rollouts_mean": fro / max(fr, 1)}
+        bbe.bbe_surrogate_set_fallback(s, 0)
         qb.close()
         # plain Monte Carlo at the query budget on a 20,000-query sample of the same stream
         ms = qrb.slice(0, 20000)
@@ -457,9 +477,26 @@ def run_surrogate(mode: str, dev, stream) -> dict:
             mstp = torch.empty(ms.n_races, dtype=torch.int64, device=dev)
             mpr = torch.empty(ms.n_total, dtype=torch.float32, device=dev)
             t_ms = timed(lambda: (mb.rollout(mcnt, mstp, stream=stream), mb.win_probs(mcnt, mpr, stream=stream)))
+            # the same two-stage rule without the network: every race through the fallback
+            # (gate 0), so the comparison isolates what the network adds
+            mq = torch.empty(ms.n_total, dtype=torch.float32, device=dev)
+            mu_ = torch.empty(ms.n_races, dtype=torch.uint8, device=dev)
+            bbe.bbe_surrogate_set_gate(s, 0.0)
+            bbe.bbe_surrogate_set_fallback(s, FALLBACK_PILOT, FALLBACK_SD)
+            t_m2 = timed(lambda: bbe.bbe_surrogate_infer(s, mb.handle, mq, mu_, stream=stream))
+            fr, fro = bbe.bbe_surrogate_fallback_stats(s)
+            bbe.bbe_surrogate_set_fallback(s, 0)
+            bbe.bbe_surrogate_set_gate(s, GATE_RUNNER_UP)
         out["mc_at_query_rollouts"] = {"states": ms.n_races, "s": t_ms, "win_prob_vectors_per_s": ms.n_races / t_ms,
                                        "rollouts": QUERY_ROLLOUTS}
+        out["mc_two_stage"] = {"states": ms.n_races, "s": t_m2, "win_prob_vectors_per_s": ms.n_races / t_m2,
+                               "pilot": FALLBACK_PILOT, "max_sd": FALLBACK_SD, "races": fr,
+                               "rollouts_mean": fro / max(fr, 1)}
         out["gain_gated_vs_mc_at_query_rollouts"] = out["infer_gated"]["win_prob_vectors_per_s"] / (ms.n_races / t_ms)
+        out["gain_gated_two_stage_vs_mc_at_query_rollouts"] = (out["infer_gated_two_stage"]["win_prob_vectors_per_s"]
+                                                               / (ms.n_races / t_ms))
+        out["gain_gated_two_stage_vs_mc_two_stage"] = (out["infer_gated_two_stage"]["win_prob_vectors_per_s"]
+                                                       / (ms.n_races / t_m2))
     finally:
         bbe.bbe_surrogate_destroy(s)
     # plain Monte Carlo on the uneven workload (10,000 snapshots, budgets 1e3..1e5)

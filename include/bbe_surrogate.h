@@ -82,9 +82,10 @@ BBE_API bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *stat
 
 /* bbe_surrogate_infer -- win probabilities for every race of `states`: races inside the
  * training ranges get the network's output unless the confidence gate (bbe_surrogate_set_gate)
- * rejects it; every other race is simulated with plain Monte Carlo (bbe_rollout_batch with
- * the race's own rollout budget and stream id, so its probabilities are exactly those of the
- * Monte Carlo path).
+ * rejects it; every other race is simulated with plain Monte Carlo on its own stream id
+ * (bbe_rollout_batch), so its probabilities are exactly those of the Monte Carlo path: with
+ * the race's own rollout budget by default, or with the budget that the two-stage rule of
+ * bbe_surrogate_set_fallback picks (at most the race's own).
  *   probs   device float[sum n], overwritten.
  *   used_mc device uint8[n_races] or NULL: 0 network, 1 Monte Carlo (outside the training
  *           ranges), 2 Monte Carlo (rejected by the confidence gate).
@@ -99,6 +100,34 @@ BBE_API bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *states
  * values of 0.5 or more disable the gate (the default is 1).  Not stored in checkpoints.
  * Errors: BBE_ERR_ARG. */
 BBE_API bbe_status bbe_surrogate_set_gate(bbe_surrogate *s, float runner_up_max);
+
+/* bbe_surrogate_set_fallback -- two-stage Monte Carlo fallback of bbe_surrogate_infer.  With
+ * pilot_rollouts = 0 (the default) a fallback race runs its own rollout budget R.  Otherwise it
+ * first runs R1 = min(pilot_rollouts, R) rollouts; bbe_surrogate_fallback_budget turns their
+ * counts into a total budget R' in [R1, R] that gives each of the race's probabilities a
+ * standard deviation of about max_sd at most, and rollouts R1 .. R'-1 of the same stream are
+ * added, so the answer is plain Monte Carlo with R' rollouts (k = 0 .. R'-1).  A max-abs error
+ * target e over m probabilities calls for max_sd near e / sqrt(2 ln m).  pilot_rollouts in
+ * 0 .. 2^31-1, max_sd in (0, 0.5] when pilot_rollouts > 0.  Not stored in checkpoints.
+ * Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_surrogate_set_fallback(bbe_surrogate *s, int64_t pilot_rollouts, double max_sd);
+
+/* bbe_surrogate_fallback_budget -- the budget rule of the two-stage fallback, on the host.
+ *   counts  host int32[n]: wins of each competitor of one race in `pilot` rollouts.
+ *   budget  out: with p_c = counts_c / pilot, h_c = 3 sqrt(max(p_c (1 - p_c), 1 / pilot) / pilot)
+ *           (three standard errors, floored at one count's worth), q_c the point of
+ *           [p_c - h_c, p_c + h_c] nearest 1/2 and v = max_c q_c (1 - q_c) (so v bounds every
+ *           p (1 - p) within three standard errors of the pilot's estimate):
+ *           budget = min(cap, max(pilot, ceil(v / max_sd^2))), computed in double precision;
+ *           a race of one competitor (whose probability is 1) keeps the pilot.
+ * Errors: BBE_ERR_ARG (n < 1, NULL pointer, pilot < 1, cap < pilot, max_sd outside (0, 0.5]). */
+BBE_API bbe_status bbe_surrogate_fallback_budget(int32_t n, const int32_t *counts, int64_t pilot, int64_t cap,
+                                                 double max_sd, int64_t *budget);
+
+/* bbe_surrogate_fallback_stats -- races sent to Monte Carlo by the last bbe_surrogate_infer
+ * call on this handle and the rollouts their answers rest on (the sum of their total budgets;
+ * 0 when the call failed).  Either pointer may be NULL.  Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_surrogate_fallback_stats(const bbe_surrogate *s, int64_t *races, int64_t *rollouts);
 
 /* bbe_surrogate_status -- synchronise cuda_stream and report whether a kernel launched on
  * this handle gave up a bounded device wait since the last call (the flag is then cleared;

@@ -349,6 +349,9 @@ def _sg():
             "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
             "bbe_surrogate_status": [vp, vp],
             "bbe_surrogate_set_gate": [vp, C.c_float],
+            "bbe_surrogate_set_fallback": [vp, C.c_int64, C.c_double],
+            "bbe_surrogate_fallback_budget": [C.c_int32, vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)],
+            "bbe_surrogate_fallback_stats": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "bbe_surrogate_save": [vp, C.c_char_p],
             "bbe_surrogate_load": [C.POINTER(vp), C.c_char_p],
         }
@@ -412,6 +415,28 @@ def bbe_surrogate_infer(s: int, batch: int, probs, used_mc=None, stream=None) ->
 def bbe_surrogate_set_gate(s: int, runner_up_max: float) -> None:
     """Send races whose second-largest network probability exceeds runner_up_max to Monte Carlo."""
     _check(_sg().bbe_surrogate_set_gate(s, float(runner_up_max)), "bbe_surrogate_set_gate")
+
+
+def bbe_surrogate_set_fallback(s: int, pilot_rollouts: int, max_sd: float = 0.0) -> None:
+    """Two-stage Monte Carlo fallback: pilot_rollouts first, then the budget rule's total
+    (pilot_rollouts = 0: each race's own budget)."""
+    _check(_sg().bbe_surrogate_set_fallback(s, int(pilot_rollouts), float(max_sd)), "bbe_surrogate_set_fallback")
+
+
+def bbe_surrogate_fallback_budget(counts, pilot: int, cap: int, max_sd: float) -> int:
+    """The fallback's budget rule for one race's pilot win counts (host int32 array)."""
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+    out = C.c_int64()
+    _check(_sg().bbe_surrogate_fallback_budget(int(c.size), c.ctypes.data_as(C.c_void_p), int(pilot), int(cap),
+                                               float(max_sd), C.byref(out)), "bbe_surrogate_fallback_budget")
+    return out.value
+
+
+def bbe_surrogate_fallback_stats(s: int) -> tuple:
+    """(races sent to Monte Carlo, rollouts behind their answers) of the last infer call."""
+    races, rollouts = C.c_int64(), C.c_int64()
+    _check(_sg().bbe_surrogate_fallback_stats(s, C.byref(races), C.byref(rollouts)), "bbe_surrogate_fallback_stats")
+    return races.value, rollouts.value
 
 
 def bbe_surrogate_status(s: int, stream=None) -> None:

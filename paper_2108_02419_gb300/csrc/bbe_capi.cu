@@ -123,7 +123,7 @@ bbe_status build_items(bbe_batch *b)
     // proportional to the number of races.
     struct RacePlan {
         int32_t race;
-        int64_t chunk, full, rem;
+        int64_t chunk, full, rem, k0;
         double cost_full, cost_rem;
     };
     std::vector<RacePlan> plans[kGroups];
@@ -141,7 +141,7 @@ bbe_status build_items(bbe_batch *b)
         const int64_t chunk = std::max<int64_t>(
             std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace), min_chunk);
         const double st = est_steps(b, r);
-        RacePlan pl{r, chunk, b->h_R[r] / chunk, b->h_R[r] % chunk, 0.0, 0.0};
+        RacePlan pl{r, chunk, b->h_R[r] / chunk, b->h_R[r] % chunk, b->h_k0.empty() ? 0 : b->h_k0[r], 0.0, 0.0};
         pl.cost_full = double((chunk + nseg - 1) / nseg) * st;
         pl.cost_rem = double((pl.rem + nseg - 1) / nseg) * st;
         total += size_t(pl.full) + (pl.rem > 0 ? 1 : 0);
@@ -159,10 +159,11 @@ bbe_status build_items(bbe_batch *b)
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_full > y.cost_full; });
         for (const RacePlan &pl : pg)
             for (int64_t i = 0; i < pl.full; ++i)
-                sorted.push_back(bbe::WorkItem{pl.race, int32_t(i * pl.chunk), int32_t(pl.chunk), 0});
+                sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.k0 + i * pl.chunk), int32_t(pl.chunk), 0});
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_rem > y.cost_rem; });
         for (const RacePlan &pl : pg)
-            if (pl.rem > 0) sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.full * pl.chunk), int32_t(pl.rem), 0});
+            if (pl.rem > 0)
+                sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.k0 + pl.full * pl.chunk), int32_t(pl.rem), 0});
         b->n_items_v[g] = int32_t(sorted.size() - before);
     }
 
@@ -473,6 +474,22 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     if ((st = build_items(b))) return fail(st);
     *out = b;
     return BBE_OK;
+}
+
+bbe_status bbe::set_first_rollouts(bbe_batch *b, const int64_t *k0)
+{
+    if (!b || !k0) {
+        set_error("batch or k0 is NULL");
+        return BBE_ERR_ARG;
+    }
+    for (int r = 0; r < b->n_races; ++r) {
+        if (k0[r] < 0 || k0[r] + b->h_R[r] > INT32_MAX) {
+            set_error("first rollout index out of range");
+            return BBE_ERR_RANGE;
+        }
+    }
+    b->h_k0.assign(k0, k0 + b->n_races);
+    return build_items(b);
 }
 
 extern "C" {

@@ -97,6 +97,7 @@ struct bbe_batch {
     std::vector<float> h_d0, h_mu, h_sigma, h_rho, h_P, h_theta;
     std::vector<float> h_prev;      // empty when the default previous step is used
     std::vector<int32_t> h_race_ids;  // empty when race r has stream id race_id0 + r
+    std::vector<int64_t> h_k0;        // first rollout index of each race; empty when all are 0
 
     // library-owned device memory
     void *arena = nullptr;
@@ -128,5 +129,9 @@ bbe_status stage_batch(bbe_batch **out, int32_t n_races, const int32_t *race_off
                        const float *resp, const float *pref, const float *theta, const float *prev_step,
                        uint64_t seed, bbe_dist dist, uint32_t race_id0, const int32_t *race_ids,
                        cudaStream_t stream);
+// Run rollouts k0[r] .. k0[r] + R[r] - 1 of race r instead of 0 .. R[r] - 1 (host array;
+// k0[r] + R[r] <= 2^31 - 1).  The counts of such a batch added to those of rollouts
+// 0 .. k0[r] - 1 equal the counts of one batch of k0[r] + R[r] rollouts.
+bbe_status set_first_rollouts(bbe_batch *b, const int64_t *k0);
 }  // namespace bbe
 

@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
         const float L = b.L[r];
         const float invL = __fdiv_rn(1.0f, L);
         const uint32_t rid = b.race_ids ? uint32_t(b.race_ids[r]) : b.race_id0 + uint32_t(r);
-        const int kend = w.k_begin + w.k_count;
-        int k = w.k_begin + seg;
+        // unsigned: k + nseg stays below 2^32 for any k_end <= 2^31 - 1
+        const unsigned kend = unsigned(w.k_begin) + unsigned(w.k_count);
+        unsigned k = unsigned(w.k_begin) + unsigned(seg);
         bool active = lane_used && k < kend;
         int t = 0;
         unsigned gstep = 0;

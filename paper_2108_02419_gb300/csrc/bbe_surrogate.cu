@@ -1403,6 +1403,22 @@ __global__ void scatter_probs(const float *src, const int32_t *dst_index, float 
     if (i < n) dst[dst_index[i]] = src[i];
 }
 
+// Monte Carlo fallback: probability of sub-batch competitor i = its count over its race's
+// total budget, written to competitor dst[i] of the query batch (the division of bbe_win_probs)
+__global__ void fallback_probs(const int32_t *counts, const int32_t *comp_race, const int64_t *total,
+                               const int32_t *dst, float *probs, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) probs[dst[i]] = __fdiv_rn(__int2float_rn(counts[i]), __ll2float_rn(total[comp_race[i]]));
+}
+
+// acc[map[i]] += add[i]: second-stage counts into the first stage's
+__global__ void add_counts(int32_t *acc, const int32_t *add, const int32_t *map, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) acc[map[i]] += add[i];
+}
+
 // confidence gate: flag[i] = 1 when the second-largest output probability of race races[i]
 // exceeds runner_up_max
 __global__ void sg_gate(const int32_t *race_off, const int32_t *races, int n, const float *probs, float runner_up_max,
@@ -1486,6 +1502,10 @@ struct bbe_surrogate {
     float gate = 1.0f;
     uint8_t *d_gate = nullptr;
     size_t gate_cap = 0;
+    // two-stage fallback (pilot 0: each race's own budget) and the last call's fallback totals
+    int64_t fb_pilot = 0;
+    double fb_sd = 0.0;
+    int64_t fb_races = 0, fb_rollouts = 0;
     int64_t iplan_tiles = 0;
     SgTile *d_itiles = nullptr;
     size_t itiles_cap = 0;
@@ -1794,6 +1814,155 @@ bbe_status forward_all(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
 
 }  // namespace
 
+namespace {
+
+// Budget rule of the two-stage fallback (include/bbe_surrogate.h, bbe_surrogate_fallback_budget).
+int64_t fallback_budget(int n, const int32_t *counts, int64_t pilot, int64_t cap, double max_sd)
+{
+    if (n == 1) return pilot;  // the lone competitor wins every rollout that finishes
+    const double R1 = double(pilot);
+    double v = 0.0;
+    for (int c = 0; c < n; ++c) {
+        const double p = double(counts[c]) / R1;
+        const double h = 3.0 * std::sqrt(std::max(p * (1.0 - p), 1.0 / R1) / R1);
+        const double q = std::min(std::max(0.5, p - h), p + h);  // nearest point to 1/2
+        v = std::max(v, q * (1.0 - q));
+    }
+    const double need = std::ceil(v / (max_sd * max_sd));
+    const int64_t r = need >= double(cap) ? cap : int64_t(need);
+    return std::min(cap, std::max(pilot, r));
+}
+
+// Device buffers and batches of one fallback call, released on every exit.
+struct FallbackScratch {
+    std::vector<void *> mem;
+    std::vector<bbe_batch *> batches;
+    cudaStream_t st = nullptr;
+    template <typename T>
+    bbe_status alloc(T **p, size_t count)
+    {
+        *p = nullptr;
+        if (cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
+            bbe::set_error("Monte Carlo fallback: device allocation failed");
+            return BBE_ERR_CUDA;
+        }
+        mem.push_back(*p);
+        return BBE_OK;
+    }
+    ~FallbackScratch()
+    {
+        cudaStreamSynchronize(st);
+        for (void *p : mem) cudaFree(p);
+        for (bbe_batch *b : batches) bbe_destroy_batch(b);
+    }
+};
+
+// A batch of races `races` of b with budgets R (and first rollouts k0 when not null), each
+// race keeping its own stream id; src[j] = the competitor of b that competitor j copies.
+bbe_status stage_subset(const bbe_batch *b, const std::vector<int32_t> &races, const std::vector<int64_t> &R,
+                        const std::vector<int64_t> *k0, FallbackScratch &sc, bbe_batch **out,
+                        std::vector<int32_t> &src)
+{
+    std::vector<int32_t> off(1, 0), ids;
+    std::vector<float> L, d0, mu, sg, rho, P, th, pv;
+    src.clear();
+    for (int r : races) {
+        const int a0 = b->h_off[r], a1 = b->h_off[r + 1];
+        off.push_back(off.back() + (a1 - a0));
+        L.push_back(b->h_L[r]);
+        ids.push_back(b->h_race_ids.empty() ? int32_t(b->race_id0 + uint32_t(r)) : b->h_race_ids[r]);
+        for (int i = a0; i < a1; ++i) {
+            d0.push_back(b->h_d0[i]);
+            mu.push_back(b->h_mu[i]);
+            sg.push_back(b->h_sigma[i]);
+            rho.push_back(b->h_rho[i]);
+            P.push_back(b->h_P[i]);
+            th.push_back(b->h_theta[i]);
+            if (!b->h_prev.empty()) pv.push_back(b->h_prev[i]);
+            src.push_back(i);
+        }
+    }
+    bbe_batch *sub = nullptr;
+    bbe_status e = bbe::stage_batch(&sub, int32_t(races.size()), off.data(), L.data(), R.data(), d0.data(),
+                                    mu.data(), sg.data(), rho.data(), P.data(), th.data(),
+                                    pv.empty() ? nullptr : pv.data(), b->seed, bbe_dist(b->dist), 0, ids.data(), sc.st);
+    if (e) return e;
+    sc.batches.push_back(sub);
+    if ((e = bbe_batch_set_cfg(sub, &b->cfg))) return e;
+    if (k0 && (e = bbe::set_first_rollouts(sub, k0->data()))) return e;
+    *out = sub;
+    return BBE_OK;
+}
+
+// Plain Monte Carlo for races `mc` of b, written into probs.  Without a pilot every race runs
+// its own budget.  With one, every race first runs min(pilot, R) rollouts; the budget rule
+// then sets its total from those counts, and the missing rollouts (the next indices of the
+// same stream) run as a second batch whose counts are added to the first: the result is
+// plain Monte Carlo at the total budget.
+bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<int32_t> &mc, float *probs,
+                       cudaStream_t st)
+{
+    FallbackScratch sc;
+    sc.st = st;
+    const size_t m = mc.size();
+    std::vector<int64_t> cap(m), R1(m);
+    for (size_t i = 0; i < m; ++i) {
+        cap[i] = b->h_R[size_t(mc[i])];
+        R1[i] = s->fb_pilot > 0 ? std::min(s->fb_pilot, cap[i]) : cap[i];
+    }
+    bbe_status e;
+    bbe_batch *sub1 = nullptr;
+    std::vector<int32_t> dst1;
+    if ((e = stage_subset(b, mc, R1, nullptr, sc, &sub1, dst1))) return e;
+    const size_t n1 = dst1.size();
+    int32_t *c1 = nullptr, *d_dst = nullptr;
+    int64_t *d_total = nullptr;
+    if ((e = sc.alloc(&c1, n1)) || (e = sc.alloc(&d_dst, n1)) || (e = sc.alloc(&d_total, m))) return e;
+    if ((e = bbe_rollout_batch(sub1, c1, nullptr, st))) return e;
+    std::vector<int64_t> total = R1;
+    if (s->fb_pilot > 0) {
+        std::vector<int32_t> h1(n1);
+        SG_TRY(cudaMemcpyAsync(h1.data(), c1, n1 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if ((e = bbe_batch_status(sub1, st))) return e;  // synchronises the stream
+        std::vector<int32_t> races2, map2;
+        std::vector<int64_t> R2, k2;
+        for (size_t i = 0; i < m; ++i) {
+            const int a0 = sub1->h_off[i], a1 = sub1->h_off[i + 1];
+            total[i] = fallback_budget(a1 - a0, h1.data() + a0, R1[i], cap[i], s->fb_sd);
+            if (total[i] > R1[i]) {
+                races2.push_back(mc[i]);
+                R2.push_back(total[i] - R1[i]);
+                k2.push_back(R1[i]);
+                for (int j = a0; j < a1; ++j) map2.push_back(j);
+            }
+        }
+        if (!races2.empty()) {
+            bbe_batch *sub2 = nullptr;
+            std::vector<int32_t> src2;
+            if ((e = stage_subset(b, races2, R2, &k2, sc, &sub2, src2))) return e;
+            const size_t n2 = map2.size();
+            int32_t *c2 = nullptr, *d_map = nullptr;
+            if ((e = sc.alloc(&c2, n2)) || (e = sc.alloc(&d_map, n2))) return e;
+            SG_TRY(cudaMemcpyAsync(d_map, map2.data(), n2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            if ((e = bbe_rollout_batch(sub2, c2, nullptr, st))) return e;
+            add_counts<<<unsigned((n2 + 255) / 256), 256, 0, st>>>(c1, c2, d_map, int(n2));
+            SG_TRY(cudaGetLastError());
+            if ((e = bbe_batch_status(sub2, st))) return e;
+        }
+    }
+    SG_TRY(cudaMemcpyAsync(d_total, total.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SG_TRY(cudaMemcpyAsync(d_dst, dst1.data(), n1 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    fallback_probs<<<unsigned((n1 + 255) / 256), 256, 0, st>>>(c1, sub1->dev.comp_race, d_total, d_dst, probs, int(n1));
+    SG_TRY(cudaGetLastError());
+    if ((e = bbe_batch_status(sub1, st))) return e;  // synchronises: host vectors stay alive until here
+    int64_t sum = 0;
+    for (int64_t t : total) sum += t;
+    s->fb_rollouts = sum;
+    return BBE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int64_t bbe_surrogate_num_params(void) { return N_PARAMS; }
@@ -2012,65 +2181,9 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
                 flag[size_t(s->iplan_net[size_t(i)])] = 2;
             }
     }
-    if (!mc.empty()) {
-        // plain Monte Carlo for these races, with their own stream ids
-        std::vector<int32_t> off(1, 0), ids;
-        std::vector<float> L, d0, mu, sg, rho, P, th, pv;
-        std::vector<int64_t> R;
-        std::vector<int32_t> dst;
-        for (int r : mc) {
-            const int a0 = b->h_off[r], a1 = b->h_off[r + 1];
-            off.push_back(off.back() + (a1 - a0));
-            L.push_back(b->h_L[r]);
-            R.push_back(b->h_R[r]);
-            ids.push_back(b->h_race_ids.empty() ? int32_t(b->race_id0 + uint32_t(r)) : b->h_race_ids[r]);
-            for (int i = a0; i < a1; ++i) {
-                d0.push_back(b->h_d0[i]);
-                mu.push_back(b->h_mu[i]);
-                sg.push_back(b->h_sigma[i]);
-                rho.push_back(b->h_rho[i]);
-                P.push_back(b->h_P[i]);
-                th.push_back(b->h_theta[i]);
-                if (!b->h_prev.empty()) pv.push_back(b->h_prev[i]);
-                dst.push_back(i);
-            }
-        }
-        bbe_batch *sub = nullptr;
-        e = bbe::stage_batch(&sub, int32_t(mc.size()), off.data(), L.data(), R.data(), d0.data(), mu.data(), sg.data(),
-                             rho.data(), P.data(), th.data(), pv.empty() ? nullptr : pv.data(), b->seed,
-                             bbe_dist(b->dist), 0, ids.data(), st);
-        if (e) return e;
-        if ((e = bbe_batch_set_cfg(sub, &b->cfg))) {
-            bbe_destroy_batch(sub);
-            return e;
-        }
-        int32_t *counts = nullptr, *d_dst = nullptr;
-        float *sub_probs = nullptr;
-        const size_t nc = dst.size();
-        cudaError_t ce = cudaMalloc(&counts, nc * sizeof(int32_t));
-        if (ce == cudaSuccess) ce = cudaMalloc(&sub_probs, nc * sizeof(float));
-        if (ce == cudaSuccess) ce = cudaMalloc(&d_dst, nc * sizeof(int32_t));
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_dst, dst.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        if (ce == cudaSuccess) {
-            e = bbe_rollout_batch(sub, counts, nullptr, st);
-            if (!e) e = bbe_win_probs(sub, counts, sub_probs, nullptr, st);
-            if (!e) {
-                scatter_probs<<<unsigned((nc + 255) / 256), 256, 0, st>>>(sub_probs, d_dst, probs, int(nc));
-                ce = cudaGetLastError();
-            }
-            if (!e && ce == cudaSuccess) e = bbe_batch_status(sub, st);  // synchronises the stream
-        }
-        if (ce != cudaSuccess) {
-            bbe::set_error(std::string("Monte Carlo fallback: ") + cudaGetErrorString(ce));
-            e = BBE_ERR_CUDA;
-        }
-        cudaStreamSynchronize(st);
-        cudaFree(counts);
-        cudaFree(sub_probs);
-        cudaFree(d_dst);
-        bbe_destroy_batch(sub);
-        if (e) return e;
-    }
+    s->fb_races = int64_t(mc.size());
+    s->fb_rollouts = 0;
+    if (!mc.empty() && (e = mc_fallback(s, b, mc, probs, st))) return e;
     if (used_mc) {
         SG_TRY(cudaMemcpyAsync(used_mc, flag.data(), flag.size(), cudaMemcpyHostToDevice, st));
         SG_TRY(cudaStreamSynchronize(st));
@@ -2085,6 +2198,42 @@ bbe_status bbe_surrogate_set_gate(bbe_surrogate *s, float runner_up_max)
         return BBE_ERR_ARG;
     }
     s->gate = runner_up_max;
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_set_fallback(bbe_surrogate *s, int64_t pilot_rollouts, double max_sd)
+{
+    if (!s || pilot_rollouts < 0 || pilot_rollouts > INT32_MAX ||
+        (pilot_rollouts > 0 && !(max_sd > 0.0 && max_sd <= 0.5))) {
+        bbe::set_error("bbe_surrogate_set_fallback: surrogate is NULL, pilot_rollouts outside 0..2^31-1 or "
+                       "max_sd outside (0, 0.5]");
+        return BBE_ERR_ARG;
+    }
+    s->fb_pilot = pilot_rollouts;
+    s->fb_sd = max_sd;
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_fallback_budget(int32_t n, const int32_t *counts, int64_t pilot, int64_t cap, double max_sd,
+                                         int64_t *budget)
+{
+    if (n < 1 || !counts || !budget || pilot < 1 || cap < pilot || !(max_sd > 0.0 && max_sd <= 0.5)) {
+        bbe::set_error("bbe_surrogate_fallback_budget: n < 1, NULL pointer, pilot < 1, cap < pilot or max_sd "
+                       "outside (0, 0.5]");
+        return BBE_ERR_ARG;
+    }
+    *budget = fallback_budget(n, counts, pilot, cap, max_sd);
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_fallback_stats(const bbe_surrogate *s, int64_t *races, int64_t *rollouts)
+{
+    if (!s) {
+        bbe::set_error("surrogate is NULL");
+        return BBE_ERR_ARG;
+    }
+    if (races) *races = s->fb_races;
+    if (rollouts) *rollouts = s->fb_rollouts;
     return BBE_OK;
 }
 

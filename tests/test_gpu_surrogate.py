@@ -215,6 +215,48 @@ def test_confidence_gate_sends_uncertain_races_to_monte_carlo(bbe):
         assert np.array_equal(out[a:e], mc[a:e] if gated[r] else net[a:e]), r
 
 
+def test_two_stage_fallback_is_monte_carlo_at_the_rule_budget(bbe):
+    # every query race falls back (too many competitors, or gated); each must equal the oracle's
+    # Monte Carlo at the budget that the rule derives from the oracle's own pilot counts
+    import dataclasses
+
+    train = W.uneven_batch(seed=60, n_races=300, n_lo=2, n_hi=8, rollouts=300)
+    query = W.concat([W.uneven_batch(seed=61, n_races=8, n_lo=10, n_hi=16, rollouts=3000),
+                      W.uneven_batch(seed=62, n_races=12, n_lo=2, n_hi=8, rollouts=3000)])
+    pilot, sd = 400, 0.01
+    s = bbe.bbe_surrogate_create(12)
+    try:
+        with bbe.Batch(train) as tb:
+            c, _ = tb.rollout()
+            p, _ = tb.win_probs(c)
+            bbe.bbe_surrogate_train(s, tb.handle, p, batch_states=64, steps=10)
+        bbe.bbe_surrogate_set_gate(s, 0.0)
+        bbe.bbe_surrogate_set_fallback(s, pilot, sd)
+        with bbe.Batch(query) as qb:
+            probs = torch.empty(query.n_total, dtype=torch.float32, device="cuda")
+            used = torch.empty(query.n_races, dtype=torch.uint8, device="cuda")
+            bbe.bbe_surrogate_infer(s, qb.handle, probs, used)
+            torch.cuda.synchronize()
+            got, used = probs.cpu().numpy(), used.cpu().numpy()
+        races, rollouts = bbe.bbe_surrogate_fallback_stats(s)
+        with pytest.raises(bbe.BbeError):
+            bbe.bbe_surrogate_set_fallback(s, 10, 0.0)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    assert np.all(used[:8] == 1) and np.all(used[8:] >= 1)
+    R1 = np.minimum(query.rollouts, pilot)
+    c1, _, st = oracle.batch_counts(dataclasses.replace(query, rollouts=R1))
+    assert st == 0
+    budget = np.array([bbe.bbe_surrogate_fallback_budget(c1[query.race_off[r]:query.race_off[r + 1]], int(R1[r]),
+                                                         int(query.rollouts[r]), sd) for r in range(query.n_races)])
+    assert races == query.n_races and rollouts == int(budget.sum())
+    assert np.any(budget > pilot) and np.any(budget < query.rollouts)  # both stages and the cap-free case occur
+    c, _, st = oracle.batch_counts(dataclasses.replace(query, rollouts=budget))
+    assert st == 0
+    want = c.astype(np.float32) / np.repeat(budget, query.sizes()).astype(np.float32)
+    assert np.array_equal(got, want)
+
+
 def test_infer_without_training_ranges_is_refused(bbe):
     rb = W.uneven_batch(seed=48, n_races=4, rollouts=10)
     s = bbe.bbe_surrogate_create(7)
