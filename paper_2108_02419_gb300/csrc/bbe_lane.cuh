@@ -25,8 +25,7 @@ __device__ __forceinline__ void lane_draw_block(float (&zc)[4], int c, int t, ui
 {
     const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, rk);
     if (DIST == BBE_DIST_NORMAL) {
-        box_muller(wd.w0, wd.w1, zc[0], zc[1]);
-        box_muller(wd.w2, wd.w3, zc[2], zc[3]);
+        box_muller2(wd, zc[0], zc[1], zc[2], zc[3]);
     } else if (DIST == BBE_DIST_UNIFORM) {
         zc[0] = uniform_z(wd.w0);
         zc[1] = uniform_z(wd.w1);

@@ -47,65 +47,79 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
     return Words4{c0, c1, c2, c3};
 }
 
-// Natural log of a positive normal float (the Box-Muller radius only needs (0, 1]).
-__device__ __forceinline__ float log_f32(float x)
+// The float arithmetic below works on two values at once (__ffma2_rn, __fadd2_rn, __fmul2_rn:
+// one instruction for both, each component rounded exactly as __fmaf_rn, __fadd_rn and
+// __fmul_rn round it), because a Philox block always feeds two Box-Muller pairs.
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
+// Natural log of two positive normal floats (the Box-Muller radius only needs (0, 1]).
+__device__ __forceinline__ float2 log_f32x2(float2 x)
 {
-    uint32_t b = __float_as_uint(x);
-    int e = int(b >> 23) - 127;
-    uint32_t mb = (b & 0x007FFFFFu) | 0x3F800000u;
-    const bool halve = mb > 0x3FB504F3u;
-    mb = halve ? mb - 0x00800000u : mb;
-    e = halve ? e + 1 : e;
-    const float f = __fsub_rn(__uint_as_float(mb), 1.0f);
-    float g = __fmaf_rn(f, -0x1.36ee94p-4f, 0x1.07eecap-3f);
-    g = __fmaf_rn(f, g, -0x1.0f4ebcp-3f);
-    g = __fmaf_rn(f, g, 0x1.228226p-3f);
-    g = __fmaf_rn(f, g, -0x1.542678p-3f);
-    g = __fmaf_rn(f, g, 0x1.99a2f8p-3f);
-    g = __fmaf_rn(f, g, -0x1.000428p-2f);
-    g = __fmaf_rn(f, g, 0x1.555552p-2f);
-    g = __fmaf_rn(f, g, -0x1.fffff8p-2f);
-    g = __fmaf_rn(f, g, 1.0f);
-    const float logm = __fmul_rn(f, g);
-    const float ef = __int2float_rn(e);
-    return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, logm));
+    uint32_t ba = __float_as_uint(x.x), bb = __float_as_uint(x.y);
+    int ea = int(ba >> 23) - 127, eb = int(bb >> 23) - 127;
+    uint32_t ma = (ba & 0x007FFFFFu) | 0x3F800000u, mb = (bb & 0x007FFFFFu) | 0x3F800000u;
+    const bool ha = ma > 0x3FB504F3u, hb = mb > 0x3FB504F3u;
+    ma = ha ? ma - 0x00800000u : ma;
+    mb = hb ? mb - 0x00800000u : mb;
+    ea = ha ? ea + 1 : ea;
+    eb = hb ? eb + 1 : eb;
+    const float2 f = __fadd2_rn(make_float2(__uint_as_float(ma), __uint_as_float(mb)), splat2(-1.0f));
+    float2 g = __ffma2_rn(f, splat2(-0x1.36ee94p-4f), splat2(0x1.07eecap-3f));
+    g = __ffma2_rn(f, g, splat2(-0x1.0f4ebcp-3f));
+    g = __ffma2_rn(f, g, splat2(0x1.228226p-3f));
+    g = __ffma2_rn(f, g, splat2(-0x1.542678p-3f));
+    g = __ffma2_rn(f, g, splat2(0x1.99a2f8p-3f));
+    g = __ffma2_rn(f, g, splat2(-0x1.000428p-2f));
+    g = __ffma2_rn(f, g, splat2(0x1.555552p-2f));
+    g = __ffma2_rn(f, g, splat2(-0x1.fffff8p-2f));
+    g = __ffma2_rn(f, g, splat2(1.0f));
+    const float2 logm = __fmul2_rn(f, g);
+    const float2 ef = make_float2(__int2float_rn(ea), __int2float_rn(eb));
+    return __ffma2_rn(ef, splat2(0x1.62e4p-1f), __ffma2_rn(ef, splat2(0x1.7f7d1cp-20f), logm));
 }
 
-// sin and cos of 2 pi m24 / 2^24.
-__device__ __forceinline__ void sincos2pi_f32(uint32_t m24, float &s_out, float &c_out)
+// sin and cos of 2 pi m / 2^24 for m = ma and m = mb.
+__device__ __forceinline__ void sincos2pi_f32x2(uint32_t ma, uint32_t mb, float2 &s_out, float2 &c_out)
 {
-    const uint32_t q = (m24 + 0x200000u) >> 22;
-    const int32_t fm = int32_t(m24) - int32_t(q << 22);
-    const float f = __fmul_rn(__int2float_rn(fm), 0x1p-24f);
-    const float y = __fmul_rn(f, f);
-    float ps = __fmaf_rn(y, 0x1.507834p+5f, -0x1.32d2ccp+6f);
-    ps = __fmaf_rn(y, ps, 0x1.466bc6p+6f);
-    ps = __fmaf_rn(y, ps, -0x1.4abbcep+5f);
-    ps = __fmaf_rn(y, ps, 0x1.921fb6p+2f);
-    const float sv = __fmul_rn(f, ps);
-    float pc = __fmaf_rn(y, -0x1.a6d1f2p+4f, 0x1.e1f506p+5f);
-    pc = __fmaf_rn(y, pc, -0x1.55d3c8p+6f);
-    pc = __fmaf_rn(y, pc, 0x1.03c1f0p+6f);
-    pc = __fmaf_rn(y, pc, -0x1.3bd3ccp+4f);
-    const float cv = __fmaf_rn(y, pc, 1.0f);
-    const uint32_t quad = q & 3u;
+    const uint32_t qa = (ma + 0x200000u) >> 22, qb = (mb + 0x200000u) >> 22;
+    const int32_t fa = int32_t(ma) - int32_t(qa << 22), fb = int32_t(mb) - int32_t(qb << 22);
+    const float2 f = __fmul2_rn(make_float2(__int2float_rn(fa), __int2float_rn(fb)), splat2(0x1p-24f));
+    const float2 y = __fmul2_rn(f, f);
+    float2 ps = __ffma2_rn(y, splat2(0x1.507834p+5f), splat2(-0x1.32d2ccp+6f));
+    ps = __ffma2_rn(y, ps, splat2(0x1.466bc6p+6f));
+    ps = __ffma2_rn(y, ps, splat2(-0x1.4abbcep+5f));
+    ps = __ffma2_rn(y, ps, splat2(0x1.921fb6p+2f));
+    const float2 sv = __fmul2_rn(f, ps);
+    float2 pc = __ffma2_rn(y, splat2(-0x1.a6d1f2p+4f), splat2(0x1.e1f506p+5f));
+    pc = __ffma2_rn(y, pc, splat2(-0x1.55d3c8p+6f));
+    pc = __ffma2_rn(y, pc, splat2(0x1.03c1f0p+6f));
+    pc = __ffma2_rn(y, pc, splat2(-0x1.3bd3ccp+4f));
+    const float2 cv = __ffma2_rn(y, pc, splat2(1.0f));
     // rotate (sin, cos) of the remainder by q quarter turns
-    const float a = (quad & 1u) ? cv : sv;   // |sin| of the result
-    const float b = (quad & 1u) ? sv : cv;   // |cos| of the result
-    s_out = (quad >= 2u) ? -a : a;
-    c_out = (quad == 1u || quad == 2u) ? -b : b;
+    const uint32_t ua = qa & 3u, ub = qb & 3u;
+    const float aa = (ua & 1u) ? cv.x : sv.x, ab = (ub & 1u) ? cv.y : sv.y;
+    const float ca = (ua & 1u) ? sv.x : cv.x, cb = (ub & 1u) ? sv.y : cv.y;
+    s_out = make_float2((ua >= 2u) ? -aa : aa, (ub >= 2u) ? -ab : ab);
+    c_out = make_float2((ua == 1u || ua == 2u) ? -ca : ca, (ub == 1u || ub == 2u) ? -cb : cb);
 }
 
-// Box-Muller pair from two Philox words: (r cos, r sin) with r = sqrt(-2 log u1),
-// u1 = ((wa >> 8) + 1) 2^-24 in (0, 1], angle 2 pi (wb >> 8) 2^-24.
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &z_cos, float &z_sin)
+// The two Box-Muller pairs of one Philox block: (z0, z1) = r (cos, sin) of (w0, w1) and
+// (z2, z3) of (w2, w3), with r = sqrt(-2 log u1), u1 = ((wa >> 8) + 1) 2^-24 in (0, 1] and
+// angle 2 pi (wb >> 8) 2^-24.
+__device__ __forceinline__ void box_muller2(const Words4 &wd, float &z0, float &z1, float &z2, float &z3)
 {
-    const float u1 = __fmul_rn(__uint2float_rn((wa >> 8) + 1u), 0x1p-24f);
-    const float radius = __fsqrt_rn(__fmul_rn(-2.0f, log_f32(u1)));
-    float sv, cv;
-    sincos2pi_f32(wb >> 8, sv, cv);
-    z_cos = __fmul_rn(radius, cv);
-    z_sin = __fmul_rn(radius, sv);
+    const float2 u1 = __fmul2_rn(make_float2(__uint2float_rn((wd.w0 >> 8) + 1u), __uint2float_rn((wd.w2 >> 8) + 1u)),
+                                 splat2(0x1p-24f));
+    const float2 m2l = __fmul2_rn(splat2(-2.0f), log_f32x2(u1));
+    const float2 radius = make_float2(__fsqrt_rn(m2l.x), __fsqrt_rn(m2l.y));
+    float2 sv, cv;
+    sincos2pi_f32x2(wd.w1 >> 8, wd.w3 >> 8, sv, cv);
+    const float2 zc = __fmul2_rn(radius, cv);
+    const float2 zs = __fmul2_rn(radius, sv);
+    z0 = zc.x;
+    z1 = zs.x;
+    z2 = zc.y;
+    z3 = zs.y;
 }
 
 __device__ __forceinline__ float uniform_z(uint32_t w)

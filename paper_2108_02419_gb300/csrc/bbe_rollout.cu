@@ -75,8 +75,7 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
     const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, rk);
     float z0, z1, z2, z3;
     if (DIST == BBE_DIST_NORMAL) {
-        box_muller(wd.w0, wd.w1, z0, z1);
-        box_muller(wd.w2, wd.w3, z2, z3);
+        box_muller2(wd, z0, z1, z2, z3);
     } else if (DIST == BBE_DIST_UNIFORM) {
         z0 = uniform_z(wd.w0);
         z1 = uniform_z(wd.w1);
