@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes: each mutant below is a copy of
 oracle/bbe_oracle.c with one deliberate error (in the oracle, on the CPU); the pin suites
-(tests/test_oracle_rng.py, tests/test_oracle_race.py, tests/test_oracle_places.py) must fail against
-every mutant."""
+(tests/test_oracle_rng.py, tests/test_oracle_race.py, tests/test_oracle_places.py,
+tests/test_oracle_trajectory.py, tests/test_oracle_preference.py) must fail against every mutant."""
 import os
 import subprocess
 import sys
@@ -37,6 +37,14 @@ MUTANTS = {
     "finished_competitors_stop": ("        if (placed >= places) break;\n        for (int c = 0; c < n; ++c) {\n",
                                   "        if (placed >= places) break;\n        for (int c = 0; c < n; ++c) {\n            if (finished[c]) continue;\n"),
     "places_short_of_n": ("int kk = places < n ? places : n;", "int kk = places < n ? places : n - 1;"),
+    "trajectory_records_start": ("if (d_traj) memcpy(d_traj + t * n, dn,", "if (d_traj) memcpy(d_traj + t * n, d,"),
+    "trajectory_ends_at_first_finisher": (
+        "int all_in = 1;\n        for (int c = 0; c < n; ++c) {\n            dn[c] = d[c] + S[c];\n"
+        "            if (!(dn[c] >= race->L)) all_in = 0;",
+        "int all_in = 0;\n        for (int c = 0; c < n; ++c) {\n            dn[c] = d[c] + S[c];\n"
+        "            if (dn[c] >= race->L) all_in = 1;"),
+    "preference_unclamped": ("if (m > 1.0f) m = 1.0f;", ";"),
+    "preference_additive": ("p = p * (1.0f - weights[i] * m);", "p = p - weights[i] * m;"),
 }
 
 
@@ -49,7 +57,10 @@ def test_pins_catch_mutant(tmp_path, name):
     msrc.write_text(src.replace(old, new, 1))
     so = oracle.compile_source(str(msrc), str(tmp_path / "libmutant.so"))
     env = dict(os.environ, BBE_ORACLE_LIB=so)
+    # the quick suites first: -x stops at the first failing pin
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_preference.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_trajectory.py"),
                           os.path.join(ROOT, "tests", "test_oracle_race.py"),
                           os.path.join(ROOT, "tests", "test_oracle_places.py"),
                           os.path.join(ROOT, "tests", "test_oracle_rng.py")],
