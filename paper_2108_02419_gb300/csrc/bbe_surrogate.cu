@@ -1149,45 +1149,51 @@ __global__ void __launch_bounds__(256, 1) sg_backward_chain(SgArgs a, int n_tile
     }
 }
 
-constexpr uint32_t WS_HALF = uint32_t(WS_BLOCK / 2);  // 64 rows of a canonical block
+// The weight-gradient kernel streams each tile through shared memory in quarters (32 rows of the
+// reduction) through WG_SLOTS slots: while the tensor cores work on quarter u (and may still be on
+// u - 1), the copies of quarters u + 1 .. u + WG_AHEAD are on their way.
+constexpr int WG_SLOTS = 4;
+constexpr int WG_AHEAD = WG_SLOTS - 2;                    // quarters fetched ahead of the one in use
+constexpr int WG_ROWS = TILE / 4;                         // rows of one quarter
+constexpr uint32_t WS_QTR = uint32_t(WS_BLOCK / 4);       // 32 rows of a canonical block
 
 struct BwSmem {
-    // two slots, each one half (64 rows) of a tile: group 0 du, h3, g, u; group 1 da3, h2, da2,
-    // h1, da1; plus x (group 1) and d logit (group 0) of that half
-    unsigned char blk[2][5][WS_HALF];
-    unsigned char x[2][TILE * KIN];      // 64 rows of x (canonical, K = 16)
-    float dlogit[2][TILE / 2];
+    // WG_SLOTS slots, each one quarter of a tile: group 0 du, h3, g, u; group 1 da3, h2, da2, h1,
+    // da1; plus x (group 1) and d logit (group 0) of that quarter
+    unsigned char blk[WG_SLOTS][5][WS_QTR];
+    unsigned char x[WG_SLOTS][WG_ROWS * KIN * 2];  // 32 rows of x (canonical, K = 16)
+    float dlogit[WG_SLOTS][WG_ROWS];
     unsigned char ones[16 * TILE * 2];   // B operand [16][128 rows]: row 0 ones, the rest zeros
     unsigned char dls[16 * TILE * 2];    // group 0: B operand, rows 0 and 1 the two bfloat16 parts of dlogit
     int abort;
     uint32_t tmem_base;
-    unsigned long long mbar_mma[2], mbar_in[2];
+    unsigned long long mbar_mma[WG_SLOTS], mbar_in[WG_SLOTS];
 };
 static_assert(sizeof(BwSmem) <= 227 * 1024, "weight-gradient shared memory");
 
 // byte offset of element (n, k) of a canonical K-major [16][128] operand
 __device__ __forceinline__ uint32_t nk_off(int n, int k) { return canon_off(n, k, TILE); }
 
-// bulk copies of half u (tile a_tile, rows 64 part ..) into slot `slot`
-__device__ __forceinline__ void load_wgrad_half(BwSmem &sm, int slot, int group, int ti, int part, const SgArgs &a)
+// bulk copies of quarter `part` (rows 32 part ..) of tile ti into slot `slot`
+__device__ __forceinline__ void load_wgrad_quarter(BwSmem &sm, int slot, int group, int ti, int part, const SgArgs &a)
 {
-    const unsigned char *ws = a.ws + size_t(ti) * WS_TILE + size_t(part) * WS_HALF;
+    const unsigned char *ws = a.ws + size_t(ti) * WS_TILE + size_t(part) * WS_QTR;
     unsigned long long *bar = &sm.mbar_in[slot];
     if (group == 0) {
-        mbar_expect_tx(bar, 4 * WS_HALF + TILE * 2);
-        bulk_g2s(sm.blk[slot][0], ws + WS_DU, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + 2 * WS_BLOCK, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][2], ws + WS_G, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][3], ws + WS_U, WS_HALF, bar);
-        bulk_g2s(sm.dlogit[slot], a.ws_dlogit + size_t(ti) * TILE + part * (TILE / 2), TILE * 2, bar);
+        mbar_expect_tx(bar, 4 * WS_QTR + WG_ROWS * 4);
+        bulk_g2s(sm.blk[slot][0], ws + WS_DU, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + 2 * WS_BLOCK, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][2], ws + WS_G, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][3], ws + WS_U, WS_QTR, bar);
+        bulk_g2s(sm.dlogit[slot], a.ws_dlogit + size_t(ti) * TILE + part * WG_ROWS, WG_ROWS * 4, bar);
     } else {
-        mbar_expect_tx(bar, 5 * WS_HALF + TILE * KIN);
-        bulk_g2s(sm.blk[slot][0], ws + WS_DA3, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + WS_BLOCK, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][2], ws + WS_DA2, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][3], ws + WS_H1, WS_HALF, bar);
-        bulk_g2s(sm.blk[slot][4], ws + WS_DA1, WS_HALF, bar);
-        bulk_g2s(sm.x[slot], a.xbuf + size_t(ti) * (TILE * KIN * 2) + part * (TILE * KIN), TILE * KIN, bar);
+        mbar_expect_tx(bar, 5 * WS_QTR + WG_ROWS * KIN * 2);
+        bulk_g2s(sm.blk[slot][0], ws + WS_DA3, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][1], ws + WS_H1 + WS_BLOCK, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][2], ws + WS_DA2, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][3], ws + WS_H1, WS_QTR, bar);
+        bulk_g2s(sm.blk[slot][4], ws + WS_DA1, WS_QTR, bar);
+        bulk_g2s(sm.x[slot], a.xbuf + size_t(ti) * (TILE * KIN * 2) + part * (WG_ROWS * KIN * 2), WG_ROWS * KIN * 2, bar);
     }
 }
 
@@ -1199,7 +1205,7 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
     const int group = blockIdx.x / a.wgroups, cta = blockIdx.x % a.wgroups;
     volatile int *abort_flag = &sm.abort;
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < WG_SLOTS; ++i) {
             mbar_init(&sm.mbar_mma[i], 1);
             mbar_init(&sm.mbar_in[i], 1);
         }
@@ -1212,7 +1218,7 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // constant operands: ones in row 0, zeros elsewhere (rows 0 and 1 of dls are rewritten per half)
+    // constant operands: ones in row 0, zeros elsewhere (rows 0 and 1 of dls are rewritten per quarter)
     for (int i = tid; i < 16 * TILE; i += 128) {
         const int n = i / TILE, kk = i - n * TILE;
         *reinterpret_cast<bf16 *>(sm.ones + nk_off(n, kk)) = __float2bfloat16_rn(n == 0 ? 1.0f : 0.0f);
@@ -1224,36 +1230,50 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
     tc_after_sync();
     const uint32_t tmem = sm.tmem_base;
     const uint32_t sones = smem_addr(sm.ones), sdls = smem_addr(sm.dls);
-    // this block's halves: u = 0 .. n_half-1 is half (u & 1) of its (u >> 1)-th tile
+    // this block's quarters: u = 0 .. n_q-1 is quarter (u & 3) of its (u >> 2)-th tile
     const int my_tiles = cta < n_tiles ? (n_tiles - 1 - cta) / a.wgroups + 1 : 0;
-    const int n_half = 2 * my_tiles;
-    uint32_t mma_phase[2] = {0u, 0u}, in_phase[2] = {0u, 0u};
-    bool pend[2] = {false, false};          // issuing thread: a copy into the slot not yet waited for
-    uint32_t pend_parity[2] = {0u, 0u};     // and the phase it completes
-    if (tid == 0 && n_half > 0) {
-        load_wgrad_half(sm, 0, group, cta, 0, a);
-        pend[0] = true;
-        pend_parity[0] = in_phase[0];
-    }
-    int done_halves = 0;
-    for (int u = 0; u < n_half; ++u) {
-        const int slot = u & 1, part = u & 1;
-        // free the other slot (its product, half u - 1, has finished), then fetch half u + 1 into it
-        if (u >= 1 && !block_wait(&sm.mbar_mma[slot ^ 1], mma_phase[slot ^ 1], &sm.abort, a)) break;
-        if (tid == 0 && u + 1 < n_half) {
-            load_wgrad_half(sm, slot ^ 1, group, cta + ((u + 1) >> 1) * a.wgroups, (u + 1) & 1, a);
-            pend[slot ^ 1] = true;
-            pend_parity[slot ^ 1] = in_phase[slot ^ 1];
+    const int n_q = 4 * my_tiles;
+    // per slot, one bit each (registers, not an indexed array): the phase of its product and copy
+    // barriers, and (issuing thread) a copy not yet waited for with the phase it completes
+    uint32_t mma_bits = 0u, in_bits = 0u, pend_bits = 0u, pend_par = 0u;
+    auto wait_slot = [&](unsigned long long *bar, uint32_t &bits, int i) {
+        uint32_t ph = (bits >> i) & 1u;
+        const bool done = block_wait(bar, ph, &sm.abort, a);
+        bits ^= 1u << i;
+        return done;
+    };
+    auto note_copy = [&](int i) {
+        pend_bits |= 1u << i;
+        pend_par = (pend_par & ~(1u << i)) | (in_bits & (1u << i));
+    };
+    if (tid == 0) {
+        for (int u = 0; u < WG_AHEAD && u < n_q; ++u) {
+            load_wgrad_quarter(sm, u, group, cta + (u >> 2) * a.wgroups, u & 3, a);
+            note_copy(u);
         }
-        if (!block_wait(&sm.mbar_in[slot], in_phase[slot], &sm.abort, a)) break;
-        pend[slot] = false;
-        if (group == 0 && tid < TILE / 2) {
-            // d logit of these 64 rows as two bfloat16 parts (hi + lo) in rows 0 and 1 of dls
+    }
+    int done_q = 0;
+    for (int u = 0; u < n_q; ++u) {
+        const int slot = u % WG_SLOTS, part = u & 3;
+        // fetch quarter u + WG_AHEAD into the slot of quarter u + WG_AHEAD - WG_SLOTS, once that
+        // quarter's product has finished (the product of u - 1 may still be running)
+        const int nxt = u + WG_AHEAD, nslot = nxt % WG_SLOTS;
+        if (nxt < n_q) {
+            if (nxt >= WG_SLOTS && !wait_slot(&sm.mbar_mma[nslot], mma_bits, nslot)) break;
+            if (tid == 0) {
+                load_wgrad_quarter(sm, nslot, group, cta + (nxt >> 2) * a.wgroups, nxt & 3, a);
+                note_copy(nslot);
+            }
+        }
+        if (!wait_slot(&sm.mbar_in[slot], in_bits, slot)) break;
+        pend_bits &= ~(1u << slot);
+        if (group == 0 && tid < WG_ROWS) {
+            // d logit of these 32 rows as two bfloat16 parts (hi + lo) in rows 0 and 1 of dls
             const float dl = sm.dlogit[slot][tid];
             const bf16 hi = __float2bfloat16_rn(dl);
             const bf16 lo = __float2bfloat16_rn(__fsub_rn(dl, __bfloat162float(hi)));
-            *reinterpret_cast<bf16 *>(sm.dls + nk_off(0, part * 64 + tid)) = hi;
-            *reinterpret_cast<bf16 *>(sm.dls + nk_off(1, part * 64 + tid)) = lo;
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(0, part * WG_ROWS + tid)) = hi;
+            *reinterpret_cast<bf16 *>(sm.dls + nk_off(1, part * WG_ROWS + tid)) = lo;
         }
         fence_async_smem();
         tc_before_sync();
@@ -1265,8 +1285,8 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
             const uint32_t b2 = smem_addr(sm.blk[slot][2]), b3 = smem_addr(sm.blk[slot][3]);
             const uint32_t b4 = smem_addr(sm.blk[slot][4]), bx = smem_addr(sm.x[slot]);
 #pragma unroll 1
-            for (int kh = 0; kh < TILE / 32; ++kh) {  // 16 rows of the reduction per step
-                const int ks = part * (TILE / 32) + kh;  // the step within the tile (ones, dls)
+            for (int kh = 0; kh < WG_ROWS / 16; ++kh) {  // 16 rows of the reduction per step
+                const int ks = part * (WG_ROWS / 16) + kh;  // the step within the tile (ones, dls)
                 const uint32_t acc = (u > 0 || kh > 0) ? 1u : 0u;
                 const uint32_t ko = uint32_t(kh) * 4096;
                 const uint64_t ones = smem_desc(sones + ks * 256, 128, 16 * 128);
@@ -1290,15 +1310,18 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
             }
             tc_commit(&sm.mbar_mma[slot]);
         }
-        done_halves = u + 1;
+        done_q = u + 1;
         if (*abort_flag) break;
     }
     // the last product, then this block's partial sums, one output row per thread
     bool ok = !*abort_flag;
-    if (ok && done_halves > 0) ok = block_wait(&sm.mbar_mma[(done_halves - 1) & 1], mma_phase[(done_halves - 1) & 1], &sm.abort, a);
-    for (int i = 0; i < 2; ++i)
-        if (tid == 0 && pend[i]) mbar_wait(&sm.mbar_in[i], pend_parity[i], a.wait_ns);
-    if (ok && done_halves == n_half && n_half > 0) {
+    const int last = (done_q + WG_SLOTS - 1) % WG_SLOTS;
+    if (ok && done_q > 0) ok = wait_slot(&sm.mbar_mma[last], mma_bits, last);
+    else if (tid == 0 && done_q > 0)  // given up: let the products already issued finish (bounded)
+        mbar_wait(&sm.mbar_mma[last], (mma_bits >> last) & 1u, a.wait_ns);
+    for (int i = 0; i < WG_SLOTS; ++i)
+        if (tid == 0 && ((pend_bits >> i) & 1u)) mbar_wait(&sm.mbar_in[i], (pend_par >> i) & 1u, a.wait_ns);
+    if (ok && done_q == n_q && n_q > 0) {
         const int j = (warp & 3) * 32 + (tid & 31);
         const uint32_t tl = tmem + (uint32_t((warp & 3) * 32) << 16);
         float *part = a.partial + (size_t(group) * a.wgroups + cta) * N_PARAMS;
@@ -1306,7 +1329,7 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
         if (group == 0) {
             for (int c = 0; c < 2 * H; c += 32) {
                 tmem_ld32(r, tl + c);
-                for (int q = 0; q < 32; ++q) part[OFF_W4 + j * 2 * H + c + q] = __uint_as_float(r[q]);
+                for (int q = 0; q < 32; ++q) part[OFF_W4 + (c + q) * H + j] = __uint_as_float(r[q]);
             }
             tmem_ld32(r, tl + 256);
             part[OFF_B4 + j] = __uint_as_float(r[0]);
@@ -1314,12 +1337,12 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
         } else {
             for (int c = 0; c < H; c += 32) {
                 tmem_ld32(r, tl + c);
-                for (int q = 0; q < 32; ++q) part[OFF_W3 + j * H + c + q] = __uint_as_float(r[q]);
+                for (int q = 0; q < 32; ++q) part[OFF_W3 + (c + q) * H + j] = __uint_as_float(r[q]);
                 tmem_ld32(r, tl + 128 + c);
-                for (int q = 0; q < 32; ++q) part[OFF_W2 + j * H + c + q] = __uint_as_float(r[q]);
+                for (int q = 0; q < 32; ++q) part[OFF_W2 + (c + q) * H + j] = __uint_as_float(r[q]);
             }
             tmem_ld32(r, tl + 256);
-            for (int q = 0; q < KIN; ++q) part[OFF_W1 + j * KIN + q] = __uint_as_float(r[q]);
+            for (int q = 0; q < KIN; ++q) part[OFF_W1 + q * H + j] = __uint_as_float(r[q]);
             part[OFF_B3 + j] = __uint_as_float(r[16]);
             tmem_ld32(r, tl + 288);
             part[OFF_B2 + j] = __uint_as_float(r[0]);
@@ -1334,17 +1357,32 @@ __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tile
     }
 }
 
-// gradient[p] = sum over the owning group's blocks of their partials, in block order (b5 is
-// accumulated by the chain kernel and left alone)
+// The blocks' partial sums store each weight matrix column by column (element (j, k) of an
+// [H][K] matrix at k * H + j), so that the thread of output row j writes consecutive rows of a
+// column together; vectors are stored as they are.  Flat parameter index of stored index s:
+__device__ __forceinline__ int param_of_stored(int s)
+{
+    int off, K;
+    if (s < OFF_B1) off = OFF_W1, K = KIN;
+    else if (s >= OFF_W2 && s < OFF_B2) off = OFF_W2, K = H;
+    else if (s >= OFF_W3 && s < OFF_B3) off = OFF_W3, K = H;
+    else if (s >= OFF_W4 && s < OFF_B4) off = OFF_W4, K = 2 * H;
+    else return s;
+    const int e = s - off;
+    return off + (e % H) * K + e / H;
+}
+
+// gradient = sum over the owning group's blocks of their partials, in block order (b5 is
+// accumulated by the chain kernel and left alone); reads in stored order, writes by parameter
 __global__ void sg_reduce_grad(float *grad, const float *partial, int wgroups)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N_PARAMS || p == OFF_B5) return;
-    const int group = (p >= OFF_W4 && p < OFF_B5) ? 0 : 1;
-    const float *src = partial + size_t(group) * wgroups * N_PARAMS + p;
+    const int si = blockIdx.x * blockDim.x + threadIdx.x;
+    if (si >= N_PARAMS || si == OFF_B5) return;
+    const int group = (si >= OFF_W4 && si < OFF_B5) ? 0 : 1;
+    const float *src = partial + size_t(group) * wgroups * N_PARAMS + si;
     float s = 0.0f;
     for (int c = 0; c < wgroups; ++c) s += src[size_t(c) * N_PARAMS];
-    grad[p] = s;
+    grad[param_of_stored(si)] = s;
 }
 
 // ------------------------------------------------------------------ optimizer
