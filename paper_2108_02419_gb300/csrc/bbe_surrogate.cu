@@ -787,43 +787,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
     }
 }
 
-// softmax over each race's logits (one warp per tile, one lane per race); training: the loss
-// and d loss / d logit per tile row (zero on padding rows)
-__global__ void sg_softmax(SgArgs a, int n_tiles)
+// softmax over each race's logits; training: the loss and d loss / d logit per tile row (zero
+// on padding rows).  One block per tile, one thread per row: the tile's logits and race layout
+// in shared memory, each row's thread takes its race's maximum and sum over the race's rows in
+// row order, then writes its own probability (and, in training, d loss / d logit).
+__global__ void __launch_bounds__(TILE) sg_softmax(SgArgs a, int n_tiles)
 {
-    const int ti = int((blockIdx.x * size_t(blockDim.x) + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    __shared__ float lg[TILE];
+    __shared__ int32_t row0[MAX_STATES + 1];
+    __shared__ float red[TILE / 32];
+    const int ti = blockIdx.x, q = threadIdx.x;
     if (ti >= n_tiles) return;
     const TileMeta &mt = a.meta[ti];
     const int ns = mt.ns;
-    const float *lg = a.logits + size_t(ti) * TILE;
-    float lossv = 0.0f;
-    for (int st = lane; st < ns; st += 32) {
-        const int r0 = mt.state_row0[st], r1 = mt.state_row0[st + 1];
+    lg[q] = a.logits[size_t(ti) * TILE + q];
+    if (q <= ns) row0[q] = mt.state_row0[q];
+    const int st = mt.row_state[q];
+    __syncthreads();
+    float lossv = 0.0f, dl = 0.0f;
+    if (st >= 0) {
+        const int r0 = row0[st], r1 = row0[st + 1];
         const int base = a.b.race_off[mt.state_race[st]];
         float mx = -INFINITY;
-        for (int q = r0; q < r1; ++q) mx = fmaxf(mx, lg[q]);
+        for (int j = r0; j < r1; ++j) mx = fmaxf(mx, lg[j]);
         float sum = 0.0f;
-        for (int q = r0; q < r1; ++q) sum += expf(lg[q] - mx);
-        const float lsum = logf(sum);
-        float tsum = 0.0f;
-        if (a.train)
-            for (int q = r0; q < r1; ++q) tsum += a.target[base + (q - r0)];
-        for (int q = r0; q < r1; ++q) {
-            const float lq = lg[q] - mx - lsum;  // log q
-            const float qv = expf(lq);
-            if (a.probs) a.probs[base + (q - r0)] = qv;
-            if (a.train) {
-                const float tv = a.target[base + (q - r0)];
-                a.ws_dlogit[size_t(ti) * TILE + q] = (qv * tsum - tv) * a.inv_races;
-                lossv -= tv * lq;
-            }
+        for (int j = r0; j < r1; ++j) sum += expf(lg[j] - mx);
+        const float lq = lg[q] - mx - logf(sum);  // log q
+        const float qv = expf(lq);
+        if (a.probs) a.probs[base + (q - r0)] = qv;
+        if (a.train) {
+            float tsum = 0.0f;
+            for (int j = r0; j < r1; ++j) tsum += a.target[base + (j - r0)];
+            const float tv = a.target[base + (q - r0)];
+            dl = (qv * tsum - tv) * a.inv_races;
+            lossv = -tv * lq;
         }
     }
     if (a.train) {
-        for (int q = mt.nrows + lane; q < TILE; q += 32) a.ws_dlogit[size_t(ti) * TILE + q] = 0.0f;
+        a.ws_dlogit[size_t(ti) * TILE + q] = dl;  // 0 on padding rows
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lossv += __shfl_xor_sync(0xffffffffu, lossv, o);
-        if (lane == 0 && a.loss_acc) atomicAdd(a.loss_acc, lossv * a.inv_races);
+        if ((q & 31) == 0) red[q >> 5] = lossv;
+        __syncthreads();
+        if (q == 0 && a.loss_acc) atomicAdd(a.loss_acc, (red[0] + red[1] + red[2] + red[3]) * a.inv_races);
     }
 }
 
@@ -1406,23 +1412,89 @@ __device__ __forceinline__ int canon_index(int i)
     return base + int(canon_off(n, k, k_dim) / 2);
 }
 
-__global__ void sg_adam(float *w, float *m, float *v, const float *grad, bf16 *wb, bf16 *wc, int n, float lr, float b1,
-                        float b2, float eps, float wd, float c1, float c2)
+// Adam step of one step's hyper-parameters (c1, c2: the bias corrections 1 - beta^t)
+struct AdamStep {
+    float lr, b1, b2, eps, wd, c1, c2;
+};
+
+// Adam (with decoupled weight decay) on parameter i with gradient gi; refreshes the bfloat16
+// copy and the canonical image
+__device__ __forceinline__ void adam_apply(int i, float gi, float *w, float *m, float *v, bf16 *wb, bf16 *wc,
+                                           const AdamStep &h)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = grad[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    const float mi = h.b1 * m[i] + (1.0f - h.b1) * gi;
+    const float vi = h.b2 * v[i] + (1.0f - h.b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    const float mh = mi / c1, vh = vi / c2;
-    const float wi = w[i] - lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
+    const float mh = mi / h.c1, vh = vi / h.c2;
+    const float wi = w[i] - h.lr * (mh / (sqrtf(vh) + h.eps) + h.wd * w[i]);
     w[i] = wi;
-    const bf16 h = __float2bfloat16_rn(wi);
-    wb[i] = h;
+    const bf16 hb = __float2bfloat16_rn(wi);
+    wb[i] = hb;
     const int ci = canon_index(i);
-    if (ci >= 0) wc[ci] = h;
+    if (ci >= 0) wc[ci] = hb;
+}
+
+// sg_reduce_grad and the Adam step in one pass (a training step).  Each weight matrix is cut
+// into 16 x 16 tiles, one 256-thread block per tile: thread (x, y) first sums, over the blocks'
+// partials in block order, stored element (row j0 + x, column k0 + y) (reads along rows, the
+// stored order), the tile goes through shared memory, and thread (x, y) then applies Adam to
+// parameter (row j0 + y, column k0 + x) (parameter order).  The vectors (biases, w5) follow in
+// blocks of their own; b5's gradient is the chain kernel's.
+constexpr int RA_TILES_W1 = (H / 16) * (KIN / 16), RA_TILES_W2 = (H / 16) * (H / 16);
+constexpr int RA_TILES_W4 = (H / 16) * (2 * H / 16);
+constexpr int RA_MATRIX_BLOCKS = RA_TILES_W1 + 2 * RA_TILES_W2 + RA_TILES_W4;
+constexpr int RA_VECTOR_BLOCKS = (5 * H + 1 + 255) / 256;  // b1, b2, b3, b4, w5, b5
+
+__global__ void __launch_bounds__(256) sg_reduce_adam(float *grad, const float *partial, int wgroups, float *w,
+                                                      float *m, float *v, bf16 *wb, bf16 *wc, AdamStep h)
+{
+    __shared__ float tile[16][17];
+    const int tid = threadIdx.x;
+    int blk = blockIdx.x;
+    if (blk >= RA_MATRIX_BLOCKS) {
+        const int e = (blk - RA_MATRIX_BLOCKS) * 256 + tid;  // index among the vector parameters
+        if (e > 5 * H) return;
+        int pidx;
+        if (e == 5 * H) pidx = OFF_B5;
+        else {
+            const int which = e / H, r = e % H;
+            const int offs[5] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4, OFF_W5};
+            pidx = offs[which] + r;
+        }
+        float g;
+        if (pidx == OFF_B5) {
+            g = grad[OFF_B5];
+        } else {
+            const int group = pidx >= OFF_W4 ? 0 : 1;
+            const float *src = partial + size_t(group) * wgroups * N_PARAMS + pidx;
+            g = 0.0f;
+            for (int c = 0; c < wgroups; ++c) g += src[size_t(c) * N_PARAMS];
+            grad[pidx] = g;
+        }
+        adam_apply(pidx, g, w, m, v, wb, wc, h);
+        return;
+    }
+    int off, K, group;
+    if (blk < RA_TILES_W1) off = OFF_W1, K = KIN, group = 1;
+    else if ((blk -= RA_TILES_W1) < RA_TILES_W2) off = OFF_W2, K = H, group = 1;
+    else if ((blk -= RA_TILES_W2) < RA_TILES_W2) off = OFF_W3, K = H, group = 1;
+    else blk -= RA_TILES_W2, off = OFF_W4, K = 2 * H, group = 0;
+    const int kt = K / 16;
+    const int j0 = (blk / kt) * 16, k0 = (blk % kt) * 16;
+    const int x = tid & 15, y = tid >> 4;
+    {
+        const int si = off + (k0 + y) * H + (j0 + x);  // stored: column k0 + y, row j0 + x
+        const float *src = partial + size_t(group) * wgroups * N_PARAMS + si;
+        float g = 0.0f;
+        for (int c = 0; c < wgroups; ++c) g += src[size_t(c) * N_PARAMS];
+        tile[y][x] = g;
+    }
+    __syncthreads();
+    const float g = tile[x][y];                           // row j0 + y, column k0 + x
+    const int pidx = off + (j0 + y) * K + (k0 + x);
+    grad[pidx] = g;
+    adam_apply(pidx, g, w, m, v, wb, wc, h);
 }
 
 __global__ void sg_to_bf16(const float *w, bf16 *wb, bf16 *wc, int n)
@@ -1650,7 +1722,7 @@ bbe_status launch_forward(bbe_surrogate *s, SgArgs &a, int64_t n_tiles, cudaStre
     else
         sg_forward_tc<false><<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
     SG_TRY(cudaGetLastError());
-    sg_softmax<<<unsigned((n_tiles + 7) / 8), 256, 0, st>>>(a, int(n_tiles));
+    sg_softmax<<<unsigned(n_tiles), TILE, 0, st>>>(a, int(n_tiles));
     SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
@@ -1687,8 +1759,10 @@ bbe_status ensure_train_buffers(bbe_surrogate *s, int64_t max_nt)
 }
 
 // one training pass (forward + backward) over tiles [t0, t1) of the uploaded plan
+// The forward and backward passes of one step over tiles t0 .. t1-1; the gradient lands in
+// s->grad, and with `adam` the parameters take the Adam step in the same final kernel.
 bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target, int64_t t0, int64_t t1,
-                      int64_t races, float *loss_slot, cudaStream_t st)
+                      int64_t races, float *loss_slot, cudaStream_t st, const AdamStep *adam = nullptr)
 {
     const int64_t nt = t1 - t0;
     if (nt <= 0) return BBE_OK;
@@ -1716,7 +1790,11 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     SG_TRY(cudaGetLastError());
     sg_backward_wgrad<<<unsigned(2 * a.wgroups), 128, wgrad_smem(), st>>>(a, int(nt));
     SG_TRY(cudaGetLastError());
-    sg_reduce_grad<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups);
+    if (adam)
+        sg_reduce_adam<<<RA_MATRIX_BLOCKS + RA_VECTOR_BLOCKS, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups, s->w,
+                                                                          s->m, s->v, s->wb, s->wc, *adam);
+    else
+        sg_reduce_grad<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups);
     SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
@@ -2130,15 +2208,13 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
     if ((e = upload_plan(s, all_order, all_tiles, st))) return e;
     if ((e = ensure_train_buffers(s, max_nt))) return e;
     for (int32_t k = 0; k < cfg->steps; ++k) {
+        const float t = float(s->step + 1);
+        const AdamStep h{cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, cfg->weight_decay,
+                         1.0f - std::pow(cfg->beta1, t), 1.0f - std::pow(cfg->beta2, t)};
         if ((e = train_pass(s, b, target, tile_begin[size_t(k)], tile_begin[size_t(k) + 1], races_in[size_t(k)],
-                            loss_log ? loss_log + k : nullptr, st)))
+                            loss_log ? loss_log + k : nullptr, st, &h)))
             return e;
         s->step += 1;
-        const float c1 = 1.0f - std::pow(cfg->beta1, float(s->step));
-        const float c2 = 1.0f - std::pow(cfg->beta2, float(s->step));
-        sg_adam<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->w, s->m, s->v, s->grad, s->wb, s->wc, N_PARAMS, cfg->lr,
-                                                       cfg->beta1, cfg->beta2, cfg->eps, cfg->weight_decay, c1, c2);
-        SG_TRY(cudaGetLastError());
     }
     return BBE_OK;
 }

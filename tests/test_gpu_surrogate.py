@@ -114,6 +114,35 @@ def test_gradient_matches_reference(bbe):
         assert rel < 2e-2, (name, rel)
 
 
+def test_first_adam_step_follows_the_reference_gradient(bbe):
+    # one training step over every race (batch = all of them) from known parameters: Adam's
+    # first step is w - lr g / (|g| + eps), about lr sign(g), so every parameter must move by
+    # the step the float64 reference gradient gives it (a misplaced gradient element or a
+    # misrouted update moves about half of them the wrong way)
+    rb = W.uneven_batch(seed=43, n_races=150, rollouts=10)
+    target = dirichlet_targets(rb, 5)
+    params = S.init_params(4).astype(np.float32)
+    lr = 1e-3
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        with bbe.Batch(rb) as b:
+            bbe.bbe_surrogate_train(s, b.handle, torch.from_numpy(target).cuda(), lr=lr, batch_states=rb.n_races,
+                                    steps=1)
+            torch.cuda.synchronize()
+        after = bbe.bbe_surrogate_get_params(s).astype(np.float64)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    g = S.backward(params.astype(np.float64), ref_inputs(rb), rb.race_off, target.astype(np.float64), bf16=True)
+    want = -lr * g / (np.abs(g) + 1e-8)
+    got = after - params.astype(np.float64)
+    assert np.all(np.abs(got) <= lr * (1 + 1e-3))
+    clear = np.abs(g) > 1e-4  # elements whose sign the GPU's bfloat16 gradient cannot flip
+    assert clear.sum() > 0.5 * g.size
+    close = np.abs(got - want) <= 2e-2 * lr
+    assert close[clear].mean() > 0.99, close[clear].mean()
+
+
 def test_training_reduces_loss_on_mc_targets(bbe):
     rb = W.uneven_batch(seed=43, n_races=3000, n_lo=2, n_hi=10, rollouts=2000, rem_lo=100.0, rem_hi=1500.0)
     s = bbe.bbe_surrogate_create(5)
