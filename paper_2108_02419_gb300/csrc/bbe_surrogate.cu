@@ -577,11 +577,24 @@ __device__ __forceinline__ void load_tile_inputs(TcPipe &P, int i, int ti, const
 
 // Tile features and race layout (one 128-thread block per tile): x in the canonical operand
 // layout (also the training pass's x), the tile's race layout record.
+// Programmatic dependent launch (the step's kernels go out with
+// cudaLaunchAttributeProgrammaticStreamSerialization): let the next kernel on the stream be
+// scheduled as soon as every block of this one has started, then wait until the kernels before
+// this one have completed and their writes are visible.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
 {
+    pdl_enter();
     __shared__ RowMap m;
     __shared__ FeatScratch fs;
     const int tid = threadIdx.x, ti = blockIdx.x;
+    // training: the b5 gradient is accumulated by the chain kernel and starts at zero
+    if (a.train && ti == 0 && tid == 0) a.grad[OFF_B5] = 0.0f;
     const SgTile t = a.tiles[ti];
     build_rowmap(m, a, t, tid, BlockSync{});
     float f[KIN];
@@ -606,6 +619,7 @@ __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
 template <bool TRAIN>
 __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_tiles)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -793,6 +807,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sg_forward_tc(SgArgs a, int n_t
 // row order, then writes its own probability (and, in training, d loss / d logit).
 __global__ void __launch_bounds__(TILE) sg_softmax(SgArgs a, int n_tiles)
 {
+    pdl_enter();
     __shared__ float lg[TILE];
     __shared__ int32_t row0[MAX_STATES + 1];
     __shared__ float red[TILE / 32];
@@ -925,6 +940,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr)
 
 __global__ void __launch_bounds__(256, 1) sg_backward_chain(SgArgs a, int n_tiles)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BcSmem &sm = *reinterpret_cast<BcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1205,6 +1221,7 @@ __device__ __forceinline__ void load_wgrad_quarter(BwSmem &sm, int slot, int gro
 
 __global__ void __launch_bounds__(128, 1) sg_backward_wgrad(SgArgs a, int n_tiles)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BwSmem &sm = *reinterpret_cast<BwSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -1382,6 +1399,7 @@ __device__ __forceinline__ int param_of_stored(int s)
 // accumulated by the chain kernel and left alone); reads in stored order, writes by parameter
 __global__ void sg_reduce_grad(float *grad, const float *partial, int wgroups)
 {
+    pdl_enter();
     const int si = blockIdx.x * blockDim.x + threadIdx.x;
     if (si >= N_PARAMS || si == OFF_B5) return;
     const int group = (si >= OFF_W4 && si < OFF_B5) ? 0 : 1;
@@ -1449,6 +1467,7 @@ constexpr int RA_VECTOR_BLOCKS = (5 * H + 1 + 255) / 256;  // b1, b2, b3, b4, w5
 __global__ void __launch_bounds__(256) sg_reduce_adam(float *grad, const float *partial, int wgroups, float *w,
                                                       float *m, float *v, bf16 *wb, bf16 *wc, AdamStep h)
 {
+    pdl_enter();
     __shared__ float tile[16][17];
     const int tid = threadIdx.x;
     int blk = blockIdx.x;
@@ -1699,6 +1718,26 @@ SgArgs base_args(const bbe_surrogate *s, const bbe_batch *b)
     return a;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled while the one
+// before it on the stream finishes (every surrogate kernel waits for its predecessors in
+// pdl_enter before it reads their results).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // forward over n_tiles tiles of a.tiles/a.order: features (one block per tile), the
 // persistent tensor-core kernel (two tile pipelines per block, at most one block per SM), softmax
 bbe_status launch_forward(bbe_surrogate *s, SgArgs &a, int64_t n_tiles, cudaStream_t st)
@@ -1715,15 +1754,12 @@ bbe_status launch_forward(bbe_surrogate *s, SgArgs &a, int64_t n_tiles, cudaStre
     SG_TRY(cudaGetDevice(&dev));
     SG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n_tiles + 1) / 2, sms));
-    sg_prep<<<unsigned(n_tiles), TILE, 0, st>>>(a);
-    SG_TRY(cudaGetLastError());
+    SG_TRY(launch_pdl(sg_prep, unsigned(n_tiles), TILE, 0, st, a));
     if (a.train)
-        sg_forward_tc<true><<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
+        SG_TRY(launch_pdl(sg_forward_tc<true>, unsigned(grid), TC_THREADS, fwd_smem(), st, a, int(n_tiles)));
     else
-        sg_forward_tc<false><<<unsigned(grid), TC_THREADS, fwd_smem(), st>>>(a, int(n_tiles));
-    SG_TRY(cudaGetLastError());
-    sg_softmax<<<unsigned(n_tiles), TILE, 0, st>>>(a, int(n_tiles));
-    SG_TRY(cudaGetLastError());
+        SG_TRY(launch_pdl(sg_forward_tc<false>, unsigned(grid), TC_THREADS, fwd_smem(), st, a, int(n_tiles)));
+    SG_TRY(launch_pdl(sg_softmax, unsigned(n_tiles), TILE, 0, st, a, int(n_tiles)));
     return BBE_OK;
 }
 
@@ -1784,18 +1820,15 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.wgroups = int32_t(std::max<int64_t>(1, std::min<int64_t>(nt, std::max(1, sms / 2))));
     if ((e = ensure_buf(s->d_partial, s->partial_cap, size_t(2) * a.wgroups * N_PARAMS))) return e;
     a.partial = s->d_partial;
-    SG_TRY(cudaMemsetAsync(s->grad, 0, N_PARAMS * sizeof(float), st));
-    if ((e = launch_forward(s, a, nt, st))) return e;
-    sg_backward_chain<<<unsigned(std::min<int64_t>(nt, sms)), 256, chain_smem(), st>>>(a, int(nt));
-    SG_TRY(cudaGetLastError());
-    sg_backward_wgrad<<<unsigned(2 * a.wgroups), 128, wgrad_smem(), st>>>(a, int(nt));
-    SG_TRY(cudaGetLastError());
+    if ((e = launch_forward(s, a, nt, st))) return e;  // sg_prep zeroes the b5 gradient
+    SG_TRY(launch_pdl(sg_backward_chain, unsigned(std::min<int64_t>(nt, sms)), 256, chain_smem(), st, a, int(nt)));
+    SG_TRY(launch_pdl(sg_backward_wgrad, unsigned(2 * a.wgroups), 128, wgrad_smem(), st, a, int(nt)));
     if (adam)
-        sg_reduce_adam<<<RA_MATRIX_BLOCKS + RA_VECTOR_BLOCKS, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups, s->w,
-                                                                          s->m, s->v, s->wb, s->wc, *adam);
+        SG_TRY(launch_pdl(sg_reduce_adam, unsigned(RA_MATRIX_BLOCKS + RA_VECTOR_BLOCKS), 256, 0, st, s->grad,
+                          static_cast<const float *>(s->d_partial), a.wgroups, s->w, s->m, s->v, s->wb, s->wc, *adam));
     else
-        sg_reduce_grad<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(s->grad, s->d_partial, a.wgroups);
-    SG_TRY(cudaGetLastError());
+        SG_TRY(launch_pdl(sg_reduce_grad, unsigned((N_PARAMS + 255) / 256), 256, 0, st, s->grad,
+                          static_cast<const float *>(s->d_partial), a.wgroups));
     return BBE_OK;
 }
 
