@@ -135,6 +135,13 @@ BBE_API bbe_status bbe_surrogate_fallback_stats(const bbe_surrogate *s, int64_t 
  * BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_surrogate_status(bbe_surrogate *s, void *cuda_stream);
 
+/* bbe_surrogate_wait_probe -- exercise the bounded-wait path without a fault: one warp waits, with
+ * the same bounded wait the surrogate kernels use for the tensor cores and bulk copies, on an
+ * mbarrier that nothing arrives at; after limit_ns (0 .. 2e9) it gives up and sets the handle's
+ * status word, which the next bbe_surrogate_status reports as BBE_ERR_TIMEOUT.  Nothing is left
+ * in flight and the context stays usable.  Asynchronous.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_surrogate_wait_probe(bbe_surrogate *s, int64_t limit_ns, void *cuda_stream);
+
 /* bbe_surrogate_save / load -- checkpoint: parameters, Adam state, step count, epoch
  * position and training ranges, in a little-endian binary file.  load creates a handle on
  * the current device.  Errors: BBE_ERR_ARG (bad file), BBE_ERR_CUDA. */

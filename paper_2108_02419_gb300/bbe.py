@@ -348,6 +348,7 @@ def _sg():
             "bbe_surrogate_forward": [vp, vp, vp, vp],
             "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
             "bbe_surrogate_status": [vp, vp],
+            "bbe_surrogate_wait_probe": [vp, C.c_int64, vp],
             "bbe_surrogate_set_gate": [vp, C.c_float],
             "bbe_surrogate_set_fallback": [vp, C.c_int64, C.c_double],
             "bbe_surrogate_fallback_budget": [C.c_int32, vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)],
@@ -442,6 +443,11 @@ def bbe_surrogate_fallback_stats(s: int) -> tuple:
 def bbe_surrogate_status(s: int, stream=None) -> None:
     """Synchronise and raise BBEError(BBE_ERR_TIMEOUT) if a bounded device wait gave up."""
     _check(_sg().bbe_surrogate_status(s, _stream(stream)), "bbe_surrogate_status")
+
+
+def bbe_surrogate_wait_probe(s: int, limit_ns: int, stream=None) -> None:
+    """Make one bounded device wait give up (no fault); the next status call reports it."""
+    _check(_sg().bbe_surrogate_wait_probe(s, int(limit_ns), _stream(stream)), "bbe_surrogate_wait_probe")
 
 
 def bbe_surrogate_save(s: int, path: str) -> None:

@@ -1526,6 +1526,22 @@ __global__ void sg_to_bf16(const float *w, bf16 *wb, bf16 *wc, int n)
     if (ci >= 0) wc[ci] = h;
 }
 
+// bbe_surrogate_wait_probe: one warp waits, with the surrogate kernels' bounded wait, on an
+// mbarrier that no thread arrives at and no copy completes; the wait gives up after limit_ns and
+// the warp records it in the status word, as the surrogate kernels do.  Nothing is in flight
+// when it gives up (no copy, no tensor-core operation, no tensor memory).
+__global__ void sg_wait_probe(int *status, long long limit_ns)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&bar, 0u, limit_ns));
+    if (!done && threadIdx.x == 0) atomicOr(status, 1);
+}
+
 __global__ void scatter_probs(const float *src, const int32_t *dst_index, float *dst, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2381,6 +2397,17 @@ bbe_status bbe_surrogate_fallback_stats(const bbe_surrogate *s, int64_t *races, 
     }
     if (races) *races = s->fb_races;
     if (rollouts) *rollouts = s->fb_rollouts;
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_wait_probe(bbe_surrogate *s, int64_t limit_ns, void *cuda_stream)
+{
+    if (!s || limit_ns < 0 || limit_ns > kWaitNs) {
+        bbe::set_error("bbe_surrogate_wait_probe: surrogate is NULL or limit_ns outside 0 .. 2e9");
+        return BBE_ERR_ARG;
+    }
+    sg_wait_probe<<<1, 32, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(s->d_status, (long long)limit_ns);
+    SG_TRY(cudaGetLastError());
     return BBE_OK;
 }
 

@@ -286,6 +286,32 @@ def test_two_stage_fallback_is_monte_carlo_at_the_rule_budget(bbe):
     assert np.array_equal(got, want)
 
 
+def test_bounded_wait_reports_timeout_and_context_stays_usable(bbe):
+    # a wait on an mbarrier that nothing completes gives up after 1 ms: the status call reports
+    # BBE_ERR_TIMEOUT once, and the handle and context keep working
+    rb = W.uneven_batch(seed=49, n_races=20, rollouts=10)
+    params = S.init_params(6).astype(np.float32)
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        bbe.bbe_surrogate_wait_probe(s, 1_000_000)
+        with pytest.raises(bbe.BbeError) as ei:
+            bbe.bbe_surrogate_status(s)
+        assert ei.value.status == -6
+        bbe.bbe_surrogate_status(s)  # cleared
+        with bbe.Batch(rb) as b:
+            probs = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_forward(s, b.handle, probs)
+            bbe.bbe_surrogate_status(s)
+            got = probs.cpu().numpy().astype(np.float64)
+        with pytest.raises(bbe.BbeError):
+            bbe.bbe_surrogate_wait_probe(s, -1)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    want, _ = S.forward(params.astype(np.float64), ref_inputs(rb), rb.race_off, bf16=True)
+    assert np.abs(got - want).max() < 5e-3
+
+
 def test_infer_without_training_ranges_is_refused(bbe):
     rb = W.uneven_batch(seed=48, n_races=4, rollouts=10)
     s = bbe.bbe_surrogate_create(7)
