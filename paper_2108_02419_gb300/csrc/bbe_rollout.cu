@@ -97,8 +97,11 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
 // rollout ends when K = min(places, n) competitors have crossed; competitors past the line keep
 // moving and keep their rank slots; a competitor has finished exactly when its position is at
 // least L, since positions only grow).
+// Launch bounds: the win mode keeps the compiler's own register choice (64 for one or two
+// competitors per lane, about 100 for four); the place mode, which holds its finishing order in
+// registers, may use up to 128 rather than spill (measured faster on GB300).
 template <int DIST, int V, int MODE>
-__global__ void __launch_bounds__(512) rollout_kernel(RolloutLaunch l)
+__global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(RolloutLaunch l)
 {
     extern __shared__ WarpStage stage_all[];
     WarpStage &st = stage_all[threadIdx.x >> 5];
