@@ -80,6 +80,8 @@ def lib():
             L.bbe_oracle_rollout_order.restype = C.c_int
             L.bbe_oracle_race_places.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
             L.bbe_oracle_race_places.restype = C.c_int
+            L.bbe_oracle_race_orders.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
+            L.bbe_oracle_race_orders.restype = C.c_int
             L.bbe_oracle_trajectory.argtypes = [C.POINTER(_Race), u64, u32, u32, i64, vp, vp, vp, i64]
             L.bbe_oracle_trajectory.restype = C.c_int
             L.bbe_oracle_preference.argtypes = [C.c_int, vp, C.c_int, vp, vp, vp, vp]
@@ -193,6 +195,54 @@ def race_places(race: dict, seed: int, places: int, r: int | None = None, R: int
     steps = np.zeros(1, np.int64)
     st = lib().bbe_oracle_race_places(C.byref(a.s), seed, r, k_begin, R, places, max_steps, _ptr(counts), _ptr(steps))
     return counts, int(steps[0]), int(st)
+
+
+def race_orders(race: dict, seed: int, places: int, r: int | None = None, R: int | None = None, k_begin: int = 0,
+                max_steps: int = MAX_STEPS_DEFAULT):
+    """Ordered top-kk tallies of one race, kk = min(places, n): (counts int32 [n ** kk], entry
+    ((o_1 n + o_2) n + ..) + o_kk, steps_total, status)."""
+    a = _RaceArgs(race)
+    r = race["race_id"] if r is None else r
+    R = race["R"] if R is None else R
+    kk = min(places, race["n"])
+    counts = np.zeros(race["n"] ** kk, np.int32)
+    steps = np.zeros(1, np.int64)
+    st = lib().bbe_oracle_race_orders(C.byref(a.s), seed, r, k_begin, R, places, max_steps, _ptr(counts), _ptr(steps))
+    return counts, int(steps[0]), int(st)
+
+
+def batch_orders(batch, places: int, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,
+                 rollout_chunk: int = 2500):
+    """Order tallies for the given races of a RaceBatch: (list of int32 [n_r ** kk_r] arrays in
+    the order given, steps int64 [len(races)], status); rollout chunks run on a thread pool."""
+    races = list(range(batch.n_races)) if races is None else [int(x) for x in races]
+    threads = threads or os.cpu_count() or 1
+    tasks = []
+    for i, r in enumerate(races):
+        R = int(batch.rollouts[r])
+        for k0 in range(0, R, rollout_chunk):
+            tasks.append((i, r, k0, min(rollout_chunk, R - k0)))
+
+    def one(task):
+        i, r, k0, cnt = task
+        return race_orders(batch.race(r), batch.seed, places, R=cnt, k_begin=k0, max_steps=max_steps)
+
+    if threads <= 1 or len(tasks) <= 1:
+        res = [one(t) for t in tasks]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(one, tasks))
+    per_race = []
+    for r in races:
+        n = int(batch.race_off[r + 1] - batch.race_off[r])
+        per_race.append(np.zeros(n ** min(places, n), np.int64))
+    steps = np.zeros(len(races), np.int64)
+    status = 0
+    for (i, r, k0, cnt), (c, st, s) in zip(tasks, res):
+        per_race[i] += c
+        steps[i] += st
+        status = min(status, s)
+    return [c.astype(np.int32) for c in per_race], steps, status
 
 
 def batch_places(batch, places: int, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,

@@ -388,6 +388,41 @@ int bbe_oracle_race_places(const bbe_oracle_race *race, uint64_t seed, uint32_t 
     return status;
 }
 
+/* Finishing-order tallies (Section 3: the rollouts estimate the distribution of outcomes; the
+ * ordered top places are the outcome a forecast or exacta-style market is about).  Rollouts
+ * k_begin .. k_begin+R-1 run to the kk-th finisher, kk = min(places, n); each completed rollout adds
+ * one to the entry of its ordered top-kk tuple (o_1, .., o_kk), entry index
+ * (..((o_1) n + o_2) n + ..) + o_kk of the n^kk counts.  A rollout cut off by max_steps counts for
+ * nobody.  Returns 0 or BBE_ORACLE_STEP_LIMIT; *steps_total sums the steps of every rollout. */
+int bbe_oracle_race_orders(const bbe_oracle_race *race, uint64_t seed, uint32_t r,
+                           int64_t k_begin, int64_t R, int places, int64_t max_steps,
+                           int32_t *counts, int64_t *steps_total)
+{
+    int n = race->n;
+    int kk = places < n ? places : n;
+    int64_t cells = 1;
+    for (int j = 0; j < kk; ++j) cells *= n;
+    int status = 0;
+    int64_t total = 0;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t i = 0; i < cells; ++i) counts[i] = 0;
+    for (int64_t k = k_begin; k < k_begin + R; ++k) {
+        int64_t steps = 0;
+        int st = bbe_oracle_rollout_order(race, seed, r, (uint32_t)k, kk, max_steps, &steps, order);
+        total += steps;
+        if (st != 0) {
+            status = st;
+            continue;
+        }
+        int64_t code = 0;
+        for (int j = 0; j < kk; ++j) code = code * n + order[j];
+        counts[code] += 1;
+    }
+    if (steps_total) *steps_total = total;
+    free(order);
+    return status;
+}
+
 /* One full run of race r (rollout k of its stream): every competitor moves under Eq. 1 until
  * the last one has crossed the line (Section 3) or max_steps steps pass; the space-time series
  * of the race (Section 6 plots one).  For t < min(steps, cap): d_traj[t * n + c] = d_c after

@@ -78,11 +78,11 @@ def exact_win_probs(L, d0, mu, sigma, P=None, theta=None, prev0=None, max_steps=
     return win
 
 
-def exact_place_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, max_steps=200):
-    """Exact probability that competitor c finishes in place j (j < places) of a two-point
-    race, by the same enumeration: every competitor keeps moving under Eq. 1 until `places`
-    competitors have crossed; those crossing in one step are placed by their binary32
-    crossing time tau, then by index.  Returns an [n, places] array."""
+def exact_order_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, max_steps=200):
+    """Exact probability of each ordered top-kk tuple (kk = min(places, n)) of a two-point race,
+    by the same enumeration: every competitor keeps moving under Eq. 1 until kk competitors have
+    crossed; those crossing in one step are placed by their binary32 crossing time tau, then by
+    index.  Returns {tuple of kk competitors: probability}."""
     n = len(d0)
     P = [1.0] * n if P is None else list(P)
     theta = [1.0] * n if theta is None else list(theta)
@@ -91,7 +91,7 @@ def exact_place_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, 
         assert float(np.float32(v)) == v and (v * 2 ** 12) == int(v * 2 ** 12), "inputs must be small dyadics"
     places = min(places, n)
     states = {(tuple(float(x) for x in d0), tuple(float(x) for x in prev), ()): 1.0}
-    out = np.zeros((n, places))
+    out = defaultdict(float)
     for _ in range(max_steps):
         nxt = defaultdict(float)
         for (d, pv, order), mass in states.items():
@@ -116,12 +116,24 @@ def exact_place_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, 
                 taus = sorted((np.float32(np.float32(L) - np.float32(d[c])) / np.float32(S[c]), c) for c in new)
                 o2 = order + tuple(c for _, c in taus)
                 if len(o2) >= places:
-                    for j in range(places):
-                        out[o2[j], j] += share
+                    out[o2[:places]] += share
                 else:
                     nxt[(tuple(dn), tuple(S), o2)] += share
         states = nxt
         if not states:
             break
     assert not states, "race did not end within max_steps"
+    return dict(out)
+
+
+def exact_place_probs(L, d0, mu, sigma, places, P=None, theta=None, prev0=None, max_steps=200):
+    """Exact probability that competitor c finishes in place j (j < places) of a two-point
+    race: the marginals of exact_order_probs.  Returns an [n, places] array."""
+    n = len(d0)
+    kk = min(places, n)
+    out = np.zeros((n, kk))
+    for tup, pr in exact_order_probs(L, d0, mu, sigma, places, P=P, theta=theta, prev0=prev0,
+                                     max_steps=max_steps).items():
+        for j, c in enumerate(tup):
+            out[c, j] += pr
     return out

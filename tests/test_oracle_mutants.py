@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes: each mutant below is a copy of
 oracle/bbe_oracle.c with one deliberate error (in the oracle, on the CPU); the pin suites
 (tests/test_oracle_rng.py, tests/test_oracle_race.py, tests/test_oracle_places.py,
-tests/test_oracle_trajectory.py, tests/test_oracle_preference.py) must fail against every mutant."""
+tests/test_oracle_trajectory.py, tests/test_oracle_preference.py, tests/test_oracle_orders.py) must fail
+against every mutant."""
 import os
 import subprocess
 import sys
@@ -45,6 +46,8 @@ MUTANTS = {
         "            if (dn[c] >= race->L) all_in = 1;"),
     "preference_unclamped": ("if (m > 1.0f) m = 1.0f;", ";"),
     "preference_additive": ("p = p * (1.0f - weights[i] * m);", "p = p - weights[i] * m;"),
+    "order_tuple_reversed": ("for (int j = 0; j < kk; ++j) code = code * n + order[j];",
+                             "for (int j = kk - 1; j >= 0; --j) code = code * n + order[j];"),
 }
 
 
@@ -61,6 +64,7 @@ def test_pins_catch_mutant(tmp_path, name):
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_preference.py"),
                           os.path.join(ROOT, "tests", "test_oracle_trajectory.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_orders.py"),
                           os.path.join(ROOT, "tests", "test_oracle_race.py"),
                           os.path.join(ROOT, "tests", "test_oracle_places.py"),
                           os.path.join(ROOT, "tests", "test_oracle_rng.py")],
