@@ -552,6 +552,21 @@ def run_places(dev, stream) -> dict:
             out[f"K{K}"] = {"s": t, "competitor_steps": cs, "competitor_steps_per_s": rate,
                             "steps_per_rollout": cs / float(rb.n_total) / 10000.0,
                             "alu_frac": rate * ALG_OPS_PER_COMPETITOR_STEP / peak}
+        # ordered top-3 tallies (tricast) in the same pass as the place counts
+        total = bbe.bbe_order_table_size(b.handle, 3)
+        orders = torch.empty(total, dtype=torch.int32, device=dev)
+        counts = torch.empty((rb.n_total, 3), dtype=torch.int32, device=dev)
+        bbe.bbe_order_counts(b.handle, 3, orders, counts, steps, stream)  # warm-up (uploads the layout)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bbe.bbe_order_counts(b.handle, 3, orders, counts, steps, stream)
+        e1.record(stream)
+        e1.synchronize()
+        b.status(stream)
+        t = e0.elapsed_time(e1) / 1e3
+        cs = float((rb.sizes() * steps.cpu().numpy()).sum())
+        out["K3_orders"] = {"s": t, "table_entries": total, "competitor_steps_per_s": cs / t,
+                            "tuples_counted": int(orders.sum().item())}
     return out
 
 

@@ -70,6 +70,7 @@ typedef enum {
 } bbe_dist;
 
 #define BBE_MAX_COMPETITORS 32
+#define BBE_MAX_ORDER_PLACES 3 /* ordered places tallied by bbe_order_counts (n^3 <= 32768 per race) */
 #define BBE_THETA_DEFAULT 1.0f
 #define BBE_MAX_STEPS_DEFAULT (1 << 20)
 
@@ -154,6 +155,27 @@ BBE_API bbe_status bbe_win_probs(const bbe_batch *batch, const int32_t *win_coun
  * sets BBE_ERR_STEP_LIMIT in the batch status.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_place_counts(bbe_batch *batch, int32_t places, int32_t *place_counts, int64_t *steps_total,
                                     void *cuda_stream);
+
+/* bbe_order_counts -- finishing-order tallies: how often each ordered tuple of the first K
+ * finishers occurs (Section 3: the dry-runs estimate the distribution of outcomes, the order of
+ * finish included; a forecast or exacta market pays on the ordered first two, a tricast on the
+ * first three).  The rollouts are bbe_place_counts's (same stream, same readings), run to the
+ * K-th finisher with K_r = min(places, n_r); each completed rollout adds one to the entry of its
+ * ordered tuple (o_1, .., o_K_r), the base-n_r number ((o_1 n_r + o_2) n_r + ..) + o_K_r.
+ *   places        1 .. BBE_MAX_ORDER_PLACES (1: the win counts).
+ *   order_counts  device int32[bbe_order_table_size entries], overwritten: race r's table of
+ *                 n_r ^ K_r entries starts at sum over r' < r of n_r' ^ K_r'.
+ *   place_counts  nullable device int32[sum n * places]: bbe_place_counts's table, same pass.
+ *   steps_total   nullable device int64[n_races].
+ * Every marginal of a race's table is a column of its place counts.  Asynchronous on
+ * cuda_stream (the first call with a new `places` uploads the table layout).  Cut-off rollouts
+ * count for nobody and set BBE_ERR_STEP_LIMIT.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_order_counts(bbe_batch *batch, int32_t places, int32_t *order_counts, int32_t *place_counts,
+                                    int64_t *steps_total, void *cuda_stream);
+
+/* bbe_order_table_size -- entries of the order tally buffer for `places` (host; no GPU work).
+ * Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_order_table_size(const bbe_batch *batch, int32_t places, int64_t *entries);
 
 /* bbe_place_probs -- probability of finishing in the first `top` places (a place market
  * paying on the first `top` places; top = 1 is the win probability):

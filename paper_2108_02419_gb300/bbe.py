@@ -54,6 +54,8 @@ def lib():
             "bbe_rollout_batch": [vp, vp, vp, vp],
             "bbe_win_probs": [vp, vp, vp, vp, vp],
             "bbe_place_counts": [vp, C.c_int32, vp, vp, vp],
+            "bbe_order_counts": [vp, C.c_int32, vp, vp, vp, vp],
+            "bbe_order_table_size": [vp, C.c_int32, C.POINTER(C.c_int64)],
             "bbe_race_trajectory": [vp, C.c_uint32, C.c_int32, vp, vp, vp, vp],
             "bbe_preference_coefficients": [C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp],
             "bbe_snapshot_batch": [C.POINTER(vp), vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32,
@@ -145,6 +147,17 @@ def bbe_win_probs(batch: int, win_counts, probs, odds=None, stream=None) -> None
 def bbe_place_counts(batch: int, places: int, place_counts, steps_total=None, stream=None) -> None:
     _check(lib().bbe_place_counts(batch, int(places), _ptr(place_counts, np.int32), _ptr(steps_total, np.int64),
                                   _stream(stream)), "bbe_place_counts")
+
+
+def bbe_order_counts(batch: int, places: int, order_counts, place_counts=None, steps_total=None, stream=None) -> None:
+    _check(lib().bbe_order_counts(batch, int(places), _ptr(order_counts, np.int32), _ptr(place_counts, np.int32),
+                                  _ptr(steps_total, np.int64), _stream(stream)), "bbe_order_counts")
+
+
+def bbe_order_table_size(batch: int, places: int) -> int:
+    out = C.c_int64()
+    _check(lib().bbe_order_table_size(batch, int(places), C.byref(out)), "bbe_order_table_size")
+    return out.value
 
 
 def bbe_place_probs(batch: int, places: int, place_counts, top: int, probs, stream=None) -> None:
@@ -284,6 +297,18 @@ class Batch:
             steps = torch.empty(self.rb.n_races, dtype=torch.int64, device="cuda")
         bbe_place_counts(self.handle, places, counts, steps, stream)
         return counts, steps
+
+    def orders(self, places: int, with_places: bool = False, stream=None):
+        """Order tallies (device int32, every race's n_r ** min(places, n_r) table back to back),
+        optionally the place counts of the same pass, and steps per race."""
+        import torch
+
+        total = bbe_order_table_size(self.handle, places)
+        counts = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+        pc = torch.empty((self.rb.n_total, places), dtype=torch.int32, device="cuda") if with_places else None
+        steps = torch.empty(self.rb.n_races, dtype=torch.int64, device="cuda")
+        bbe_order_counts(self.handle, places, counts, pc, steps, stream)
+        return counts[:total], pc, steps
 
     def place_probs(self, counts, top: int, probs=None, stream=None):
         import torch

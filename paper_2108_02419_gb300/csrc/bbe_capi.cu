@@ -537,6 +537,43 @@ bbe_status bbe_win_probs(const bbe_batch *b, const int32_t *win_counts, float *p
     return BBE_OK;
 }
 
+namespace {
+// The rollout kernel in place mode over the whole batch: place table (nullable) and, with
+// `orders`, the ordered top-`places` tallies at b->d_order_off.
+bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, int32_t *orders,
+                          int64_t *steps_total, cudaStream_t s)
+{
+    if (place_counts)
+        BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
+    if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, kGroups * sizeof(int32_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s));
+    for (int g = kGroups - 1; g >= 0; --g) {
+        if (b->n_items_v[g] == 0) continue;
+        bbe::RolloutLaunch l = make_launch(b, place_counts, steps_total, g);
+        l.places = places;
+        l.orders = orders;
+        l.order_off = orders ? b->d_order_off : nullptr;
+        const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block);
+        l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
+        BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
+    }
+    return BBE_OK;
+}
+
+// per-race first entries of the order tally tables for `places` (n_r ^ min(places, n_r) entries)
+void order_layout(const bbe_batch *b, int32_t places, std::vector<int64_t> &off)
+{
+    off.assign(size_t(b->n_races) + 1, 0);
+    for (int r = 0; r < b->n_races; ++r) {
+        const int n = b->h_off[r + 1] - b->h_off[r];
+        int64_t cells = 1;
+        for (int j = 0; j < std::min(places, n); ++j) cells *= n;
+        off[size_t(r) + 1] = off[size_t(r)] + cells;
+    }
+}
+}  // namespace
+
 bbe_status bbe_place_counts(bbe_batch *b, int32_t places, int32_t *place_counts, int64_t *steps_total,
                             void *cuda_stream)
 {
@@ -548,20 +585,40 @@ bbe_status bbe_place_counts(bbe_batch *b, int32_t places, int32_t *place_counts,
         set_error("places outside 1..BBE_MAX_COMPETITORS");
         return BBE_ERR_ARG;
     }
-    cudaStream_t s = as_stream(cuda_stream);
-    BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
-    if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));
-    BBE_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, kGroups * sizeof(int32_t), s));
-    BBE_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), s));
-    for (int g = kGroups - 1; g >= 0; --g) {
-        if (b->n_items_v[g] == 0) continue;
-        bbe::RolloutLaunch l = make_launch(b, place_counts, steps_total, g);
-        l.places = places;
-        const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block);
-        l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
-        BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
+    return run_place_mode(b, places, place_counts, nullptr, steps_total, as_stream(cuda_stream));
+}
+
+bbe_status bbe_order_table_size(const bbe_batch *b, int32_t places, int64_t *entries)
+{
+    if (!b || !entries || places < 1 || places > BBE_MAX_ORDER_PLACES) {
+        set_error("bbe_order_table_size: batch or entries is NULL, or places outside 1..BBE_MAX_ORDER_PLACES");
+        return BBE_ERR_ARG;
     }
+    std::vector<int64_t> off;
+    order_layout(b, places, off);
+    *entries = off.back();
     return BBE_OK;
+}
+
+bbe_status bbe_order_counts(bbe_batch *b, int32_t places, int32_t *order_counts, int32_t *place_counts,
+                            int64_t *steps_total, void *cuda_stream)
+{
+    if (!b || !order_counts || places < 1 || places > BBE_MAX_ORDER_PLACES) {
+        set_error("bbe_order_counts: batch or order_counts is NULL, or places outside 1..BBE_MAX_ORDER_PLACES");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    if (b->order_places != places || !b->d_order_off) {
+        order_layout(b, places, b->h_order_off);
+        if (b->d_order_off) cudaFree(b->d_order_off);
+        b->d_order_off = nullptr;
+        BBE_CUDA_TRY(cudaMalloc(&b->d_order_off, b->h_order_off.size() * sizeof(int64_t)));
+        BBE_CUDA_TRY(cudaMemcpyAsync(b->d_order_off, b->h_order_off.data(), b->h_order_off.size() * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s));  // the host copy lives with the batch
+        b->order_places = places;
+    }
+    BBE_CUDA_TRY(cudaMemsetAsync(order_counts, 0, size_t(b->h_order_off.back()) * sizeof(int32_t), s));
+    return run_place_mode(b, places, place_counts, order_counts, steps_total, s);
 }
 
 namespace {
@@ -758,6 +815,7 @@ void bbe_destroy_batch(bbe_batch *b)
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_order_off) cudaFree(b->d_order_off);
     if (b->arena) cudaFree(b->arena);
     delete b;
 }

@@ -45,7 +45,9 @@ struct RolloutLaunch {
     int32_t max_steps;
     int32_t grid, block;
     uint32_t round_key[20];  // Philox round keys (k0, k1) of rounds 0..9, from the seed
-    int32_t places;          // place-count kernel: places per competitor in `counts`
+    int32_t places;          // place-count kernel: places per competitor in `counts` (null: no place table)
+    int32_t *orders;         // place-count kernel, or null: ordered top-`places` tallies, n^places per race
+    const int64_t *order_off;  // [n_races]: first entry of each race's tally table in `orders`
 };
 
 // Philox4x32-10 key schedule: round i uses (seed_lo + i * 0x9E3779B9, seed_hi + i * 0xBB67AE85).
@@ -115,6 +117,11 @@ struct bbe_batch {
     // graph cache (captured on the second pass with the same output buffers)
     int32_t *last_counts = nullptr;
     int64_t *last_steps = nullptr;
+
+    // finishing-order tally layout (bbe_order_counts): first entry of each race's table
+    int32_t order_places = 0;
+    std::vector<int64_t> h_order_off;  // [n_races + 1]
+    int64_t *d_order_off = nullptr;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int32_t *g_counts = nullptr;

@@ -459,6 +459,20 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
                                 const int j = ql + m * nl;
                                 if (seg_fin && j < K) atomicAdd(&cnt[my_ord[m] * K + j], 1);
                             }
+                            if (l.orders != nullptr && seg_fin) {
+                                // the ordered top K as one base-n number, gathered from the lanes
+                                // holding places 0 .. K-1 into the segment's first lane
+                                int code = 0;
+                                for (int j = 0; j < K; ++j) {
+                                    const int mj = j / nl;
+                                    int mine = my_ord[0];
+#pragma unroll
+                                    for (int m = 1; m < V; ++m)
+                                        if (m == mj) mine = my_ord[m];
+                                    code = code * n + __shfl_sync(segmask, mine, segbase + (j - mj * nl));
+                                }
+                                if (ql == 0) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                            }
                             placed = 0;
                         }
                         steps += seg_fin ? (t + 1) : t;
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
         } else {
             // one flush of the place table per work item
             __syncwarp();
-            for (int i = lane; i < n * K; i += 32) {
+            for (int i = lane; i < n * K && l.counts != nullptr; i += 32) {
                 const int c = cnt[i];
                 if (c != 0) atomicAdd(&l.counts[(off + i / K) * l.places + i % K], c);
             }
