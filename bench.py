@@ -642,6 +642,15 @@ def run_population(dev, stream, bettors: int = 1000, dry_runs: int = 50) -> dict
                            "pooled dry-runs": float((pooled.argmax(axis=1) == winner).mean()),
                            "LW": float((pr[:, 0] == winner).mean()), "UD(3)": float((pr[:, 1] == winner).mean()),
                            "LinEx(10)": float((pr[:, 2] == winner).mean()), "ZI": float((pr[:, 3] == winner).mean())},
+        # each rule scored against the Monte Carlo probabilities at every snapshot (all bettors'
+        # dry-runs pooled, 50,000 per snapshot): the probability that its pick wins, and how often
+        # it picks the Monte Carlo favourite
+        "mc_prob_of_pick": {"RP(d) bettor": float(np.take_along_axis(pooled, rp_pick, axis=1).mean()),
+                            **{name: float(pooled[np.arange(n_snap), pr[:, i]].mean())
+                               for i, name in enumerate(("LW", "UD(3)", "LinEx(10)", "ZI"))}},
+        "picks_mc_favourite": {"RP(d) bettor": float((rp_pick == pooled.argmax(axis=1)[:, None]).mean()),
+                               **{name: float((pr[:, i] == pooled.argmax(axis=1)).mean())
+                                  for i, name in enumerate(("LW", "UD(3)", "LinEx(10)", "ZI"))}},
     })
     return out
 
