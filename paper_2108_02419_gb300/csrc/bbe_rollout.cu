@@ -181,7 +181,11 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
 #pragma unroll
         for (int m = 0; m < V; ++m) my_ord[m] = 0;
 
-        while (__any_sync(kFull, active)) {
+        // place mode: every work item starts with an active segment, and segments change state
+        // only at a finish or a step-limit abort, so the warp checks for remaining work only
+        // after such a step (measured faster there; the win mode keeps the check per step)
+        while (MODE == 1 || __any_sync(kFull, active)) {
+            bool fired = false;  // place mode: a segment finished or was cut off in this step
             __syncwarp();  // z-cache writes of earlier steps are visible to every lane
             const bool running = active && t >= 0;
             // i+: the next rank (same lane, or slot 0 of the next lane).  The same shuffles
@@ -384,6 +388,7 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
             } else {
                 // place this step's new finishers of each segment, earliest crossing first
                 if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
+                    fired = true;
                     const unsigned amask = __ballot_sync(kFull, aborted);
                     for (;;) {
                         unsigned fm[V];
@@ -503,7 +508,9 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
                 }
             }
             ++gstep;
-
+            if constexpr (MODE == 1) {
+                if (fired && !__any_sync(kFull, active)) break;
+            }
         }
         if constexpr (MODE == 0) {
             // one reduction per work item: wins of each home competitor summed over segments
