@@ -57,7 +57,7 @@ typedef enum {
     BBE_ERR_FINISHED = -3,    /* a competitor already at or past the finish line (d >= L) */
     BBE_ERR_CUDA = -4,        /* a CUDA runtime call failed (message in bbe_last_error) */
     BBE_ERR_STEP_LIMIT = -5,  /* some rollout reached max_steps without a finisher; it counts for nobody */
-    BBE_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up */
+    BBE_ERR_TIMEOUT = -6,     /* a bounded device wait gave up (surrogate kernels, bbe_surrogate_status) */
     BBE_ERR_RANGE = -7        /* a value outside the range the call supports */
 } bbe_status;
 
@@ -80,7 +80,8 @@ typedef struct bbe_batch bbe_batch; /* opaque, library-owned */
 typedef struct {
     int32_t warps_per_block;    /* 1..16 */
     int32_t blocks_per_sm;      /* 1..32; grid = SMs x blocks_per_sm (persistent) */
-    int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 */
+    int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 (halved, down
+                                   to 1, for a batch too small to give every warp slot an item) */
     int32_t max_steps;          /* step limit per rollout, 1..2^30 */
     int32_t slots_per_lane;     /* competitors per lane: 0 = automatic (the layout measured fastest
                                    for the race's competitor count), 1, 2 or 4 = that layout for every

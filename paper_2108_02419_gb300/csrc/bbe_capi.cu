@@ -127,19 +127,40 @@ bbe_status build_items(bbe_batch *b)
         double cost_full, cost_rem;
     };
     std::vector<RacePlan> plans[kGroups];
-    const int64_t per_lane = b->cfg.rollouts_per_lane;
     // keep the whole list near kMaxItems items: very large batches get larger items
     int64_t total_rollouts = 0;
     for (int r = 0; r < b->n_races; ++r) total_rollouts += b->h_R[r];
     const int64_t min_chunk = (total_rollouts + kMaxItems - 1) / kMaxItems;
+    auto chunk_of = [&](int r, int64_t per_lane, int nseg) {
+        // at least per_lane rollouts per segment, at most kMaxItemsPerRace items per race
+        return std::max<int64_t>(std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace),
+                                 min_chunk);
+    };
+    auto nseg_of = [&](int r) {
+        const int n = b->h_off[r + 1] - b->h_off[r];
+        const int v = slots_for(n, b->cfg.slots_per_lane);
+        return 32 / ((n + v - 1) / v);
+    };
+    // A batch too small to give every warp the GPU can hold (64 per SM) a work item runs fewer
+    // rollouts per lane, down to one: the chunking decides which warp runs a rollout, never its
+    // result.  (An item holds at most 32 x per_lane rollouts, so large batches skip the count.)
+    int64_t per_lane = b->cfg.rollouts_per_lane;
+    const int64_t warp_slots = int64_t(std::max(1, b->num_sms)) * 64;
+    while (per_lane > 1 && total_rollouts < warp_slots * per_lane * 32) {
+        int64_t items = 0;
+        for (int r = 0; r < b->n_races && items < warp_slots; ++r) {
+            const int64_t chunk = chunk_of(r, per_lane, nseg_of(r));
+            items += (b->h_R[r] + chunk - 1) / chunk;
+        }
+        if (items >= warp_slots) break;
+        per_lane = std::max<int64_t>(1, per_lane / 2);
+    }
     size_t total = 0;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
         const int v = slots_for(n, b->cfg.slots_per_lane);
-        const int nseg = 32 / ((n + v - 1) / v);
-        // at least rollouts_per_lane per segment, at most kMaxItemsPerRace items per race
-        const int64_t chunk = std::max<int64_t>(
-            std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace), min_chunk);
+        const int nseg = nseg_of(r);
+        const int64_t chunk = chunk_of(r, per_lane, nseg);
         const double st = est_steps(b, r);
         RacePlan pl{r, chunk, b->h_R[r] / chunk, b->h_R[r] % chunk, b->h_k0.empty() ? 0 : b->h_k0[r], 0.0, 0.0};
         pl.cost_full = double((chunk + nseg - 1) / nseg) * st;
