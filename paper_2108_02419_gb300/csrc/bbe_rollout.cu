@@ -12,8 +12,8 @@
 // strictly in front (i+) is the next slot: a register (same lane) or one shuffle (next
 // lane).  Finishing is detected with a ballot; the winner (least within-step crossing time,
 // lowest index on ties) comes from the ballot mask, or from a shuffle reduction when several
-// cross in the same step.  Each slot counts the wins of the competitor that starts every
-// rollout in it; the counts are reduced once per work item.  The same kernel in place mode
+// cross in the same step.  Wins are counted per slot in registers (one or two slots per lane)
+// or per warp in shared memory (four), and reach the global counts once per work item.  The same kernel in place mode
 // runs every rollout to the K-th finisher (include/bbe.h: bbe_place_counts): finished
 // competitors keep moving in their rank slots, the finishers of a step are placed by repeated
 // argmin of (crossing time, index), the lane of place j records its competitor, and completed
@@ -44,6 +44,7 @@ struct WarpStage {
     float kr[32];
     float d0[32], prev0[32];
     int init_c[32];
+    int wins[32];   // win mode with four slots per lane: wins of each competitor in the work item
     float zc[3][128];
 };
 
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
             st.kr[lane] = __fmul_rn(kKappa, __fsub_rn(__fmul_rn(2.0f, b.rho[ci]), 1.0f));
             st.d0[lane] = my_d0;
             st.prev0[lane] = b.prev0 ? b.prev0[ci] : __fmul_rn(mu, P);
+            st.wins[lane] = 0;
         }
         int rank = 0;
         for (int i = 0; i < n; ++i) {
@@ -164,6 +166,11 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
         bool active = lane_used && k < kend;
         int t = 0;
         unsigned gstep = 0;
+        // Win counting: with one or two slots per lane each slot counts, in registers, the wins
+        // of the competitor that starts every rollout in it (home); with four, whose registers
+        // are scarcer, the segment's first lane adds each winner to the warp's table in shared
+        // memory (measured faster for four, slower for one and two).
+        constexpr bool kSmemWins = V == 4;
         int home[V], wins[V];
         Slot s[V];
 #pragma unroll
@@ -380,9 +387,13 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
                         const int cu = __shfl_sync(kFull, s[u].c, wl);
                         cw = wv == u ? cu : cw;
                     }
+                    if constexpr (kSmemWins) {
+                        if (seg_fin && ql == 0) atomicAdd(&st.wins[cw], 1);
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
+                        for (int v = 0; v < V; ++v)
+                            if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
+                    }
                 }
 
             } else {
@@ -489,9 +500,10 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
                         t = nseg > 1 ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            s[v].c = home[v];
-                            s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
-                            s[v].prev = st.prev0[home[v]];
+                            const int hc = kSmemWins ? (valid[v] ? st.init_c[rank0 + v] : 0) : home[v];
+                            s[v].c = hc;
+                            s[v].d = valid[v] ? st.d0[hc] : INFINITY;
+                            s[v].prev = st.prev0[hc];
                         }
                     } else {
 #pragma unroll
@@ -513,12 +525,18 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
             }
         }
         if constexpr (MODE == 0) {
-            // one reduction per work item: wins of each home competitor summed over segments
+            if constexpr (kSmemWins) {
+                // one flush of the work item's win table
+                __syncwarp();
+                if (lane < n && st.wins[lane] != 0) atomicAdd(&l.counts[off + lane], st.wins[lane]);
+            } else {
+                // one reduction per work item: wins of each home competitor summed over segments
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                int total = 0;
-                for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
-                if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
+                for (int v = 0; v < V; ++v) {
+                    int total = 0;
+                    for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
+                    if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
+                }
             }
         } else {
             // one flush of the place table per work item
