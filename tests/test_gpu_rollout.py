@@ -77,7 +77,7 @@ def test_uneven_batch_small(bbe):
 
 
 @pytest.mark.parametrize("slots", [1, 2, 4])
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 11, 12, 13, 16, 17, 20, 24, 31, 32])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 11, 12, 13, 16, 17, 20, 21, 22, 23, 24, 31, 32])
 def test_every_segment_packing(bbe, n, slots):
     # one or two competitors per lane, every segment width and odd/even counts
     rb = W.uneven_batch(seed=100 + n, n_races=3, n_lo=n, n_hi=n, rollouts=333, rem_lo=50.0, rem_hi=900.0)
