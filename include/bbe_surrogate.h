@@ -8,7 +8,14 @@
  * then answers the same question with one network evaluation per race.  The paper has no
  * learned model; the network below is this library's design:
  *
- *   per competitor c: x_c = [d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1]
+ *   per competitor c, 16 input columns: x_c[0..4] = [d_c / L, (L - d_c) / 5000, mu_c - 16,
+ *            sigma_c - 1, 2 rho_c - 1]; x_c[5..13] derived per race from those: with
+ *            v = mu (1 + 0.1 (2 rho - 1) d / L), T = (L - d) / v and s = sigma sqrt(T) / v,
+ *            T / 100, the lag behind the race's least T (capped at 100, / 10), s, that lag over
+ *            sqrt(s^2 + s_min^2 + 0.01) (capped at 20, / 5), the gap to the nearest competitor
+ *            ahead and behind (capped at 100, / 10), 1 / n, and whether c catches the one ahead
+ *            (and the one behind catches c) before the line, as a capped share of the remaining
+ *            race; x_c[14..15] = 0
  *   encoder  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)  (width 128)
  *   context  g = mean over the race's competitors of h3
  *   head     u = relu(W4 [h3; g] + b4) (256 -> 128), logit = w5 . u + b5
@@ -18,7 +25,7 @@
  * Matrix products take bfloat16 operands with float32 accumulation; the master weights and
  * the Adam state are float32.  The forward kernel waits on the tensor cores with a bounded
  * wait (2 s); a wait that gives up is reported by bbe_surrogate_status.  Parameters are one float vector of bbe_surrogate_num_params()
- * values: W1 [128][16] (inputs 5..15 zero), b1 [128], W2 [128][128], b2, W3 [128][128], b3,
+ * values: W1 [128][16] (input columns 14 and 15 are zero), b1 [128], W2 [128][128], b2, W3 [128][128], b3,
  * W4 [128][256], b4, w5 [128], b5 [1] (row-major [out][in]).
  *
  * Conventions are those of bbe.h (status codes, thread-local bbe_last_error, caller-owned
