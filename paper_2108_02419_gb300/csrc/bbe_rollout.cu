@@ -313,10 +313,27 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
             // delta(v_c): z for (race, rollout k, step t, competitor c)
             float z[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                z[v] = 0.0f;
-                if (running && valid[v])
-                    z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
+            for (int v = 0; v < V; ++v) z[v] = 0.0f;
+            if constexpr (V <= 2) {
+                // one branch per lane for its slots: a Philox block at the first step of four,
+                // else the cached normals (an invalid slot reads a harmless entry of its segment)
+                if (running) {
+                    if ((t & 3) == 0) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            if (valid[v])
+                                z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
+                    } else {
+                        const float *zrow = st.zc[(t & 3) - 1] + zbase;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) z[v] = zrow[s[v].c];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (running && valid[v])
+                        z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
             }
             // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
