@@ -98,11 +98,11 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
 // rollout ends when K = min(places, n) competitors have crossed; competitors past the line keep
 // moving and keep their rank slots; a competitor has finished exactly when its position is at
 // least L, since positions only grow).
-// Launch bounds: the win mode keeps the compiler's own register choice (64 for one or two
-// competitors per lane, about 100 for four); the place mode, which holds its finishing order in
-// registers, may use up to 128 rather than spill (measured faster on GB300).
+// Launch bounds: the win mode with one or two competitors per lane keeps the compiler's own
+// register choice (64); the place mode, which holds its finishing order in registers, and four
+// competitors per lane may use up to 128 rather than spill (each measured faster on GB300).
 template <int DIST, int V, int MODE>
-__global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(RolloutLaunch l)
+__global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kernel(RolloutLaunch l)
 {
     extern __shared__ WarpStage stage_all[];
     WarpStage &st = stage_all[threadIdx.x >> 5];
@@ -314,26 +314,18 @@ __global__ void __launch_bounds__(512, MODE == 1 ? 1 : 0) rollout_kernel(Rollout
             float z[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) z[v] = 0.0f;
-            if constexpr (V <= 2) {
-                // one branch per lane for its slots: a Philox block at the first step of four,
-                // else the cached normals (an invalid slot reads a harmless entry of its segment)
-                if (running) {
-                    if ((t & 3) == 0) {
+            // one branch per lane for all its slots: a Philox block at the first step of four,
+            // else the cached normals (an invalid slot reads a harmless entry of its segment)
+            if (running) {
+                if ((t & 3) == 0) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            if (valid[v])
-                                z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
-                    } else {
-                        const float *zrow = st.zc[(t & 3) - 1] + zbase;
+                    for (int v = 0; v < V; ++v)
+                        if (valid[v]) z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
+                } else {
+                    const float *zrow = st.zc[(t & 3) - 1] + zbase;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) z[v] = zrow[s[v].c];
-                    }
+                    for (int v = 0; v < V; ++v) z[v] = zrow[s[v].c];
                 }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (running && valid[v])
-                        z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
             }
             // Eq. 1, then advance
             const bool aborted = running && t >= l.max_steps;
