@@ -315,8 +315,23 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
 #pragma unroll
             for (int v = 0; v < V; ++v) z[v] = 0.0f;
             // one branch per lane for all its slots: a Philox block at the first step of four,
-            // else the cached normals (an invalid slot reads a harmless entry of its segment)
-            if (running) {
+            // else the cached normals (an invalid slot reads a harmless entry of its segment).
+            // In win mode every rollout starts on the warp's common 4-step phase, so the step
+            // within the Philox block follows the warp's step counter and the branch is one the
+            // whole warp takes (measured faster there, slower in place mode).
+            if constexpr (MODE == 0) {
+                const unsigned phase = gstep & 3u;
+                if (phase == 0u) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (running && valid[v])
+                            z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
+                } else {
+                    const float *zrow = st.zc[phase - 1u] + zbase;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) z[v] = zrow[s[v].c];
+                }
+            } else if (running) {
                 if ((t & 3) == 0) {
 #pragma unroll
                     for (int v = 0; v < V; ++v)
@@ -504,9 +519,9 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                         hit_limit |= !seg_fin;
                         k += nseg;
                         active = k < kend;
-                        // packed segments start rollouts on a common 4-step phase so the
-                        // warp draws its Philox blocks together
-                        t = nseg > 1 ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
+                        // packed segments (in win mode, all) start rollouts on a common 4-step
+                        // phase so the warp draws its Philox blocks together
+                        t = (MODE == 0 || nseg > 1) ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const int hc = kSmemWins ? (valid[v] ? st.init_c[rank0 + v] : 0) : home[v];
