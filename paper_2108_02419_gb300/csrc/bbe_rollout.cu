@@ -489,7 +489,32 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
             }
 
             // advance, or start the segment's next rollout
-            if (active) {
+            if constexpr (MODE == 0) {
+                // win mode: the common case (advance) without branches; a slot that does not
+                // hold a competitor stays at +infinity (its step is floored or infinite)
+                const bool adv = running && !seg_done;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    s[v].d = adv ? dn[v] : s[v].d;
+                    s[v].prev = adv ? S[v] : s[v].prev;
+                }
+                t += (active && !seg_done) ? 1 : 0;
+                if (seg_done) {
+                    steps += seg_fin ? (t + 1) : t;
+                    hit_limit |= !seg_fin;
+                    k += nseg;
+                    active = k < kend;
+                    // every rollout starts on the warp's common 4-step phase
+                    t = -int((4u - ((gstep + 1u) & 3u)) & 3u);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int hc = kSmemWins ? (valid[v] ? st.init_c[rank0 + v] : 0) : home[v];
+                        s[v].c = hc;
+                        s[v].d = valid[v] ? st.d0[hc] : INFINITY;
+                        s[v].prev = st.prev0[hc];
+                    }
+                }
+            } else if (active) {
                 if (running) {
                     if (seg_done) {
                         if constexpr (MODE == 1) {
