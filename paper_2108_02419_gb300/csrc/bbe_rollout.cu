@@ -13,7 +13,10 @@
 // lane).  Finishing is detected with a ballot; the winner (least within-step crossing time,
 // lowest index on ties) comes from the ballot mask, or from a shuffle reduction when several
 // cross in the same step.  Wins are counted per slot in registers (one or two slots per lane)
-// or per warp in shared memory (four), and reach the global counts once per work item.  The same kernel in place mode
+// or per warp in shared memory (four), and reach the global counts once per work item.  The
+// hot loop keeps branches few: one per lane for the normal draws (a Philox block at the first
+// step of four, else cached normals), and in win mode the advance by select, with the restart
+// of a finished segment the only branch of the common path's tail.  The same kernel in place mode
 // runs every rollout to the K-th finisher (include/bbe.h: bbe_place_counts): finished
 // competitors keep moving in their rank slots, the finishers of a step are placed by repeated
 // argmin of (crossing time, index), the lane of place j records its competitor, and completed
@@ -98,6 +101,7 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
 // rollout ends when K = min(places, n) competitors have crossed; competitors past the line keep
 // moving and keep their rank slots; a competitor has finished exactly when its position is at
 // least L, since positions only grow).
+//
 // Launch bounds: the win mode with one or two competitors per lane keeps the compiler's own
 // register choice (64); the place mode, which holds its finishing order in registers, and four
 // competitors per lane may use up to 128 rather than spill (each measured faster on GB300).
