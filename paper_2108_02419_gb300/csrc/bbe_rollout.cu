@@ -224,9 +224,14 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                 // an overtake in the last step (or equal positions): restore rank order by
                 // odd-even transposition, then handle ties by a search over the segment
                 if (V == 1) {
-                    const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                    const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                    bool ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
+                    // win mode: the position check above covers every out-of-order pair (and
+                    // ties); the place mode measured faster with its own check by key
+                    bool ooo = bad;
+                    if constexpr (MODE == 1) {
+                        const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                        const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                        ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
+                    }
                     while (__any_sync(kFull, ooo)) {
     #pragma unroll
                         for (int ph = 0; ph < 2; ++ph) {
@@ -245,11 +250,15 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                 } else {
                     // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs are the
                     // inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of lane q+1)
-                    bool ooo = false;
-    #pragma unroll
-                    for (int v = 0; v + 1 < V; ++v)
-                        ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
-                    {
+                    // win mode: the position check above covers every out-of-order pair (ties
+                    // cost one pass that swaps nothing); the place mode measured faster with its
+                    // own check by key
+                    bool ooo = bad;
+                    if constexpr (MODE == 1) {
+                        ooo = false;
+#pragma unroll
+                        for (int v = 0; v + 1 < V; ++v)
+                            ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
                         const float nd = __shfl_down_sync(kFull, s[0].d, 1);
                         const int nc = __shfl_down_sync(kFull, s[0].c, 1);
                         ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc);
