@@ -75,7 +75,6 @@ template <int DIST>
 __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uint32_t k, uint32_t rid,
                                         const uint32_t (&rk)[20])
 {
-    if ((t & 3) != 0) return st.zc[(t & 3) - 1][zi];
     const Words4 wd = philox4x32_10(k, uint32_t(t) >> 2, uint32_t(c), rid, rk);
     float z0, z1, z2, z3;
     if (DIST == BBE_DIST_NORMAL) {
@@ -203,9 +202,7 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
             // verify the rank order: every slot's next rank must be strictly in front.
             float fd[V], fp[V];
             bool hf[V];
-            auto next_ranks = [&]() {
-                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                const float np = __shfl_down_sync(kFull, s[0].prev, 1);
+            auto set_next = [&](float nd, float np) {
 #pragma unroll
                 for (int v = 0; v < V - 1; ++v) {
                     fd[v] = s[v + 1].d;
@@ -216,92 +213,102 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                 fp[V - 1] = np;
                 hf[V - 1] = valid[V - 1] && has_next_lane;
             };
+            auto next_ranks = [&]() {
+                const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                set_next(nd, __shfl_down_sync(kFull, s[0].prev, 1));
+            };
             next_ranks();
             bool bad = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) bad |= hf[v] && !(fd[v] > s[v].d);
             if (__any_sync(kFull, bad)) {
                 // an overtake in the last step (or equal positions): restore rank order by
-                // odd-even transposition, then handle ties by a search over the segment
-                if (V == 1) {
-                    // win mode: the position check above covers every out-of-order pair (and
-                    // ties); the place mode measured faster with its own check by key
-                    bool ooo = bad;
-                    if constexpr (MODE == 1) {
-                        const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                        const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                        ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd, nc);
-                    }
-                    while (__any_sync(kFull, ooo)) {
-    #pragma unroll
-                        for (int ph = 0; ph < 2; ++ph) {
-                            const bool lower = ((ql - ph) & 1) == 0;
-                            const int pq = lower ? ql + 1 : ql - 1;
-                            const bool ok = lane_used && pq >= 0 && pq < nl;
-                            const int pl = ok ? segbase + pq : lane;
-                            const Slot o = shfl_slot(s[0], pl);
-                            const bool mine_after = key_gt(s[0].d, s[0].c, o.d, o.c);
-                            if (ok && (lower ? mine_after : !mine_after)) s[0] = o;
-                        }
-                        const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
-                        const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
-                        ooo = has_next_lane && key_gt(s[0].d, s[0].c, nd2, nc2);
-                    }
-                } else {
-                    // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs are the
-                    // inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of lane q+1)
-                    // win mode: the position check above covers every out-of-order pair (ties
-                    // cost one pass that swaps nothing); the place mode measured faster with its
-                    // own check by key
-                    bool ooo = bad;
-                    if constexpr (MODE == 1) {
-                        ooo = false;
+                // odd-even transposition, then handle ties by a search over the segment.
+                // after(by_key, a, b): a belongs behind b, by position then competitor index,
+                // or by position alone
+                auto after = [](bool by_key, const Slot &a, const Slot &b) {
+                    return by_key ? key_gt(a.d, a.c, b.d, b.c) : a.d > b.d;
+                };
+                // some pair of neighbouring ranks is out of order by key
+                auto key_ooo = [&]() {
+                    bool o = false;
 #pragma unroll
-                        for (int v = 0; v + 1 < V; ++v)
-                            ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
-                        const float nd = __shfl_down_sync(kFull, s[0].d, 1);
-                        const int nc = __shfl_down_sync(kFull, s[0].c, 1);
-                        ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc);
-                    }
+                    for (int v = 0; v + 1 < V; ++v) o |= valid[v + 1] && after(true, s[v], s[v + 1]);
+                    const float nd = __shfl_down_sync(kFull, s[0].d, 1);
+                    const int nc = __shfl_down_sync(kFull, s[0].c, 1);
+                    return o || (has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd, nc));
+                };
+                // odd-even transposition passes while any lane has a pair out of order; returns
+                // the position of the next lane's first rank after the last pass
+                auto transpose = [&](bool by_key, bool ooo) {
+                    float nd = 0.0f;
                     while (__any_sync(kFull, ooo)) {
-    #pragma unroll
-                        for (int v = 0; v + 1 < V; v += 2) {
-                            if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
-                                const Slot tmp = s[v];
-                                s[v] = s[v + 1];
-                                s[v + 1] = tmp;
-                            }
-                        }
-    #pragma unroll
-                        for (int v = 1; v + 1 < V; v += 2) {
-                            if (valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c)) {
-                                const Slot tmp = s[v];
-                                s[v] = s[v + 1];
-                                s[v + 1] = tmp;
-                            }
-                        }
-                        const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
-                        const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
-                        const bool swap_hi = has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, from_next.d, from_next.c);
-                        const bool swap_lo = lane_used && ql > 0 && key_gt(from_prev.d, from_prev.c, s[0].d, s[0].c);
-                        if (swap_hi) s[V - 1] = from_next;
-                        if (swap_lo) s[0] = from_prev;
                         ooo = false;
-    #pragma unroll
-                        for (int v = 0; v + 1 < V; ++v)
-                            ooo |= valid[v + 1] && key_gt(s[v].d, s[v].c, s[v + 1].d, s[v + 1].c);
-                        const float nd2 = __shfl_down_sync(kFull, s[0].d, 1);
-                        const int nc2 = __shfl_down_sync(kFull, s[0].c, 1);
-                        ooo |= has_next_lane && key_gt(s[V - 1].d, s[V - 1].c, nd2, nc2);
+                        if (V == 1) {
+#pragma unroll
+                            for (int ph = 0; ph < 2; ++ph) {
+                                const bool lower = ((ql - ph) & 1) == 0;
+                                const int pq = lower ? ql + 1 : ql - 1;
+                                const bool ok = lane_used && pq >= 0 && pq < nl;
+                                const int pl = ok ? segbase + pq : lane;
+                                const Slot o = shfl_slot(s[0], pl);
+                                const bool sw = lower ? after(by_key, s[0], o) : after(by_key, o, s[0]);
+                                if (ok && sw) s[0] = o;
+                            }
+                        } else {
+                            // ranks q*V + v: even pairs (2i, 2i+1) lie inside a lane; odd pairs
+                            // are the inner ones (1,2), (3,4).. of a lane and (V-1 of lane q, 0 of
+                            // lane q+1)
+#pragma unroll
+                            for (int v = 0; v + 1 < V; v += 2) {
+                                if (valid[v + 1] && after(by_key, s[v], s[v + 1])) {
+                                    const Slot tmp = s[v];
+                                    s[v] = s[v + 1];
+                                    s[v + 1] = tmp;
+                                }
+                            }
+#pragma unroll
+                            for (int v = 1; v + 1 < V; v += 2) {
+                                if (valid[v + 1] && after(by_key, s[v], s[v + 1])) {
+                                    const Slot tmp = s[v];
+                                    s[v] = s[v + 1];
+                                    s[v + 1] = tmp;
+                                }
+                            }
+                            const Slot from_next = shfl_slot(s[0], has_next_lane ? lane + 1 : lane);
+                            const Slot from_prev = shfl_slot(s[V - 1], (lane_used && ql > 0) ? lane - 1 : lane);
+                            const bool swap_hi = has_next_lane && after(by_key, s[V - 1], from_next);
+                            const bool swap_lo = lane_used && ql > 0 && after(by_key, from_prev, s[0]);
+                            if (swap_hi) s[V - 1] = from_next;
+                            if (swap_lo) s[0] = from_prev;
+#pragma unroll
+                            for (int v = 0; v + 1 < V; ++v) ooo |= valid[v + 1] && after(by_key, s[v], s[v + 1]);
+                        }
+                        nd = __shfl_down_sync(kFull, s[0].d, 1);
+                        const int nc = by_key ? __shfl_down_sync(kFull, s[0].c, 1) : 0;
+                        ooo |= has_next_lane && after(by_key, s[V - 1], Slot{nc, nd, 0.0f});
                     }
+                    return nd;
+                };
+                if constexpr (MODE == 0) {
+                    // win mode: order by position first, entered on the check above (equal
+                    // positions cost one pass that swaps nothing); competitors at equal positions
+                    // are put in index order below, only when there are any.  The last pass's
+                    // shuffle gives the next lane's first position.
+                    const float nd = transpose(false, bad);
+                    set_next(nd, __shfl_down_sync(kFull, s[0].prev, 1));
+                } else {
+                    // place mode: by key throughout (measured faster there)
+                    transpose(true, key_ooo());
+                    next_ranks();
                 }
-
-                next_ranks();
                 bool tie = false;
 #pragma unroll
                 for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
                 if (__any_sync(kFull, tie)) {
-                    // equal positions: the first later rank with a larger position
+                    // equal positions: index order among them (win mode), then for each slot
+                    // the first later rank with a larger position
+                    if constexpr (MODE == 0) transpose(true, key_ooo());
 #pragma unroll
                     for (int v = 0; v < V; ++v) hf[v] = false;
                     for (int j = 0; j < nl; ++j) {
