@@ -290,25 +290,19 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                     }
                     return nd;
                 };
-                if constexpr (MODE == 0) {
-                    // win mode: order by position first, entered on the check above (equal
-                    // positions cost one pass that swaps nothing); competitors at equal positions
-                    // are put in index order below, only when there are any.  The last pass's
-                    // shuffle gives the next lane's first position.
-                    const float nd = transpose(false, bad);
-                    set_next(nd, __shfl_down_sync(kFull, s[0].prev, 1));
-                } else {
-                    // place mode: by key throughout (measured faster there)
-                    transpose(true, key_ooo());
-                    next_ranks();
-                }
+                // order by position first, entered on the check above (equal positions cost
+                // one pass that swaps nothing); competitors at equal positions are put in index
+                // order below, only when there are any.  The last pass's shuffle gives the next
+                // lane's first position.
+                const float nd_sorted = transpose(false, bad);
+                set_next(nd_sorted, __shfl_down_sync(kFull, s[0].prev, 1));
                 bool tie = false;
 #pragma unroll
                 for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
                 if (__any_sync(kFull, tie)) {
                     // equal positions: index order among them (win mode), then for each slot
                     // the first later rank with a larger position
-                    if constexpr (MODE == 0) transpose(true, key_ooo());
+                    transpose(true, key_ooo());
 #pragma unroll
                     for (int v = 0; v < V; ++v) hf[v] = false;
                     for (int j = 0; j < nl; ++j) {
