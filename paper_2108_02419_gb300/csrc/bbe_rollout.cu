@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
 #pragma unroll
                 for (int v = 0; v < V; ++v) tie |= hf[v] && fd[v] == s[v].d;
                 if (__any_sync(kFull, tie)) {
-                    // equal positions: index order among them (win mode), then for each slot
-                    // the first later rank with a larger position
+                    // equal positions: index order among them, then for each slot the first
+                    // later rank with a larger position
                     transpose(true, key_ooo());
 #pragma unroll
                     for (int v = 0; v < V; ++v) hf[v] = false;
