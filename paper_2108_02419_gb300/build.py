@@ -27,6 +27,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "bbe_capi.cu": ["--fmad=false"],
     "bbe_rollout.cu": ["--fmad=false"],
+    "bbe_win.cu": ["--fmad=false"],
     "bbe_noalloc.cu": ["--fmad=false"],
     "bbe_trajectory.cu": ["--fmad=false"],
     "bbe_surrogate.cu": [],

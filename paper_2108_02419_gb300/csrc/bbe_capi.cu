@@ -75,10 +75,27 @@ bbe_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s, con
 
 void free_graph(bbe_batch *b)
 {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);  // an executable graph still running is freed when it ends
     b->gexec = nullptr;
     b->g_counts = nullptr;
     b->g_steps = nullptr;
+}
+
+cudaError_t ensure_free_stream(bbe_batch *b)
+{
+    return b->free_stream ? cudaSuccess : cudaStreamCreateWithFlags(&b->free_stream, cudaStreamNonBlocking);
+}
+
+// Free `p` (stream-ordered allocation) on the batch's free stream once every recorded use of the
+// batch has completed; the host does not wait.
+cudaError_t free_behind_uses(bbe_batch *b, void *p)
+{
+    if (!p) return cudaSuccess;
+    cudaError_t e = ensure_free_stream(b);
+    for (auto &u : b->uses)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->free_stream, u.second, 0);
+    if (e == cudaSuccess) e = cudaFreeAsync(p, b->free_stream);
+    return e;
 }
 
 // Expected steps of one rollout: the leader's remaining distance over the largest mean
@@ -188,11 +205,17 @@ bbe_status build_items(bbe_batch *b)
         b->n_items_v[g] = int32_t(sorted.size() - before);
     }
 
-    if (b->d_items) cudaFree(b->d_items);
-    b->d_items = nullptr;
-    BBE_CUDA_TRY(cudaMalloc(&b->d_items, std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem)));
-    BBE_CUDA_TRY(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice));
+    // the new list is in place before the call returns; the old one is freed behind this batch's
+    // work that may still read it
+    bbe::WorkItem *fresh = nullptr;
+    BBE_CUDA_TRY(ensure_free_stream(b));
+    BBE_CUDA_TRY(cudaMallocAsync(&fresh, std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), b->free_stream));
+    BBE_CUDA_TRY(cudaMemcpyAsync(fresh, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice,
+                                 b->free_stream));
+    BBE_CUDA_TRY(cudaStreamSynchronize(b->free_stream));
     free_graph(b);
+    BBE_CUDA_TRY(free_behind_uses(b, b->d_items));
+    b->d_items = fresh;
     return BBE_OK;
 }
 
@@ -366,7 +389,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     std::vector<float> &h_sigma = b->h_sigma, &h_rho = b->h_rho, &h_P = b->h_P, &h_theta = b->h_theta,
                        &h_prev = b->h_prev;
     auto fail = [&](bbe_status code) {
-        delete b;
+        bbe_destroy_batch(b);  // frees whatever was allocated so far
         return code;
     };
     if ((st = copy_in(b->h_L.data(), track_len, n_races * sizeof(float), s, "track_len")) ||
@@ -445,7 +468,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     add(4 * kGroups); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) e = cudaMalloc(&b->arena, bytes);
+    if (e == cudaSuccess) e = cudaMallocAsync(&b->arena, bytes, s);
     if (e != cudaSuccess) {
         set_error(std::string("device allocation: ") + cudaGetErrorString(e));
         return fail(BBE_ERR_CUDA);
@@ -513,6 +536,21 @@ bbe_status bbe::set_first_rollouts(bbe_batch *b, const int64_t *k0)
     return build_items(b);
 }
 
+cudaError_t bbe::note_use(const bbe_batch *b, cudaStream_t s)
+{
+    // work captured into a caller's graph runs when that graph does: its lifetime is the caller's
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    for (auto &u : b->uses)
+        if (u.first == s) return cudaEventRecord(u.second, s);
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    b->uses.emplace_back(s, ev);
+    return cudaEventRecord(ev, s);
+}
+
 extern "C" {
 
 const char *bbe_last_error(void) { return bbe::g_last_error.c_str(); }
@@ -540,11 +578,13 @@ bbe_status bbe_rollout_batch(bbe_batch *b, int32_t *win_counts, int64_t *steps_t
         bbe_status st = ensure_aux(b);
         if (st) return st;
         BBE_CUDA_TRY(enqueue_pass(b, win_counts, steps_total, as_stream(cuda_stream), b->side_stream));
+        BBE_CUDA_TRY(bbe::note_use(b, as_stream(cuda_stream)));
         return BBE_OK;
     }
     bbe_status st = ensure_graph(b, win_counts, steps_total);
     if (st) return st;
     BBE_CUDA_TRY(cudaGraphLaunch(b->gexec, as_stream(cuda_stream)));
+    BBE_CUDA_TRY(bbe::note_use(b, as_stream(cuda_stream)));
     return BBE_OK;
 }
 
@@ -555,6 +595,7 @@ bbe_status bbe_win_probs(const bbe_batch *b, const int32_t *win_counts, float *p
         return BBE_ERR_ARG;
     }
     BBE_CUDA_TRY(bbe::launch_win_probs(b->dev, win_counts, probs, odds, as_stream(cuda_stream)));
+    BBE_CUDA_TRY(bbe::note_use(b, as_stream(cuda_stream)));
     return BBE_OK;
 }
 
@@ -579,6 +620,7 @@ bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, i
         l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
         BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
     }
+    BBE_CUDA_TRY(bbe::note_use(b, s));
     return BBE_OK;
 }
 
@@ -631,9 +673,10 @@ bbe_status bbe_order_counts(bbe_batch *b, int32_t places, int32_t *order_counts,
     cudaStream_t s = as_stream(cuda_stream);
     if (b->order_places != places || !b->d_order_off) {
         order_layout(b, places, b->h_order_off);
-        if (b->d_order_off) cudaFree(b->d_order_off);
+        BBE_CUDA_TRY(free_behind_uses(b, b->d_order_off));
         b->d_order_off = nullptr;
-        BBE_CUDA_TRY(cudaMalloc(&b->d_order_off, b->h_order_off.size() * sizeof(int64_t)));
+        b->order_places = 0;
+        BBE_CUDA_TRY(cudaMallocAsync(&b->d_order_off, b->h_order_off.size() * sizeof(int64_t), s));
         BBE_CUDA_TRY(cudaMemcpyAsync(b->d_order_off, b->h_order_off.data(), b->h_order_off.size() * sizeof(int64_t),
                                      cudaMemcpyHostToDevice, s));  // the host copy lives with the batch
         b->order_places = places;
@@ -694,6 +737,7 @@ bbe_status bbe_place_probs(const bbe_batch *b, int32_t places, const int32_t *pl
         return BBE_ERR_ARG;
     }
     BBE_CUDA_TRY(bbe::launch_place_probs(b->dev, places, place_counts, top, probs, as_stream(cuda_stream)));
+    BBE_CUDA_TRY(bbe::note_use(b, as_stream(cuda_stream)));
     return BBE_OK;
 }
 
@@ -769,7 +813,7 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
             if ((st = bbe_batch_set_cfg(b, &c))) goto done;
             // warm the item list, then time one full pass
             cudaEventRecord(e0, s);
-            if (enqueue_pass(b, win_counts, nullptr, s, nullptr) != cudaSuccess) {
+            if (enqueue_pass(b, win_counts, nullptr, s, nullptr) != cudaSuccess || bbe::note_use(b, s) != cudaSuccess) {
                 set_error("autotune launch failed");
                 st = BBE_ERR_CUDA;
                 goto done;
@@ -829,16 +873,28 @@ bbe_status bbe_batch_launches(const bbe_batch *b, int32_t *kernels_per_pass)
 void bbe_destroy_batch(bbe_batch *b)
 {
     if (!b) return;
-    cudaDeviceSynchronize();
+    int cur = -1;
+    const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != b->device && cudaSetDevice(b->device) == cudaSuccess;
+    // The memory is freed in stream order behind the batch's own recorded work: the host waits
+    // for nothing and no other stream is held up.  Streams and events still in use are released
+    // by CUDA when their work completes.
     free_graph(b);
+    for (void *p : {static_cast<void *>(b->d_items), static_cast<void *>(b->d_order_off), b->arena}) {
+        if (p && free_behind_uses(b, p) != cudaSuccess) {
+            // no free stream could be made: wait for this batch's uses on the host instead
+            cudaGetLastError();
+            for (auto &u : b->uses) cudaEventSynchronize(u.second);
+            cudaFree(p);
+        }
+    }
+    for (auto &u : b->uses) cudaEventDestroy(u.second);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     if (b->side_stream) cudaStreamDestroy(b->side_stream);
+    if (b->free_stream) cudaStreamDestroy(b->free_stream);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->d_items) cudaFree(b->d_items);
-    if (b->d_order_off) cudaFree(b->d_order_off);
-    if (b->arena) cudaFree(b->arena);
     delete b;
+    if (switched) cudaSetDevice(cur);
 }
 
 }  // extern "C"

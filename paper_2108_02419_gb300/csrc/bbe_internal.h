@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "bbe.h"
@@ -126,6 +127,13 @@ struct bbe_batch {
     cudaGraphExec_t gexec = nullptr;
     int32_t *g_counts = nullptr;
     int64_t *g_steps = nullptr;
+
+    // Streams that carried work reading this batch, each with an event recorded after its
+    // latest use.  The batch's device memory comes from the stream-ordered allocator and is
+    // freed on `free_stream` behind those events, so replacing a buffer or destroying the batch
+    // waits for this batch's own work only, never for the whole device.
+    mutable std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
+    cudaStream_t free_stream = nullptr;
 };
 
 
@@ -140,5 +148,7 @@ bbe_status stage_batch(bbe_batch **out, int32_t n_races, const int32_t *race_off
 // k0[r] + R[r] <= 2^31 - 1).  The counts of such a batch added to those of rollouts
 // 0 .. k0[r] - 1 equal the counts of one batch of k0[r] + R[r] rollouts.
 bbe_status set_first_rollouts(bbe_batch *b, const int64_t *k0);
+// Record that work just enqueued on `s` reads the batch (see bbe_batch::uses).
+cudaError_t note_use(const bbe_batch *b, cudaStream_t s);
 }  // namespace bbe
 

@@ -12,6 +12,7 @@
 //           log m = f g(f), g a degree-9 fit of log(1 + f) / f on [sqrt(1/2) - 1, sqrt(2) - 1]
 //           (least squares on Chebyshev nodes reweighted towards the minimax relative
 //           error) [Horner, fma], log x = e ln2_hi + (e ln2_lo + log m).
+//   sqrt:   correctly rounded (see sqrt_f32x2).
 //   sincos: u = m24 2^-24, q = round(4u) by integer arithmetic, f = u - q/4 exactly,
 //           Taylor series of sin(2 pi f) to degree 9 and cos(2 pi f) to degree 10 in f
 //           [Horner, fma], then the quadrant rotation by q mod 4.
@@ -28,17 +29,16 @@ struct Words4 {
 };
 
 // Philox4x32-10 with the round keys given: rk[2i], rk[2i+1] are the key words of round i.
-// With rk in the kernel's parameter block every round is two 32x32->64 multiplies and two
-// three-input XORs with constant-bank operands.
+// With rk in the kernel's parameter block every round is the high and low halves of two
+// 32x32-bit products (taken as two separate multiplies each, which issue faster on sm_103a than
+// one 64-bit product) and two three-input XORs with constant-bank operands.
 __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                 const uint32_t (&rk)[20])
 {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint64_t p0 = uint64_t(0xD2511F53u) * c0;
-        const uint64_t p1 = uint64_t(0xCD9E8D57u) * c2;
-        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
-        const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
         c0 = hi1 ^ c1 ^ rk[2 * i];
         c2 = hi0 ^ c3 ^ rk[2 * i + 1];
         c1 = lo1;
@@ -103,15 +103,42 @@ __device__ __forceinline__ void sincos2pi_f32x2(uint32_t ma, uint32_t mb, float2
     c_out = make_float2((ua == 1u || ua == 2u) ? -ca : ca, (ub == 1u || ub == 2u) ? -cb : cb);
 }
 
+// Correctly rounded square roots of x.x and x.y, each -0 or a positive normal float (the
+// Box-Muller radius: -2 log u1 is -0 for u1 = 1, else in [1.19e-7, 33.3]).  Markstein's
+// sequence (P. Markstein, "IA-64 and Elementary Functions", 2000): from the hardware estimate
+// y ~ 1/sqrt(x) (rsqrtf), g = x y and h = y / 2; one coupled Newton step with the residual
+// e = 1/2 - g h refines both (g' = g + g e ~ sqrt x, h' = h + h e ~ 1 / (2 sqrt x), relative
+// errors of order 2^-44); the exact residual d = x - g'^2 (an FMA) then gives g' + d h',
+// rounded once, which is the correctly rounded square root.  A GPU test compares all 2^24
+// radii the generator can produce with the IEEE square root and with the CPU oracle's.
+__device__ __forceinline__ float2 sqrt_f32x2(float2 x)
+{
+    // x = -0: the estimate of the least normal keeps g = -0 * 2^63 = -0, and sqrt(-0) = -0
+    const float2 y = make_float2(rsqrtf(fmaxf(x.x, 0x1p-126f)), rsqrtf(fmaxf(x.y, 0x1p-126f)));
+    const float2 g = __fmul2_rn(x, y);
+    const float2 h = __fmul2_rn(y, splat2(0.5f));
+    const float2 e = __ffma2_rn(make_float2(-g.x, -g.y), h, splat2(0.5f));
+    const float2 g1 = __ffma2_rn(g, e, g);
+    const float2 h1 = __ffma2_rn(h, e, h);
+    const float2 d = __ffma2_rn(make_float2(-g1.x, -g1.y), g1, x);
+    return __ffma2_rn(d, h1, g1);
+}
+
+// The Box-Muller radii sqrt(-2 log u1) of the two pairs of a Philox block, u1 = ((wa >> 8) + 1)
+// 2^-24 in (0, 1] for wa = w0 and w2.
+__device__ __forceinline__ float2 bm_radius2(uint32_t wa, uint32_t wb)
+{
+    const float2 u1 = __fmul2_rn(make_float2(__uint2float_rn((wa >> 8) + 1u), __uint2float_rn((wb >> 8) + 1u)),
+                                 splat2(0x1p-24f));
+    return sqrt_f32x2(__fmul2_rn(splat2(-2.0f), log_f32x2(u1)));
+}
+
 // The two Box-Muller pairs of one Philox block: (z0, z1) = r (cos, sin) of (w0, w1) and
 // (z2, z3) of (w2, w3), with r = sqrt(-2 log u1), u1 = ((wa >> 8) + 1) 2^-24 in (0, 1] and
 // angle 2 pi (wb >> 8) 2^-24.
 __device__ __forceinline__ void box_muller2(const Words4 &wd, float &z0, float &z1, float &z2, float &z3)
 {
-    const float2 u1 = __fmul2_rn(make_float2(__uint2float_rn((wd.w0 >> 8) + 1u), __uint2float_rn((wd.w2 >> 8) + 1u)),
-                                 splat2(0x1p-24f));
-    const float2 m2l = __fmul2_rn(splat2(-2.0f), log_f32x2(u1));
-    const float2 radius = make_float2(__fsqrt_rn(m2l.x), __fsqrt_rn(m2l.y));
+    const float2 radius = bm_radius2(wd.w0, wd.w2);
     float2 sv, cv;
     sincos2pi_f32x2(wd.w1 >> 8, wd.w3 >> 8, sv, cv);
     const float2 zc = __fmul2_rn(radius, cv);

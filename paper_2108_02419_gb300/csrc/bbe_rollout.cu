@@ -678,24 +678,6 @@ int resident_v(int dist, int block)
 
 }  // namespace
 
-cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
-{
-    switch (slots_per_lane) {
-    case 4: return launch_v<4, 0>(l, stream);
-    case 2: return launch_v<2, 0>(l, stream);
-    default: return launch_v<1, 0>(l, stream);
-    }
-}
-
-int rollout_resident_blocks(int dist, int slots_per_lane, int block)
-{
-    switch (slots_per_lane) {
-    case 4: return resident_v<4, 0>(dist, block);
-    case 2: return resident_v<2, 0>(dist, block);
-    default: return resident_v<1, 0>(dist, block);
-    }
-}
-
 cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
     switch (slots_per_lane) {

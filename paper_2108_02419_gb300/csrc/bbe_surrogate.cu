@@ -1998,7 +1998,9 @@ bbe_status forward_all(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     SgArgs a = base_args(s, b);
     a.probs = probs;
     a.train = 0;
-    return launch_forward(s, a, int64_t(tiles.size()), st);
+    if ((e = launch_forward(s, a, int64_t(tiles.size()), st))) return e;
+    SG_TRY(bbe::note_use(b, st));
+    return BBE_OK;
 }
 
 }  // namespace
@@ -2229,6 +2231,7 @@ bbe_status bbe_surrogate_grad(bbe_surrogate *s, const bbe_batch *b, const float 
     if (loss) SG_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
     if ((e = train_pass(s, b, target, 0, int64_t(tiles.size()), b->n_races, loss, st))) return e;
     SG_TRY(cudaMemcpyAsync(grad, s->grad, N_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    SG_TRY(bbe::note_use(b, st));
     return BBE_OK;
 }
 
@@ -2289,6 +2292,7 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
             return e;
         s->step += 1;
     }
+    SG_TRY(bbe::note_use(b, st));
     return BBE_OK;
 }
 
@@ -2371,6 +2375,7 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
     s->fb_races = int64_t(mc.size());
     s->fb_rollouts = 0;
     if (!mc.empty() && (e = mc_fallback(s, b, mc, probs, st))) return e;
+    SG_TRY(bbe::note_use(b, st));
     if (used_mc) {
         SG_TRY(cudaMemcpyAsync(used_mc, flag.data(), flag.size(), cudaMemcpyHostToDevice, st));
         SG_TRY(cudaStreamSynchronize(st));

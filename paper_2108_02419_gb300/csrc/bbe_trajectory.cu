@@ -211,6 +211,7 @@ bbe_status bbe_race_trajectory(bbe_batch *b, uint32_t k, int32_t cap, float *pos
     default: bbe::trajectory_kernel<BBE_DIST_TWO_POINT><<<grid, 32 * warps, 0, s>>>(l); break;
     }
     TRAJ_TRY(cudaGetLastError());
+    TRAJ_TRY(bbe::note_use(b, s));
     return BBE_OK;
 }
 
@@ -319,6 +320,7 @@ bbe_status bbe_bettor_predictions(const bbe_batch *src, int32_t race, const floa
     bbe::fill_keys(a.round_key, a.b.seed_lo, a.b.seed_hi);
     bbe::predictors_kernel<<<unsigned((n_snapshots + 127) / 128), 128, 0, as_stream(cuda_stream)>>>(a);
     TRAJ_TRY(cudaGetLastError());
+    TRAJ_TRY(bbe::note_use(src, as_stream(cuda_stream)));
     return BBE_OK;
 }
 
