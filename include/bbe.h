@@ -83,9 +83,9 @@ typedef struct {
     int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 (halved, down
                                    to 1, for a batch too small to give every warp slot an item) */
     int32_t max_steps;          /* step limit per rollout, 1..2^30 */
-    int32_t slots_per_lane;     /* competitors per lane: 0 = automatic (the layout measured fastest
-                                   for the race's competitor count), 1, 2 or 4 = that layout for every
-                                   race large enough for it */
+    int32_t slots_per_lane;     /* competitors per lane, 0..4: 0 = automatic (two), 1..4 = that layout
+                                   for every race of at least that many competitors (smaller races
+                                   take two, or one for a lone competitor) */
 } bbe_launch_cfg;
 
 /* bbe_race_init -- validate a batch of race states and stage it on the current device.

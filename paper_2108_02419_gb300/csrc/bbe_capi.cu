@@ -112,24 +112,19 @@ double est_steps(const bbe_batch *b, int r)
 }
 
 // Slots-per-lane groups: group g holds races run with kSlots[g] competitors per lane.
-constexpr int kGroups = 3;
-constexpr int kSlots[kGroups] = {1, 2, 4};
+constexpr int kGroups = 4;
+constexpr int kSlots[kGroups] = {1, 2, 3, 4};
 
-int group_of(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
+int group_of(int v) { return v - 1; }
 
-// Competitors per lane for a race of n.  Automatic choice: the fastest layout per
-// competitor count, measured on GB300 (one GPU, 1,200 races of n competitors x 4,000 rollouts,
-// remaining distance U(100, 5000), normal steps): one per lane up to 5, four for 21..24
-// (two would leave a third of the lanes idle), two otherwise.  `mode` forces a layout where
-// the race is large enough.
+// Competitors per lane for a race of n.  Automatic choice: two, the layout measured fastest
+// on GB300 for the uneven mix of 2..24 competitors (3.13e11 competitor-steps/s against
+// 1.72e11 with one per lane up to 5 and four for 21..24, whose four-slot kernel runs short of
+// registers).  `mode` forces a layout.
 int slots_for(int n, int mode)
 {
-    if (mode == 1 || n < 2) return 1;
-    if (mode == 2) return 2;
-    if (mode == 4) return n >= 4 ? 4 : 2;
-    if (n <= 5) return 1;
-    if (n >= 21 && n <= 24) return 4;
-    return 2;
+    if (mode == 0) return 2;
+    return n >= mode ? mode : std::min(n, 2);  // a forced layout wider than the race falls back
 }
 
 bbe_status build_items(bbe_batch *b)
@@ -153,10 +148,9 @@ bbe_status build_items(bbe_batch *b)
         return std::max<int64_t>(std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace),
                                  min_chunk);
     };
-    auto nseg_of = [&](int r) {
+    auto nseg_of = [&](int r) {  // segments of a warp: floor(32 V / n) slots of n
         const int n = b->h_off[r + 1] - b->h_off[r];
-        const int v = slots_for(n, b->cfg.slots_per_lane);
-        return 32 / ((n + v - 1) / v);
+        return 32 * slots_for(n, b->cfg.slots_per_lane) / n;
     };
     // A batch too small to give every warp the GPU can hold (64 per SM) a work item runs fewer
     // rollouts per lane, down to one: the chunking decides which warp runs a rollout, never its
@@ -223,7 +217,7 @@ bbe_status check_cfg(const bbe_launch_cfg &c)
 {
     if (c.warps_per_block < 1 || c.warps_per_block > 16 || c.blocks_per_sm < 1 || c.blocks_per_sm > 32 ||
         c.rollouts_per_lane < 1 || c.rollouts_per_lane > 65536 || c.max_steps < 1 || c.max_steps > (1 << 30) ||
-        !(c.slots_per_lane == 0 || c.slots_per_lane == 1 || c.slots_per_lane == 2 || c.slots_per_lane == 4)) {
+        c.slots_per_lane < 0 || c.slots_per_lane > 4) {
         set_error("launch configuration out of range");
         return BBE_ERR_ARG;
     }

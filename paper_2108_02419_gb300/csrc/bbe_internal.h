@@ -63,7 +63,7 @@ inline void fill_round_keys(RolloutLaunch &l)
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;
 
-// slots_per_lane: competitors held per lane (1, 2 or 4).
+// slots_per_lane: competitors held per lane (1 to 4; the place-count kernel takes 1, 2 or 4).
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
 // Blocks of `block` threads of the rollout kernel that fit on one SM at once.
 int rollout_resident_blocks(int dist, int slots_per_lane, int block);
@@ -105,13 +105,13 @@ struct bbe_batch {
     // library-owned device memory
     void *arena = nullptr;
     DevBatch dev{};
-    WorkItem *d_items = nullptr;  // items grouped by slots per lane (1, 2, 4)
-    int32_t n_items_v[3] = {0, 0, 0};  // item counts per group
+    WorkItem *d_items = nullptr;  // items grouped by slots per lane (1, 2, 3, 4)
+    int32_t n_items_v[4] = {0, 0, 0, 0};  // item counts per group
     int32_t *d_queue = nullptr;        // one queue head per group
     int32_t *d_status = nullptr;
 
     bbe_launch_cfg cfg{};
-    int32_t resident[3] = {1, 1, 1};  // rollout-kernel blocks resident per SM, per group
+    int32_t resident[4] = {1, 1, 1, 1};  // rollout-kernel blocks resident per SM, per group
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 

@@ -78,11 +78,14 @@ __device__ __forceinline__ float2 log_f32x2(float2 x)
     return __ffma2_rn(ef, splat2(0x1.62e4p-1f), __ffma2_rn(ef, splat2(0x1.7f7d1cp-20f), logm));
 }
 
-// sin and cos of 2 pi m / 2^24 for m = ma and m = mb.
-__device__ __forceinline__ void sincos2pi_f32x2(uint32_t ma, uint32_t mb, float2 &s_out, float2 &c_out)
+// sin and cos of 2 pi m / 2^24 for m = wa >> 8 and m = wb >> 8.  With q = round(m / 2^22)
+// (halves up) the remainder m - q 2^22 in [-2^21, 2^21) is the low 22 bits of m sign-extended,
+// (int)(w << 2) >> 10, and q mod 4 is the top two bits of u = w + 2^29: bit 30 says whether
+// sin and cos trade places, bit 31 whether sin changes sign, and bit 31 of u + 2^30 whether
+// cos does (the sign flips are XORs of the sign bit, exactly the negations).
+__device__ __forceinline__ void sincos2pi_words(uint32_t wa, uint32_t wb, float2 &s_out, float2 &c_out)
 {
-    const uint32_t qa = (ma + 0x200000u) >> 22, qb = (mb + 0x200000u) >> 22;
-    const int32_t fa = int32_t(ma) - int32_t(qa << 22), fb = int32_t(mb) - int32_t(qb << 22);
+    const int32_t fa = int32_t(wa << 2) >> 10, fb = int32_t(wb << 2) >> 10;
     const float2 f = __fmul2_rn(make_float2(__int2float_rn(fa), __int2float_rn(fb)), splat2(0x1p-24f));
     const float2 y = __fmul2_rn(f, f);
     float2 ps = __ffma2_rn(y, splat2(0x1.507834p+5f), splat2(-0x1.32d2ccp+6f));
@@ -96,11 +99,14 @@ __device__ __forceinline__ void sincos2pi_f32x2(uint32_t ma, uint32_t mb, float2
     pc = __ffma2_rn(y, pc, splat2(-0x1.3bd3ccp+4f));
     const float2 cv = __ffma2_rn(y, pc, splat2(1.0f));
     // rotate (sin, cos) of the remainder by q quarter turns
-    const uint32_t ua = qa & 3u, ub = qb & 3u;
-    const float aa = (ua & 1u) ? cv.x : sv.x, ab = (ub & 1u) ? cv.y : sv.y;
-    const float ca = (ua & 1u) ? sv.x : cv.x, cb = (ub & 1u) ? sv.y : cv.y;
-    s_out = make_float2((ua >= 2u) ? -aa : aa, (ub >= 2u) ? -ab : ab);
-    c_out = make_float2((ua == 1u || ua == 2u) ? -ca : ca, (ub == 1u || ub == 2u) ? -cb : cb);
+    const uint32_t ua = wa + 0x20000000u, ub = wb + 0x20000000u;
+    const bool oa = (ua & 0x40000000u) != 0u, ob = (ub & 0x40000000u) != 0u;
+    const float aa = oa ? cv.x : sv.x, ab = ob ? cv.y : sv.y;
+    const float ca = oa ? sv.x : cv.x, cb = ob ? sv.y : cv.y;
+    s_out = make_float2(__uint_as_float(__float_as_uint(aa) ^ (ua & 0x80000000u)),
+                        __uint_as_float(__float_as_uint(ab) ^ (ub & 0x80000000u)));
+    c_out = make_float2(__uint_as_float(__float_as_uint(ca) ^ ((ua + 0x40000000u) & 0x80000000u)),
+                        __uint_as_float(__float_as_uint(cb) ^ ((ub + 0x40000000u) & 0x80000000u)));
 }
 
 // Correctly rounded square roots of x.x and x.y, each -0 or a positive normal float (the
@@ -126,10 +132,12 @@ __device__ __forceinline__ float2 sqrt_f32x2(float2 x)
 
 // The Box-Muller radii sqrt(-2 log u1) of the two pairs of a Philox block, u1 = ((wa >> 8) + 1)
 // 2^-24 in (0, 1] for wa = w0 and w2.
+// (w & ~0xff) has at most 24 significant bits, so its conversion is exact, and
+// (w & ~0xff) 2^-32 + 2^-24 = ((w >> 8) + 1) 2^-24 is exact in one FMA.
 __device__ __forceinline__ float2 bm_radius2(uint32_t wa, uint32_t wb)
 {
-    const float2 u1 = __fmul2_rn(make_float2(__uint2float_rn((wa >> 8) + 1u), __uint2float_rn((wb >> 8) + 1u)),
-                                 splat2(0x1p-24f));
+    const float2 u1 = __ffma2_rn(make_float2(__uint2float_rn(wa & 0xFFFFFF00u), __uint2float_rn(wb & 0xFFFFFF00u)),
+                                 splat2(0x1p-32f), splat2(0x1p-24f));
     return sqrt_f32x2(__fmul2_rn(splat2(-2.0f), log_f32x2(u1)));
 }
 
@@ -140,7 +148,7 @@ __device__ __forceinline__ void box_muller2(const Words4 &wd, float &z0, float &
 {
     const float2 radius = bm_radius2(wd.w0, wd.w2);
     float2 sv, cv;
-    sincos2pi_f32x2(wd.w1 >> 8, wd.w3 >> 8, sv, cv);
+    sincos2pi_words(wd.w1, wd.w3, sv, cv);
     const float2 zc = __fmul2_rn(radius, cv);
     const float2 zs = __fmul2_rn(radius, sv);
     z0 = zc.x;

@@ -682,6 +682,7 @@ cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cud
 {
     switch (slots_per_lane) {
     case 4: return launch_v<4, 1>(l, stream);
+    case 3:
     case 2: return launch_v<2, 1>(l, stream);
     default: return launch_v<1, 1>(l, stream);
     }
@@ -691,6 +692,7 @@ int place_resident_blocks(int dist, int slots_per_lane, int block)
 {
     switch (slots_per_lane) {
     case 4: return resident_v<4, 1>(dist, block);
+    case 3:
     case 2: return resident_v<2, 1>(dist, block);
     default: return resident_v<1, 1>(dist, block);
     }

@@ -59,6 +59,7 @@ struct WinStage {
     int wins[32];                       // wins per competitor in the current work item
     int order[NS];                      // order[segment base + r]: slot holding rank r
     int rnk[NS];                        // rank of each slot
+    int flag[NS];                       // by segment base + rank: the slot there swaps with its successor
     unsigned segk[NS];                  // by segment base: rollout index handed to a restart
     unsigned long long key[NS];         // by segment base: least (tau, slot) of the step's finishers
     unsigned next_k;                    // next rollout index of the work item
@@ -148,7 +149,10 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
             st.rank0[lane] = rank;
             st.byrank0[rank] = lane;
         }
-        for (int i = lane; i < NS; i += 32) st.key[i] = kNoKey;
+        for (int i = lane; i < NS; i += 32) {
+            st.key[i] = kNoKey;
+            st.flag[i] = 0;
+        }
         if (lane == 0) st.next_k = unsigned(w.k_begin) + unsigned(nseg);
         __syncwarp();
 
@@ -166,6 +170,7 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
         const float *kra[V];   // register-lean variant: this slot's kappa (2 rho - 1)
         bool alive[V], pend[V];
         unsigned long long steps = 0;
+        unsigned gblk = 0;  // blocks run in this work item (saturating)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int slot = 32 * v + lane;
@@ -202,7 +207,7 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
         // A segment whose rank order broke (an overtake, or equal positions): odd-even
         // transposition by (position, slot) over the segment's rank table, then each slot's
         // successor, and i+ for a slot level with its successor.  pb is the step's row.
-        auto repair = [&](const char *pb, float (&fd)[V], float (&fp)[V]) {
+        auto full_sort = [&](const char *pb, float (&fd)[V], float (&fp)[V]) {
             const float2 *row = reinterpret_cast<const float2 *>(pb);
             int rk[V];
 #pragma unroll
@@ -261,6 +266,53 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
                 fp[v] = f.y;
             }
             __syncwarp();
+        };
+
+        // The common case first: isolated overtakes.  A slot whose successor is now strictly
+        // behind it swaps ranks with that successor, unless a neighbouring pair swaps too (a
+        // chain); then every slot re-reads its successor, and what is still out of order or
+        // level goes to the full sort.
+        auto repair = [&](const char *pb, float (&fd)[V], float (&fp)[V]) {
+            int rk[V];
+            bool init[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                rk[v] = alive[v] ? st.rnk[32 * v + lane] : 0;
+                init[v] = alive[v] && fd[v] < d[v];
+                if (init[v]) st.flag[sb[v] + rk[v]] = 1;
+            }
+            __syncwarp();
+            bool ok[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                ok[v] = init[v] && !(rk[v] > 0 && st.flag[sb[v] + rk[v] - 1]) && !(rk[v] + 2 < n && st.flag[sb[v] + rk[v] + 1]);
+            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!init[v]) continue;
+                st.flag[sb[v] + rk[v]] = 0;
+                if (ok[v]) {
+                    const int slot = 32 * v + lane;
+                    const int f = st.order[sb[v] + rk[v] + 1];
+                    st.order[sb[v] + rk[v]] = f;
+                    st.order[sb[v] + rk[v] + 1] = slot;
+                    st.rnk[f] = rk[v];
+                    st.rnk[slot] = rk[v] + 1;
+                }
+            }
+            __syncwarp();
+            bool again = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!alive[v]) continue;
+                const int r1 = st.rnk[32 * v + lane] + 1;
+                fo[v] = r1 < n ? st.order[sb[v] + r1] * int(sizeof(float2)) : kSent;
+                const float2 f = *reinterpret_cast<const float2 *>(pb + fo[v]);
+                fd[v] = f.x;
+                fp[v] = f.y;
+                again |= !(f.x > d[v]);
+            }
+            if (__any_sync(kAll, again)) full_sort(pb, fd, fp);
         };
 
         // One step of every slot: sub-step J of the Philox block (its normal is z[v][J]); CHK
@@ -403,9 +455,14 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 draw_block<DIST>(kk[v], blk[v], uint32_t(32 * v + lane - sb[v]), rid, l.round_key, z[v]);
+            // no slot is further into its rollout than the work item's block count, so one
+            // warp-uniform compare rules out the step limit in all but the longest items
             bool near_limit = false;
+            if (gblk * 4u + 4u > unsigned(l.max_steps)) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) near_limit |= alive[v] && int(blk[v]) * 4 + 4 > l.max_steps;
+                for (int v = 0; v < V; ++v) near_limit |= alive[v] && int(blk[v]) * 4 + 4 > l.max_steps;
+            }
+            gblk += gblk < (1u << 28) ? 1u : 0u;
             if (__any_sync(kAll, near_limit)) {
                 step(std::integral_constant<int, 0>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 1>{}, std::true_type{}, z);

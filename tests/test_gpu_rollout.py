@@ -76,7 +76,7 @@ def test_uneven_batch_small(bbe):
     assert_matches_oracle(rb, counts, steps, probs)
 
 
-@pytest.mark.parametrize("slots", [1, 2, 4])
+@pytest.mark.parametrize("slots", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 11, 12, 13, 16, 17, 20, 21, 22, 23, 24, 31, 32])
 def test_every_segment_packing(bbe, n, slots):
     # one or two competitors per lane, every segment width and odd/even counts
@@ -95,7 +95,7 @@ def test_enumerated_two_point_races(bbe, case):
     assert_matches_oracle(rb, counts, steps)
 
 
-@pytest.mark.parametrize("slots", [1, 2, 4])
+@pytest.mark.parametrize("slots", [1, 2, 3, 4])
 @pytest.mark.parametrize("dist", [W.DIST_UNIFORM, W.DIST_TWO_POINT])
 def test_other_distributions(bbe, dist, slots):
     rb = W.uneven_batch(seed=7, n_races=40, rollouts=500, rem_lo=100.0, rem_hi=1500.0)
@@ -104,7 +104,7 @@ def test_other_distributions(bbe, dist, slots):
     assert_matches_oracle(rb, counts, steps, probs)
 
 
-@pytest.mark.parametrize("slots", [1, 2, 4])
+@pytest.mark.parametrize("slots", [1, 2, 3, 4])
 def test_heavy_blocking_ties_and_given_inputs(bbe, slots):
     # start-line races (all positions equal) with large thresholds, explicit preference
     # and previous steps: the blocked branch, equal-position ties and delta_min dominate
@@ -123,7 +123,7 @@ def test_launch_shape_does_not_change_counts(bbe):
     rb = W.uneven_batch(seed=8, n_races=60, r_lo_exp=1.5, r_hi_exp=3.0)
     ref = run_gpu(bbe, rb)
     for cfg in ({"warps_per_block": 1, "blocks_per_sm": 1, "rollouts_per_lane": 1},
-                {"slots_per_lane": 1}, {"slots_per_lane": 2}, {"slots_per_lane": 4},
+                {"slots_per_lane": 1}, {"slots_per_lane": 2}, {"slots_per_lane": 3}, {"slots_per_lane": 4},
                 {"warps_per_block": 16, "blocks_per_sm": 2, "rollouts_per_lane": 1000},
                 {"warps_per_block": 4, "blocks_per_sm": 16, "rollouts_per_lane": 7}):
         got = run_gpu(bbe, rb, cfg)
