@@ -415,11 +415,16 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
         };
 
         for (;;) {
-            // segments that finished in the last block start their next rollout
-            bool pany = false;
+            // segments that finished in the last block start their next rollout; one reduction
+            // says whether any did and whether anything still runs
+            bool pany = false, aany = false;
 #pragma unroll
-            for (int v = 0; v < V; ++v) pany |= pend[v];
-            if (__any_sync(kAll, pany)) {
+            for (int v = 0; v < V; ++v) {
+                pany |= pend[v];
+                aany |= alive[v];
+            }
+            const unsigned state = __reduce_or_sync(kAll, (pany ? 1u : 0u) | (aany ? 2u : 0u));
+            if (state & 1u) {
 #pragma unroll
                 for (int v = 0; v < V; ++v)
                     if (pend[v] && 32 * v + lane == sb[v]) st.segk[sb[v]] = atomicAdd(&st.next_k, 1u);
@@ -444,11 +449,13 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
                     }
                 }
                 __syncwarp();
-            }
-            bool any_alive = false;
+                bool any_alive = false;
 #pragma unroll
-            for (int v = 0; v < V; ++v) any_alive |= alive[v];
-            if (!__any_sync(kAll, any_alive)) break;
+                for (int v = 0; v < V; ++v) any_alive |= alive[v];
+                if (!__any_sync(kAll, any_alive)) break;
+            } else if (!(state & 2u)) {
+                break;
+            }
 
             // the block's normals: one Philox4x32-10 output per slot, counter (k, t >> 2, c, race)
             float z[V][4];
