@@ -36,12 +36,18 @@ from paper_2108_02419_gb300 import workloads as W  # noqa: E402
 METRIC = "competitor-steps/s & win-prob vectors/s, MC vs surrogate (≤0.01 max-abs err), 1 GB300"
 UNIT = "competitor-steps/s"
 
-# Algorithmic 32-bit operations per competitor-step of the rollout contract:
-#   Philox4x32-10 per 4 steps: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor) + 9 x 2 key adds = 98 -> 24.5
-#   Box-Muller per 2 steps: u1 (4), log (20), radius (2), sin/cos (22), 2 products      = 50 -> 25
-#   Eq. 1: responsiveness (2), i+ lookup and blocking test (6), step (3 or 1), floor (2),
-#          advance (1), finish test (1), bookkeeping (1)                                   = 16.5
-ALG_OPS_PER_COMPETITOR_STEP = 66.0
+# Algorithmic 32-bit operations per competitor-step of the rollout contract (the operations
+# the contract itself names, independent of how an implementation issues them):
+#   Philox4x32-10 per 4 steps: 10 rounds x (2 mul.hi + 2 mul.lo + 4 two-input xor)     = 80 -> 20
+#     (the round-key schedule depends on the seed alone and is computed once per launch)
+#   Box-Muller per pair (2 steps): u1 = ((w >> 8) + 1) 2^-24 (4); log: exponent and
+#     mantissa (4), range test and the two adjustments (3), f = m - 1 (1), 9 Horner FMAs,
+#     f g (1), int -> float of e (1), 2 FMAs (21); radius -2 log, sqrt (2); angle:
+#     shift, q (2), remainder (2), int -> float, scale (7); f^2, sin (4 FMA + 1 mul) and
+#     cos (5 FMA) (11); quadrant rotation (7); r cos, r sin (2)                            = 54 -> 27
+#   Eq. 1: R (2 FMA), successor load and order test (2), Delta and the theta test (2),
+#     free step (FMA + 2 mul), blocked step (min, mul), select, floor, advance, finish test = 15
+ALG_OPS_PER_COMPETITOR_STEP = 62.0
 SMS = 152
 LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock
 
@@ -235,7 +241,7 @@ def kernel_traffic(workload: str, races: int):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256()
-    for f in ("bbe_rollout.cu", "bbe_rng.cuh"):
+    for f in ("bbe_win.cu", "bbe_rng.cuh"):
         with open(os.path.join(ROOT, "paper_2108_02419_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
@@ -655,6 +661,175 @@ def run_population(dev, stream, bettors: int = 1000, dry_runs: int = 50) -> dict
     return out
 
 
+
+# ---------------------------------------------------------------------------- batching legs
+
+def _peak_ops() -> float:
+    return SMS * LANES_PER_SM * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+
+
+def _device_passes(batch, rb, counts, steps_t, probs, stream, dev, passes: int, warmup: int = 2, flush=None):
+    """Device time (CUDA events on the batch's stream) of `passes` rollout + probability passes,
+    after `warmup` untimed ones; L2 flushed between passes when `flush` is given."""
+    import torch
+
+    for _ in range(warmup):
+        batch.rollout(counts, steps_t, stream=stream)
+        batch.win_probs(counts, probs, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(passes)]
+    for i in range(passes):
+        if flush is not None:
+            flush.fill_(i)
+        ev[i][0].record(stream)
+        batch.rollout(counts, steps_t, stream=stream)
+        batch.win_probs(counts, probs, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    batch.status(stream)
+    return [a.elapsed_time(b) / 1e3 for a, b in ev], competitor_steps(rb, steps_t.cpu().numpy())
+
+
+def _e2e_calls(rb, counts, probs, odds, stream, dev, calls: int, cfg=None, layout=None):
+    """End to end through the public API: pinned host inputs -> bbe_race_init (H2D inside) ->
+    [launch configuration] -> rollouts -> probabilities -> D2H of probabilities and counts.
+    Median seconds per call, and the bytes copied each way."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    host = {k: pin(getattr(rb, k)) for k in ("race_off", "L", "rollouts", "d0", "mu", "sigma", "rho", "P", "theta")}
+    h_probs = torch.empty(rb.n_total, dtype=torch.float32).pin_memory()
+    h_counts = torch.empty(rb.n_total, dtype=torch.int32).pin_memory()
+    times = []
+    for i in range(2 + calls):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h = bbe.bbe_race_init(rb.n_races, host["race_off"], host["L"], host["rollouts"], host["d0"], host["mu"],
+                              host["sigma"], host["rho"], host["P"], host["theta"], None, rb.seed, rb.dist,
+                              rb.race_id0, stream)
+        if layout is not None:
+            bbe.bbe_batch_set_layout(h, layout)
+        if cfg is not None:
+            bbe.bbe_batch_set_cfg(h, **cfg)
+        bbe.bbe_rollout_batch(h, counts, None, stream)
+        bbe.bbe_win_probs(h, counts, probs, odds, stream)
+        h_probs.copy_(probs, non_blocking=True)
+        h_counts.copy_(counts, non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        bbe.bbe_destroy_batch(h)
+        if i >= 2:
+            times.append(dt)
+    h2d = sum(int(t.numel() * t.element_size()) for t in host.values())
+    return statistics.median(times), h2d, int(h_probs.numel() * 4 + h_counts.numel() * 4)
+
+
+def run_uneven(dev, stream) -> dict:
+    """The uneven batch (10^4 snapshots of 2..24 competitors, remaining distance U(100, 5000),
+    budgets floor(10^U(3, 5))) in one captured graph: at the default launch, then at the launch
+    the autotuner picks (a layout per competitor count, then the block shape and work-item size),
+    device-timed and end to end."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rb = W.uneven_batch(seed=0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    counts = torch.empty(rb.n_total, dtype=torch.int32, device=dev)
+    steps_t = torch.empty(rb.n_races, dtype=torch.int64, device=dev)
+    probs = torch.empty(rb.n_total, dtype=torch.float32, device=dev)
+    odds = torch.empty_like(probs)
+    peak = _peak_ops()
+    out = {"workload": "uneven 10,000 snapshots, n U{2..24}, L 5000, L - d U(100, 5000), rollouts floor(10^U(3,5))",
+           "l2": "flushed between timed passes"}
+    with bbe.Batch(rb, stream=stream) as b:
+        def leg(tag):
+            t, cs = _device_passes(b, rb, counts, steps_t, probs, stream, dev, passes=5, flush=flush)
+            m = statistics.mean(t)
+            out[tag] = {"value": cs / m, "unit": UNIT, "ms_per_pass": 1e3 * m, "win_prob_vectors_per_s": rb.n_races / m,
+                        "alu_frac": ALG_OPS_PER_COMPETITOR_STEP * cs / m / peak, "launches_per_pass":
+                        bbe.bbe_batch_launches(b.handle), "cfg": b.cfg(), "layout": b.layout()[1:25].tolist()}
+        leg("default")
+        t0 = time.perf_counter()
+        cfg = b.autotune(counts, budget_ms=20000.0, stream=stream)
+        out["autotune_wall_s"] = time.perf_counter() - t0
+        leg("autotuned")
+        layout = b.layout()
+    out["gain_autotuned_vs_default"] = out["autotuned"]["value"] / out["default"]["value"]
+    cfg = {k: cfg[k] for k in ("warps_per_block", "blocks_per_sm", "rollouts_per_lane", "max_steps", "slots_per_lane")}
+    e, h2d, d2h = _e2e_calls(rb, counts, probs, odds, stream, dev, calls=3, cfg=cfg, layout=layout)
+    cs = out["autotuned"]["value"] * out["autotuned"]["ms_per_pass"] / 1e3
+    out["e2e"] = {"value": cs / e, "unit": UNIT, "seconds_per_call": e, "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "launch": "the autotuned configuration, set on each new batch"}
+    return out
+
+
+def run_single(dev, stream) -> dict:
+    """The single start-line race (5 competitors, L 2000, 10^3 rollouts): latency per pass on
+    the device (graph replay) and per call end to end."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rb = W.single_race_start()
+    counts = torch.empty(rb.n_total, dtype=torch.int32, device=dev)
+    steps_t = torch.empty(rb.n_races, dtype=torch.int64, device=dev)
+    probs = torch.empty(rb.n_total, dtype=torch.float32, device=dev)
+    odds = torch.empty_like(probs)
+    with bbe.Batch(rb, stream=stream) as b:
+        t, cs = _device_passes(b, rb, counts, steps_t, probs, stream, dev, passes=50, warmup=5)
+    e, h2d, d2h = _e2e_calls(rb, counts, probs, odds, stream, dev, calls=20)
+    return {"workload": "1 race, 5 competitors from the start line, L 2000, 1000 rollouts",
+            "device_ms_per_pass_median": 1e3 * statistics.median(t), "device_ms_per_pass_min": 1e3 * min(t),
+            "competitor_steps_per_pass": cs, "e2e_ms_per_call_median": 1e3 * e,
+            "e2e_h2d_bytes": h2d, "e2e_d2h_bytes": d2h}
+
+
+def run_sweep(dev, stream, repeats: int = 10) -> dict:
+    """Competitor count against throughput (the analogue of the paper's runtime-against-
+    competitors figures, Section 6): 1024 mid-race snapshots of n competitors, L 5000, positions
+    U(0, 0.9 L), 2000 rollouts each, n = 2..32; `repeats` timed passes per n, with the
+    coefficient of variation of the pass times."""
+    import torch
+
+    from paper_2108_02419_gb300 import bbe
+
+    rows = []
+    for n in range(2, 33):
+        rb = W.uniform_batch(seed=600 + n, n_races=1024, n=n, rollouts=2000)
+        counts = torch.empty(rb.n_total, dtype=torch.int32, device=dev)
+        steps_t = torch.empty(rb.n_races, dtype=torch.int64, device=dev)
+        probs = torch.empty(rb.n_total, dtype=torch.float32, device=dev)
+        with bbe.Batch(rb, stream=stream) as b:
+            t, cs = _device_passes(b, rb, counts, steps_t, probs, stream, dev, passes=repeats, warmup=2)
+        m = statistics.mean(t)
+        rows.append({"n": n, "ms_per_pass": 1e3 * m, "cov": statistics.pstdev(t) / m,
+                     "competitor_steps_per_s": cs / m, "rollouts_per_s": rb.n_races * 2000 / m})
+    return {"workload": "1024 snapshots x n competitors, L 5000, d U(0, 0.9 L), 2000 rollouts, n = 2..32",
+            "repeats": repeats, "rows": rows}
+
+
+def run_oracle_timings(threads: int) -> dict:
+    """The CPU oracle as it stands, on one host thread and on all of them: the single race in
+    full, and leading samples of the uniform and uneven batches."""
+    import oracle
+
+    oracle.build()
+    out = {"threads_all": threads}
+    rb = W.single_race_start()
+    for tag, th in (("single_1thread", 1), ("single_all", threads)):
+        t0 = time.perf_counter()
+        _, steps, _ = oracle.batch_counts(rb, threads=th)
+        dt = time.perf_counter() - t0
+        out[tag] = {"value": int((rb.sizes() * steps).sum()) / dt, "unit": UNIT, "s": dt, "sample": "the whole race"}
+    for name, wb in (("uniform", W.uniform_batch(seed=0)), ("uneven", W.uneven_batch(seed=0))):
+        for tag, th, sec in (("1thread", 1, 4.0), ("all", threads, 4.0)):
+            v, desc, _ = oracle_sample(wb, sec, th)
+            out[f"{name}_{tag}"] = {"value": v, "unit": UNIT, "cores": th, "sample": desc}
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU leg
 
 def run_gpu(args, rank, world, dist):
@@ -762,7 +937,7 @@ def run_gpu(args, rank, world, dist):
     achieved = ALG_OPS_PER_COMPETITOR_STEP * units_per_step / roll_s
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                 "frac": achieved / peak_ops, "traffic": kernel_traffic(args.workload, args.races),
-                "kernel": "rollout_kernel", "ops_per_competitor_step": ALG_OPS_PER_COMPETITOR_STEP,
+                "kernel": "win_rollout_kernel", "ops_per_competitor_step": ALG_OPS_PER_COMPETITOR_STEP,
                 "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (maximum SM clock)"}
 
     cpu = None
@@ -776,8 +951,13 @@ def run_gpu(args, rank, world, dist):
     sur = None
     if rank == 0 and args.surrogate != "off" and not args.races:
         sur = run_surrogate(args.surrogate, dev, stream)
-    places = run_places(dev, stream) if rank == 0 and not args.races and args.workload == "uniform" else None
+    legs_on = rank == 0 and not args.races and args.workload == "uniform"
+    places = run_places(dev, stream) if legs_on else None
     population = run_population(dev, stream) if rank == 0 and not args.races else None
+    uneven = run_uneven(dev, stream) if legs_on else None
+    single = run_single(dev, stream) if legs_on else None
+    sweep = run_sweep(dev, stream) if legs_on else None
+    oracle_t = run_oracle_timings(os.cpu_count() or 1) if legs_on and not args.no_cpu_baseline else None
 
     cfg = workload_config(args.workload, rb)
     cfg.update({"l2": "flushed between timed steps (256 MB write)", "launch": batch_cfg,
@@ -790,9 +970,56 @@ def run_gpu(args, rank, world, dist):
             "rollout_kernel_ms": 1e3 * roll_s, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps, "surrogate": sur, "places": places,
-            "population": population}
+            "population": population, "uneven": uneven, "single": single, "sweep": sweep, "cpu_oracle": oracle_t}
+    # the numbers the results table quotes, last on the line (a reader of its tail sees them)
+    line["summary"] = make_summary(line)
+    line["surrogate_summary"] = surrogate_summary(sur)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+
+def make_summary(line: dict) -> dict:
+    r = lambda x, k=4: None if x is None else float(f"{x:.{k}g}")
+    out = {"uniform": {"value": r(line["value"]), "alu_frac": r(line["roofline"]["frac"], 3),
+                       "e2e": r((line.get("e2e") or {}).get("value")),
+                       "oracle_all_cores": r((line.get("cpu_baseline") or {}).get("value"))}}
+    u, si, sw, co = line.get("uneven"), line.get("single"), line.get("sweep"), line.get("cpu_oracle")
+    if u:
+        out["uneven"] = {"default": r(u["default"]["value"]), "autotuned": r(u["autotuned"]["value"]),
+                         "gain": r(u["gain_autotuned_vs_default"], 3), "alu_frac": r(u["autotuned"]["alu_frac"], 3),
+                         "vectors_per_s": r(u["autotuned"]["win_prob_vectors_per_s"]), "e2e": r(u["e2e"]["value"])}
+    if si:
+        out["single"] = {"device_ms": r(si["device_ms_per_pass_median"], 3), "e2e_ms": r(si["e2e_ms_per_call_median"], 3)}
+    if sw:
+        rows = sw["rows"]
+        out["sweep"] = {"cov_max": r(max(x["cov"] for x in rows), 3),
+                        "rate_n": {str(x["n"]): r(x["competitor_steps_per_s"], 3) for x in rows if x["n"] in (2, 5, 10, 20, 24, 32)}}
+    if co:
+        out["oracle"] = {k: r(v["value"], 3) for k, v in co.items() if isinstance(v, dict)}
+    return out
+
+
+def surrogate_summary(sur):
+    if not sur:
+        return None
+    r = lambda x, k=4: None if x is None else float(f"{x:.{k}g}")
+    h = sur.get("heldout", {})
+    err = lambda d: {"max_abs": r(d.get("max_abs"), 3), "kl_mean": r(d.get("kl_mean"), 3)}
+    out = {"train": {"states_per_s": r(sur.get("train_states_per_s")), "tflops": r(sur.get("train_tflops"), 3),
+                     "loss_last": r(sur.get("loss_last"), 3)},
+           "network": dict(err(h.get("network", {})), vectors_per_s=r(sur.get("infer", {}).get("win_prob_vectors_per_s"))),
+           "gated": dict(err(h.get("gated", {})), vectors_per_s=r(sur.get("infer_gated", {}).get("win_prob_vectors_per_s"))),
+           "gated_two_stage": dict(err(h.get("gated_two_stage", {})),
+                                   vectors_per_s=r(sur.get("infer_gated_two_stage", {}).get("win_prob_vectors_per_s"))),
+           "mc_at_query_rollouts": dict(err(h.get("mc_at_query_rollouts", {})),
+                                        vectors_per_s=r(sur.get("mc_at_query_rollouts", {}).get("win_prob_vectors_per_s"))),
+           "gain_gated_two_stage_vs_mc": r(sur.get("gain_gated_two_stage_vs_mc_at_query_rollouts"), 3)}
+    for k in ("reference_1e6", "five_input"):
+        if k in sur:
+            out[k] = sur[k] if not isinstance(sur[k], dict) else {kk: (r(v, 3) if isinstance(v, float) else v)
+                                                                   for kk, v in sur[k].items() if not isinstance(v, dict)}
+    return out
 
 
 def main():

@@ -264,24 +264,40 @@ BBE_API bbe_status bbe_batch_status(bbe_batch *batch, void *cuda_stream);
 BBE_API bbe_status bbe_batch_set_cfg(bbe_batch *batch, const bbe_launch_cfg *cfg);
 BBE_API bbe_status bbe_batch_get_cfg(const bbe_batch *batch, bbe_launch_cfg *cfg);
 
-/* bbe_batch_autotune -- time candidate launch shapes on this batch and keep the fastest.
- * Runs the batch's rollouts once per candidate (bounded by `budget_ms` of GPU time per
- * candidate: candidates are timed on a leading subset of the work list), writing into
- * win_counts (device int32[sum n]) as scratch.  Synchronous.  Errors: BBE_ERR_ARG,
- * BBE_ERR_CUDA. */
+/* bbe_batch_autotune -- pick this batch's launch by timing it (the batching workload asks for
+ * block shapes and rollouts per warp chosen by measurement).  First, for each competitor count
+ * present, a sample of up to 64 of its races is run once per layout (1 to 4 competitors per
+ * lane) and the fastest layout is kept for that count (ties within 1 % keep two); then block
+ * shapes (warps per block x blocks per SM, capped by occupancy: 4 x 16, 8 x 8, 2 x 32) and
+ * work-item sizes (16, 32, 64 rollouts per lane) are each timed (the better of two full passes
+ * with that per-count layout); the starting shape stays unless another is at least 1 % faster.
+ * win_counts (device int32[sum n]) is scratch.
+ * Stops early once `budget_ms` of GPU time is spent (the per-count layouts not reached keep
+ * the default).  Counts do not depend on the launch shape.  Synchronous; allocates (sample
+ * batches).  Errors: BBE_ERR_ARG, BBE_ERR_CUDA (the batch keeps its previous launch). */
 BBE_API bbe_status bbe_batch_autotune(bbe_batch *batch, int32_t *win_counts, double budget_ms, void *cuda_stream);
+
+/* bbe_batch_layout -- competitors per lane used for a race of n competitors, n = 1..32, into
+ * slots_by_n[n] (int32[BBE_MAX_COMPETITORS + 1]; entry 0 is set to 0).
+ * bbe_batch_set_layout -- set that table (entries 0..4; 0 = the default of two; NULL clears
+ * it).  It applies while the launch configuration's slots_per_lane is 0, and rebuilds the
+ * work list.  Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_batch_layout(const bbe_batch *batch, int32_t *slots_by_n);
+BBE_API bbe_status bbe_batch_set_layout(bbe_batch *batch, const int32_t *slots_by_n);
 
 /* bbe_batch_launches -- rollout-kernel launches of one bbe_rollout_batch or bbe_place_counts
  * call on this batch (one persistent launch per group of races with the same competitors per
- * lane, 1 to 3).  Errors: BBE_ERR_ARG. */
+ * lane, 1 to 4, forked from one stream inside the captured graph).  Errors: BBE_ERR_ARG. */
 BBE_API bbe_status bbe_batch_launches(const bbe_batch *batch, int32_t *kernels_per_pass);
 
 /* bbe_batch_info -- sizes of a staged batch (any output pointer may be NULL). */
 BBE_API bbe_status bbe_batch_info(const bbe_batch *batch, int32_t *n_races, int64_t *n_competitors,
                           int64_t *total_rollouts, int32_t *max_competitors);
 
-/* bbe_destroy_batch -- free a handle (NULL is ignored).  Synchronises the device work
- * that uses it first. */
+/* bbe_destroy_batch -- free a handle (NULL is ignored).  Does not block: the batch's device
+ * memory is freed in stream order after the last work that the library enqueued on it (on
+ * every stream it was given); work the caller captured into a graph of its own must not run
+ * after the batch is destroyed. */
 BBE_API void bbe_destroy_batch(bbe_batch *batch);
 
 /* bbe_rollout_noalloc -- the rollout pass of bbe_race_init + bbe_rollout_batch for callers
@@ -291,25 +307,27 @@ BBE_API void bbe_destroy_batch(bbe_batch *batch);
  * allocator that another framework holds).
  *
  * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its work list,
- * queue heads and status word live in one file-scope device array of 1,179,680 bytes
- * (a 32-byte header, 2 x BBE_NOALLOC_MAX_RACES int32 per-race counts and
- * BBE_NOALLOC_MAX_ITEMS 16-byte work items) that every GPU which loads the library holds
- * until the process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call before any
- * stream capture on the device.
+ * queue head and status word live in one file-scope device array of 1,114,144 bytes (a
+ * 32-byte header, BBE_NOALLOC_MAX_RACES int32 per-race item counts and BBE_NOALLOC_MAX_ITEMS
+ * 16-byte work items) that every GPU which loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture on the device.
  *
  * Arguments are those of bbe_race_init plus the outputs of bbe_rollout_batch, with these
- * differences: every array must be device memory (host pointers are rejected), pref and
- * theta are required, n_competitors = race_off[n_races] is the length of the per-competitor
- * arrays, and the launch shape is the library default.  Counts and step totals are
- * identical to bbe_rollout_batch's for the same inputs.
+ * differences: every array must be memory of the current device (or managed memory; host
+ * pointers and other devices' memory are rejected), pref and theta are required,
+ * n_competitors = race_off[n_races] is the length of the per-competitor arrays, and the
+ * launch shape is the library default (two competitors per lane, 4-warp blocks, 32
+ * rollouts per lane and work item).  Counts and step totals are identical to
+ * bbe_rollout_batch's for the same inputs.
  *
  * Synchronous: the call synchronises cuda_stream after validating the batch on the device
  * and again after the rollouts, and returns their status.  All calls share the array: calls
  * that overlap on the GPU (from several host threads or streams) race and must be
  * serialised by the caller; each call resets what it reads before use.
  * Errors: BBE_ERR_RANGE (n_races outside 1..BBE_NOALLOC_MAX_RACES), BBE_ERR_ARG,
- * BBE_ERR_UNSUPPORTED, BBE_ERR_FINISHED (as bbe_race_init), BBE_ERR_STEP_LIMIT, BBE_ERR_CUDA. */
+ * BBE_ERR_UNSUPPORTED, BBE_ERR_FINISHED (as bbe_race_init: the code of the lowest-numbered
+ * invalid race, named in bbe_last_error), BBE_ERR_STEP_LIMIT, BBE_ERR_CUDA. */
 #define BBE_NOALLOC_MAX_RACES 16384
 #define BBE_NOALLOC_MAX_ITEMS 65536
 BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_competitors, const int32_t *race_off,

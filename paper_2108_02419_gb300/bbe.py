@@ -67,6 +67,8 @@ def lib():
             "bbe_batch_set_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_autotune": [vp, vp, C.c_double, vp],
+            "bbe_batch_layout": [vp, vp],
+            "bbe_batch_set_layout": [vp, vp],
             "bbe_batch_info": [vp, vp, vp, vp, vp],
             "bbe_batch_launches": [vp, vp],
             "bbe_rollout_noalloc": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, u64, C.c_int, u32, vp, vp, vp],
@@ -222,6 +224,19 @@ def bbe_batch_autotune(batch: int, win_counts, budget_ms: float = 2000.0, stream
     return bbe_batch_get_cfg(batch)
 
 
+def bbe_batch_layout(batch: int) -> np.ndarray:
+    out = np.zeros(BBE_MAX_COMPETITORS + 1, np.int32)
+    _check(lib().bbe_batch_layout(batch, out.ctypes.data), "bbe_batch_layout")
+    return out
+
+
+def bbe_batch_set_layout(batch: int, slots_by_n=None) -> None:
+    tab = None if slots_by_n is None else np.ascontiguousarray(slots_by_n, np.int32)
+    if tab is not None and tab.shape != (BBE_MAX_COMPETITORS + 1,):
+        raise ValueError("slots_by_n must have BBE_MAX_COMPETITORS + 1 entries")
+    _check(lib().bbe_batch_set_layout(batch, None if tab is None else tab.ctypes.data), "bbe_batch_set_layout")
+
+
 def bbe_batch_info(batch: int) -> dict:
     nr, nc, tr, mx = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
     _check(lib().bbe_batch_info(batch, C.byref(nr), C.byref(nc), C.byref(tr), C.byref(mx)), "bbe_batch_info")
@@ -326,6 +341,12 @@ class Batch:
 
     def cfg(self):
         return bbe_batch_get_cfg(self.handle)
+
+    def layout(self):
+        return bbe_batch_layout(self.handle)
+
+    def set_layout(self, slots_by_n=None):
+        bbe_batch_set_layout(self.handle, slots_by_n)
 
     def autotune(self, counts, budget_ms=2000.0, stream=None):
         return bbe_batch_autotune(self.handle, counts, budget_ms, stream)

@@ -121,10 +121,10 @@ int group_of(int v) { return v - 1; }
 // on GB300 for the uneven mix of 2..24 competitors (3.13e11 competitor-steps/s against
 // 1.72e11 with one per lane up to 5 and four for 21..24, whose four-slot kernel runs short of
 // registers).  `mode` forces a layout.
-int slots_for(int n, int mode)
+int slots_for(int n, int mode, const int8_t *by_n = nullptr)
 {
-    if (mode == 0) return 2;
-    return n >= mode ? mode : std::min(n, 2);  // a forced layout wider than the race falls back
+    const int v = mode != 0 ? mode : (by_n && by_n[n] ? by_n[n] : 2);  // forced, the per-count table, or two
+    return n >= v ? v : std::min(n, 2);  // a layout wider than the race falls back
 }
 
 bbe_status build_items(bbe_batch *b)
@@ -150,7 +150,7 @@ bbe_status build_items(bbe_batch *b)
     };
     auto nseg_of = [&](int r) {  // segments of a warp: floor(32 V / n) slots of n
         const int n = b->h_off[r + 1] - b->h_off[r];
-        return 32 * slots_for(n, b->cfg.slots_per_lane) / n;
+        return 32 * slots_for(n, b->cfg.slots_per_lane, b->slots_by_n) / n;
     };
     // A batch too small to give every warp the GPU can hold (64 per SM) a work item runs fewer
     // rollouts per lane, down to one: the chunking decides which warp runs a rollout, never its
@@ -169,7 +169,7 @@ bbe_status build_items(bbe_batch *b)
     size_t total = 0;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
-        const int v = slots_for(n, b->cfg.slots_per_lane);
+        const int v = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n);
         const int nseg = nseg_of(r);
         const int64_t chunk = chunk_of(r, per_lane, nseg);
         const double st = est_steps(b, r);
@@ -783,6 +783,35 @@ bbe_status bbe_batch_get_cfg(const bbe_batch *b, bbe_launch_cfg *cfg)
     return BBE_OK;
 }
 
+bbe_status bbe_batch_layout(const bbe_batch *b, int32_t *slots_by_n)
+{
+    if (!b || !slots_by_n) {
+        set_error("batch or slots_by_n is NULL");
+        return BBE_ERR_ARG;
+    }
+    slots_by_n[0] = 0;
+    for (int n = 1; n <= BBE_MAX_COMPETITORS; ++n) slots_by_n[n] = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n);
+    return BBE_OK;
+}
+
+bbe_status bbe_batch_set_layout(bbe_batch *b, const int32_t *slots_by_n)
+{
+    if (!b) {
+        set_error("batch is NULL");
+        return BBE_ERR_ARG;
+    }
+    int8_t tab[BBE_MAX_COMPETITORS + 1] = {};
+    for (int n = 1; slots_by_n && n <= BBE_MAX_COMPETITORS; ++n) {
+        if (slots_by_n[n] < 0 || slots_by_n[n] > 4) {
+            set_error("slots_by_n entries must be 0..4");
+            return BBE_ERR_ARG;
+        }
+        tab[n] = int8_t(slots_by_n[n]);
+    }
+    std::memcpy(b->slots_by_n, tab, sizeof(tab));
+    return build_items(b);
+}
+
 bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_ms, void *cuda_stream)
 {
     if (!b || !win_counts || !(budget_ms > 0.0)) {
@@ -791,48 +820,123 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     }
     cudaStream_t s = as_stream(cuda_stream);
     const bbe_launch_cfg start = b->cfg;
-    // candidates: resident warps per SM (occupancy) x block shape x work-item size
-    const int32_t shapes[][2] = {{8, 8}, {4, 16}, {16, 4}, {8, 4}, {16, 2}};
-    const int32_t per_lane[] = {8, 32, 128};
-    cudaEvent_t e0, e1;
+    int8_t start_tab[BBE_MAX_COMPETITORS + 1];
+    std::memcpy(start_tab, b->slots_by_n, sizeof(start_tab));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     BBE_CUDA_TRY(cudaEventCreate(&e0));
     BBE_CUDA_TRY(cudaEventCreate(&e1));
-    float best_ms = INFINITY;
-    bbe_launch_cfg best = start;
     double spent = 0.0;
     bbe_status st = BBE_OK;
-    for (int32_t pl : per_lane) {
-        for (auto &sh : shapes) {
-            bbe_launch_cfg c{sh[0], sh[1], pl, start.max_steps, start.slots_per_lane};
-            if ((st = bbe_batch_set_cfg(b, &c))) goto done;
-            // warm the item list, then time one full pass
-            cudaEventRecord(e0, s);
-            if (enqueue_pass(b, win_counts, nullptr, s, nullptr) != cudaSuccess || bbe::note_use(b, s) != cudaSuccess) {
-                set_error("autotune launch failed");
+    // one pass of batch x into counts, timed on the device (the launch path of a first pass)
+    auto time_pass = [&](bbe_batch *x, int32_t *counts, float &ms) -> bbe_status {
+        bbe_status e = ensure_aux(x);
+        if (e) return e;
+        if (cudaEventRecord(e0, s) != cudaSuccess || enqueue_pass(x, counts, nullptr, s, x->side_stream) != cudaSuccess ||
+            cudaEventRecord(e1, s) != cudaSuccess || bbe::note_use(x, s) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            set_error("autotune: a timed pass failed");
+            return BBE_ERR_CUDA;
+        }
+        spent += ms;
+        return BBE_OK;
+    };
+    float ms = 0.0f;
+    int8_t tab[BBE_MAX_COMPETITORS + 1] = {};
+    bbe_launch_cfg best = start;
+    best.slots_per_lane = 0;
+    float best_ms = INFINITY;
+    {
+        // 1. competitors per lane, for each competitor count of the batch: a sample of up to 64 of
+        // its races (spread over the batch), one pass per layout, the fastest kept (ties within
+        // 1 % stay with the default of two)
+        std::vector<std::vector<int32_t>> by_n(BBE_MAX_COMPETITORS + 1);
+        for (int r = 0; r < b->n_races; ++r) by_n[size_t(b->h_off[r + 1] - b->h_off[r])].push_back(r);
+        for (int n = 1; n <= BBE_MAX_COMPETITORS && st == BBE_OK && spent < budget_ms; ++n) {
+            const std::vector<int32_t> &all = by_n[size_t(n)];
+            if (all.empty()) continue;
+            std::vector<int32_t> pick;
+            const size_t stride = std::max<size_t>(1, all.size() / 64);
+            for (size_t i = 0; i < all.size() && pick.size() < 64; i += stride) pick.push_back(all[i]);
+            std::vector<int32_t> off(1, 0);
+            std::vector<float> L, d0, mu, sg, rho, P, th;
+            std::vector<int64_t> R;
+            for (int32_t r : pick) {
+                L.push_back(b->h_L[size_t(r)]);
+                R.push_back(b->h_R[size_t(r)]);
+                for (int i = b->h_off[size_t(r)]; i < b->h_off[size_t(r) + 1]; ++i) {
+                    d0.push_back(b->h_d0[size_t(i)]);
+                    mu.push_back(b->h_mu[size_t(i)]);
+                    sg.push_back(b->h_sigma[size_t(i)]);
+                    rho.push_back(b->h_rho[size_t(i)]);
+                    P.push_back(b->h_P[size_t(i)]);
+                    th.push_back(b->h_theta[size_t(i)]);
+                }
+                off.push_back(int32_t(d0.size()));
+            }
+            bbe_batch *sub = nullptr;
+            st = bbe::stage_batch(&sub, int32_t(pick.size()), off.data(), L.data(), R.data(), d0.data(), mu.data(),
+                                  sg.data(), rho.data(), P.data(), th.data(), nullptr, b->seed, bbe_dist(b->dist),
+                                  0u, nullptr, s);
+            if (st) break;
+            int32_t *sc = nullptr;
+            if (cudaMallocAsync(&sc, d0.size() * sizeof(int32_t), s) != cudaSuccess) {
+                set_error("autotune: scratch allocation failed");
                 st = BBE_ERR_CUDA;
-                goto done;
+                bbe_destroy_batch(sub);
+                break;
             }
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                set_error("autotune synchronise failed");
-                st = BBE_ERR_CUDA;
-                goto done;
+            float t_v[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+            for (int v = 1; v <= 4 && st == BBE_OK; ++v) {
+                if (v > n && v > 2) continue;  // a forced layout wider than the race falls back to two
+                bbe_launch_cfg c = start;
+                c.slots_per_lane = v;
+                if ((st = bbe_batch_set_cfg(sub, &c))) break;
+                if ((st = time_pass(sub, sc, ms))) break;  // first launch of the layout on this sample
+                if ((st = time_pass(sub, sc, ms))) break;
+                t_v[v] = ms;
             }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            spent += ms;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
-            if (spent > budget_ms) goto done;
+            int vbest = 2;
+            for (int v = 1; v <= 4; ++v)
+                if (t_v[v] < t_v[vbest] * 0.99f) vbest = v;
+            tab[n] = int8_t(vbest);
+            cudaFreeAsync(sc, s);
+            bbe_destroy_batch(sub);
         }
     }
-done:
+    if (st == BBE_OK) {
+        // 2. block shape and work-item size with that layout, each timed on the whole batch (the
+        // better of two passes); the starting shape is the first candidate and stays unless
+        // another is at least 1 % faster
+        std::memcpy(b->slots_by_n, tab, sizeof(tab));
+        st = build_items(b);
+        bbe_launch_cfg first = start;
+        first.slots_per_lane = 0;
+        const bbe_launch_cfg cands[] = {first,
+                                        {4, 16, 32, start.max_steps, 0}, {8, 8, 32, start.max_steps, 0},
+                                        {2, 32, 32, start.max_steps, 0}, {4, 16, 16, start.max_steps, 0},
+                                        {4, 16, 64, start.max_steps, 0}, {8, 8, 16, start.max_steps, 0}};
+        float first_ms = INFINITY;
+        for (size_t i = 0; i < sizeof(cands) / sizeof(cands[0]) && st == BBE_OK; ++i) {
+            if (i > 0 && spent >= budget_ms) break;
+            if ((st = bbe_batch_set_cfg(b, &cands[i]))) break;
+            float t = INFINITY;
+            for (int rep = 0; rep < 2 && st == BBE_OK; ++rep) {
+                if ((st = time_pass(b, win_counts, ms))) break;
+                t = std::min(t, ms);
+            }
+            if (i == 0) first_ms = t;
+            if (t < best_ms && (i == 0 || t < 0.99f * first_ms)) {
+                best_ms = t;
+                best = cands[i];
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) {
+        std::memcpy(b->slots_by_n, start_tab, sizeof(start_tab));
         bbe_batch_set_cfg(b, &start);
+        build_items(b);
         return st;
     }
     return bbe_batch_set_cfg(b, &best);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -25,19 +26,22 @@ constexpr int kMaxRaces = BBE_NOALLOC_MAX_RACES;
 constexpr int kMaxItems = BBE_NOALLOC_MAX_ITEMS;
 constexpr int kPlanThreads = 1024;
 constexpr int kMaxDevices = 64;
+constexpr int kSlots = 2;              // competitors per lane: the library's automatic layout
+constexpr int kRolloutsPerLane = 32;   // the library's default work-item size
 
 struct NoallocHeader {
-    int32_t queue[2];    // work-queue heads of the two rollout kernels
-    int32_t status;      // device status bits written by the rollout kernels
-    int32_t plan_error;  // bbe_status of the first invalid input found, 0 if none
-    int32_t n_items[2];  // items per slots-per-lane value (1, 2)
-    int32_t pad[2];
+    int32_t queue;       // work-queue head of the rollout kernel
+    int32_t status;      // device status bits written by the rollout kernel
+    int32_t plan_error;  // bbe_status of the lowest-numbered invalid race, 0 if none
+    int32_t plan_race;   // that race
+    int32_t n_items;     // work items in the list
+    int32_t pad[3];
 };
 
 struct NoallocScratch {
     NoallocHeader h;
-    int32_t race_items[2][kMaxRaces];  // per-race item counts, then offsets
-    bbe::WorkItem items[kMaxItems];    // one-slot items first, then two-slot items
+    int32_t race_items[kMaxRaces];   // per-race item counts, then offsets
+    bbe::WorkItem items[kMaxItems];  // the work list, race by race
 };
 
 // The only memory this entry point uses besides the caller's arrays.  Host code must not
@@ -54,39 +58,27 @@ struct PlanArgs {
     const float *d0, *mu, *sigma, *rho, *P, *theta, *prev0;
 };
 
-__device__ int slots_for_n(int n)
-{
-    if (n < 2) return 1;
-    const int used1 = n * (32 / n);
-    const int used2 = n * (32 / ((n + 1) / 2));
-    return 2 * used1 < used2 ? 2 : 1;
-}
-
+// Rollouts per work item: the library's (kRolloutsPerLane per segment of the warp, the warp
+// holding floor(64 / n) segments), raised so that a race has at most `cap` items.
 __device__ int64_t chunk_for(int n, int64_t R, int cap)
 {
-    const int v = slots_for_n(n);
-    const int nseg = 32 / ((n + v - 1) / v);
-    const int64_t base = 32 * int64_t(nseg);
-    const int64_t need = (R + cap - 1) / cap;  // keeps a race to at most `cap` items
+    const int64_t base = int64_t(kRolloutsPerLane) * (32 * kSlots / n);
+    const int64_t need = (R + cap - 1) / cap;
     return base > need ? base : need;
-}
-
-__device__ void note_error(int *err, int code)
-{
-    atomicCAS(err, 0, code);
 }
 
 // One block validates the batch, counts the work items of every race and writes the work
 // list into the scratch array.  Every read of the caller's per-competitor arrays is
-// bounded by n_competitors after the offsets have been checked.
+// bounded by n_competitors after the offsets have been checked.  An invalid batch writes no
+// items and reports its lowest-numbered invalid race (as bbe_race_init does).
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs a)
 {
     NoallocScratch &sc = g_noalloc_scratch;
-    __shared__ int s_err;
-    __shared__ int s_part[2][kPlanThreads];
-    __shared__ int s_total[2];
+    __shared__ int s_err;  // least (race * 8 + |status|) over invalid races
+    __shared__ int s_part[kPlanThreads];
+    __shared__ int s_total;
     const int tid = threadIdx.x;
-    if (tid == 0) s_err = 0;
+    if (tid == 0) s_err = INT_MAX;
     __syncthreads();
     const int cap = kMaxItems / a.n_races;
     for (int r = tid; r < a.n_races; r += kPlanThreads) {
@@ -112,55 +104,46 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs a)
             else if (a.prev0 && (!isfinite(a.prev0[i]) || !(a.prev0[i] > 0.0f)))
                 err = BBE_ERR_ARG;
         }
-        int items = 0, v = 1;
-        if (err) {
-            note_error(&s_err, err);
-        } else {
-            v = slots_for_n(n);
-            const int64_t chunk = chunk_for(n, R, cap);
-            items = int((R + chunk - 1) / chunk);
-        }
-        sc.race_items[v - 1][r] = items;
-        sc.race_items[2 - v][r] = 0;
+        int items = 0;
+        if (err) atomicMin(&s_err, r * 8 - err);
+        else items = int((R + chunk_for(n, R, cap) - 1) / chunk_for(n, R, cap));
+        sc.race_items[r] = items;
     }
     __syncthreads();
     // exclusive scan of the per-race item counts (contiguous chunks of races per thread)
     const int per = (a.n_races + kPlanThreads - 1) / kPlanThreads;
     const int r0 = tid * per;
     const int r1 = min(a.n_races, r0 + per);
-    for (int v = 0; v < 2; ++v) {
-        int sum = 0;
-        for (int r = r0; r < r1; ++r) sum += sc.race_items[v][r];
-        s_part[v][tid] = sum;
-    }
+    int sum = 0;
+    for (int r = r0; r < r1; ++r) sum += sc.race_items[r];
+    s_part[tid] = sum;
     __syncthreads();
-    if (tid < 2) {
+    if (tid == 0) {
         int run = 0;
         for (int i = 0; i < kPlanThreads; ++i) {
-            const int x = s_part[tid][i];
-            s_part[tid][i] = run;
+            const int x = s_part[i];
+            s_part[i] = run;
             run += x;
         }
-        s_total[tid] = run;
+        s_total = run;
+        // at most cap items per race keeps the list within the array; checked all the same
+        if (run > kMaxItems && s_err == INT_MAX) s_err = 8 * a.n_races - BBE_ERR_RANGE;
     }
     __syncthreads();
-    for (int v = 0; v < 2; ++v) {
-        int run = s_part[v][tid];
-        for (int r = r0; r < r1; ++r) {
-            const int x = sc.race_items[v][r];
-            sc.race_items[v][r] = run;
-            run += x;
-        }
+    int run = s_part[tid];
+    for (int r = r0; r < r1; ++r) {
+        const int x = sc.race_items[r];
+        sc.race_items[r] = run;
+        run += x;
     }
     __syncthreads();
-    const bool ok = s_err == 0;
+    const bool ok = s_err == INT_MAX;
     if (ok) {
         for (int r = tid; r < a.n_races; r += kPlanThreads) {
             const int n = a.race_off[r + 1] - a.race_off[r];
-            const int v = slots_for_n(n);
             const int64_t R = a.R[r];
             const int64_t chunk = chunk_for(n, R, cap);
-            int pos = (v == 2 ? s_total[0] : 0) + sc.race_items[v - 1][r];
+            int pos = sc.race_items[r];
             for (int64_t k = 0; k < R; k += chunk, ++pos) {
                 const int64_t cnt = R - k < chunk ? R - k : chunk;
                 sc.items[pos] = bbe::WorkItem{r, int32_t(k), int32_t(cnt), 0};
@@ -168,12 +151,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs a)
         }
     }
     if (tid == 0) {
-        sc.h.queue[0] = 0;
-        sc.h.queue[1] = 0;
+        sc.h.queue = 0;
         sc.h.status = 0;
-        sc.h.plan_error = s_err;
-        sc.h.n_items[0] = ok ? s_total[0] : 0;
-        sc.h.n_items[1] = ok ? s_total[1] : 0;
+        sc.h.plan_error = ok ? 0 : -(s_err & 7);
+        sc.h.plan_race = ok ? -1 : s_err >> 3;
+        sc.h.n_items = ok ? s_total : 0;
     }
 }
 
@@ -202,14 +184,15 @@ bbe_status scratch_for_current_device(NoallocScratch **out)
     return BBE_OK;
 }
 
-bool on_device(const void *p)
+// p is device memory of device `dev` (or managed memory, which any device may read)
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -243,16 +226,18 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
         bbe::set_error("bbe_rollout_noalloc: unknown distribution");
         return BBE_ERR_ARG;
     }
+    int dev = 0, sms = 0;
+    NA_TRY(cudaGetDevice(&dev));
     const void *required[] = {race_off, track_len, rollouts, pos, mu, sigma, resp, pref, theta, win_counts};
     for (const void *p : required) {
-        if (!p || !on_device(p)) {
-            bbe::set_error("bbe_rollout_noalloc: every array must be non-null device memory "
+        if (!p || !on_device(p, dev)) {
+            bbe::set_error("bbe_rollout_noalloc: every array must be non-null memory of the current device "
                            "(pref and theta included; only prev_step and steps_total may be NULL)");
             return BBE_ERR_ARG;
         }
     }
-    if ((prev_step && !on_device(prev_step)) || (steps_total && !on_device(steps_total))) {
-        bbe::set_error("bbe_rollout_noalloc: prev_step / steps_total must be device memory");
+    if ((prev_step && !on_device(prev_step, dev)) || (steps_total && !on_device(steps_total, dev))) {
+        bbe::set_error("bbe_rollout_noalloc: prev_step / steps_total must be memory of the current device");
         return BBE_ERR_ARG;
     }
     NoallocScratch *sc = nullptr;
@@ -267,34 +252,32 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
     NA_TRY(cudaMemcpyAsync(&h, &sc->h, sizeof(h), cudaMemcpyDeviceToHost, s));
     NA_TRY(cudaStreamSynchronize(s));
     if (h.plan_error != 0) {
-        bbe::set_error("bbe_rollout_noalloc: invalid race batch (offsets, sizes 1..32, L > 0, R in 1..2^31-1, "
-                       "0 <= d < L, mu > 0, sigma >= 0, rho in [0,1], P in (0,1], theta >= 0, prev > 0)");
+        bbe::set_error("bbe_rollout_noalloc: race " + std::to_string(h.plan_race) +
+                       " is invalid (offsets, sizes 1..32, L > 0, R in 1..2^31-1, 0 <= d < L, mu > 0, "
+                       "sigma >= 0, rho in [0,1], P in (0,1], theta >= 0, prev > 0)");
         return static_cast<bbe_status>(h.plan_error);
     }
 
     NA_TRY(cudaMemsetAsync(win_counts, 0, size_t(n_competitors) * sizeof(int32_t), s));
     if (steps_total) NA_TRY(cudaMemsetAsync(steps_total, 0, size_t(n_races) * sizeof(int64_t), s));
-    int dev = 0, sms = 0;
-    NA_TRY(cudaGetDevice(&dev));
     NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int block = 128;
     bbe::DevBatch b{race_off, track_len, rollouts, nullptr, pos, mu, sigma, resp, pref, theta, prev_step,
                     nullptr, n_races, n_competitors, race_id0, uint32_t(seed), uint32_t(seed >> 32), int32_t(dist)};
-    for (int v = 2; v >= 1; --v) {
-        if (h.n_items[v - 1] == 0) continue;
+    if (h.n_items > 0) {
         bbe::RolloutLaunch l{};
         l.b = b;
-        l.items = sc->items + (v == 2 ? h.n_items[0] : 0);
-        l.n_items = h.n_items[v - 1];
-        l.queue = &sc->h.queue[v - 1];
+        l.items = sc->items;
+        l.n_items = h.n_items;
+        l.queue = &sc->h.queue;
         l.counts = win_counts;
         l.steps = reinterpret_cast<unsigned long long *>(steps_total);
         l.status = &sc->h.status;
         l.max_steps = BBE_MAX_STEPS_DEFAULT;
         l.block = block;
-        l.grid = sms * std::max(1, std::min(16, bbe::rollout_resident_blocks(int(dist), v, block)));
+        l.grid = sms * std::max(1, std::min(16, bbe::rollout_resident_blocks(int(dist), kSlots, block)));
         bbe::fill_round_keys(l);
-        NA_TRY(bbe::launch_rollout(l, v, s));
+        NA_TRY(bbe::launch_rollout(l, kSlots, s));
     }
     int32_t status = 0;
     NA_TRY(cudaMemcpyAsync(&status, &sc->h.status, sizeof(status), cudaMemcpyDeviceToHost, s));

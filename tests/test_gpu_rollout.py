@@ -168,15 +168,39 @@ def test_step_limit_status(bbe):
 
 
 def test_autotune_keeps_counts(bbe):
+    # the tuner picks a layout per competitor count and a launch shape; counts stay those of
+    # the oracle whatever it picks
     rb = W.uneven_batch(seed=12, n_races=200, r_lo_exp=2.0, r_hi_exp=3.0)
-    ref = run_gpu(bbe, rb)
     with bbe.Batch(rb) as b:
         scratch = torch.empty(rb.n_total, dtype=torch.int32, device="cuda")
-        cfg = b.autotune(scratch, budget_ms=500.0)
-        assert 1 <= cfg["warps_per_block"] <= 16 and cfg["rollouts_per_lane"] >= 1
+        cfg = b.autotune(scratch, budget_ms=5000.0)
+        assert 1 <= cfg["warps_per_block"] <= 16 and cfg["rollouts_per_lane"] >= 1 and cfg["slots_per_lane"] == 0
+        tab = b.layout()
+        assert tab[0] == 0 and np.all((tab[1:] >= 1) & (tab[1:] <= 4))
         counts, steps = b.rollout()
+        b.status()
         torch.cuda.synchronize()
-        assert np.array_equal(counts.cpu().numpy(), ref[0])
+        assert_matches_oracle(rb, counts.cpu().numpy(), steps.cpu().numpy())
+
+
+def test_mixed_layout_table(bbe):
+    # every layout in one pass (one persistent launch per layout, forked in one graph), on a
+    # repeated pass too (the graph replay)
+    rb = W.uneven_batch(seed=14, n_races=120, n_lo=1, n_hi=32, rollouts=600)
+    tab = np.zeros(33, np.int32)
+    for n in range(1, 33):
+        tab[n] = (1, 3, 4, 2)[n % 4]
+    with bbe.Batch(rb) as b:
+        b.set_layout(tab)
+        ns = np.arange(1, 33)
+        assert np.array_equal(b.layout()[1:], np.where(tab[1:] > ns, np.minimum(ns, 2), tab[1:]))
+        assert bbe.bbe_batch_launches(b.handle) == 4
+        for _ in range(2):
+            counts, steps = b.rollout()
+            b.status()
+        torch.cuda.synchronize()
+        got_c, got_s = counts.cpu().numpy(), steps.cpu().numpy()
+    assert_matches_oracle(rb, got_c, got_s)
 
 
 @pytest.mark.parametrize("mutate,code", [

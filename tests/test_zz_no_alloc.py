@@ -56,7 +56,7 @@ def _noalloc(bbe, rb, counts=None, steps=None):
 
 
 def test_two_calls_match_allocating_path(bbe):
-    first = W.uneven_batch(seed=31, n_races=300, r_lo_exp=1.5, r_hi_exp=3.5)  # sizes 2..24, both lane packings
+    first = W.uneven_batch(seed=31, n_races=300, r_lo_exp=1.5, r_hi_exp=3.5)  # sizes 2..24, ragged budgets
     second = W.uniform_batch(seed=32, n_races=40, n=20, rollouts=2000)        # smaller: stale items must not leak
     for rb in (first, second):
         want_c, want_s = _allocating(bbe, rb)
@@ -100,3 +100,29 @@ def test_rejects_host_memory_and_bad_states(bbe):
     want = _allocating(bbe, rb)
     got = _noalloc(bbe, rb)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_scratch_edges_match_allocating_path(bbe):
+    # the most races the array takes (16,384 races of 2: at most 4 items each), one race of 32
+    # competitors with a large budget (its items grow to keep the list short), and a mix with
+    # lone competitors
+    many = W.uniform_batch(seed=36, n_races=16384, n=2, rollouts=1000)
+    big = W.uniform_batch(seed=37, n_races=1, n=32, rollouts=100000)
+    mix = W.concat([W.uneven_batch(seed=38, n_races=30, n_lo=1, n_hi=1, rollouts=500),
+                    W.uneven_batch(seed=39, n_races=30, n_lo=2, n_hi=32, rollouts=3000)])
+    for rb in (many, big, mix):
+        want_c, want_s = _allocating(bbe, rb)
+        got_c, got_s = _noalloc(bbe, rb)
+        assert np.array_equal(got_c, want_c)
+        assert np.array_equal(got_s, want_s)
+
+
+def test_reports_the_lowest_invalid_race(bbe):
+    rb = W.uneven_batch(seed=40, n_races=50, rollouts=10)
+    rb.sigma[rb.race_off[40]] = -1.0       # race 40: BBE_ERR_ARG
+    rb.d0[rb.race_off[7] + 1] = rb.L[7]    # race 7: BBE_ERR_FINISHED, the lowest
+    for _ in range(3):
+        with pytest.raises(bbe.BbeError) as ei:
+            _noalloc(bbe, rb)
+        assert ei.value.status == -3
+        assert "race 7 " in bbe.bbe_last_error()
