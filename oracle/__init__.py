@@ -29,6 +29,7 @@ _lib = None
 DIST_NORMAL, DIST_UNIFORM, DIST_TWO_POINT = 0, 1, 2
 MAX_STEPS_DEFAULT = 1 << 20
 STEP_LIMIT = -5
+LAW_POSITION, LAW_TIME = 0, 1  # responsiveness laws (bbe_oracle.c: responsiveness, responsiveness_time)
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wextra"]
 
@@ -58,7 +59,7 @@ def build(force: bool = False) -> str:
 class _Race(C.Structure):
     _fields_ = [("n", C.c_int), ("L", C.c_float), ("d0", C.c_void_p), ("mu", C.c_void_p), ("sigma", C.c_void_p),
                 ("rho", C.c_void_p), ("P", C.c_void_p), ("theta", C.c_void_p), ("prev0", C.c_void_p),
-                ("dist", C.c_int)]
+                ("dist", C.c_int), ("law", C.c_int), ("t0", C.c_float), ("T", C.c_float)]
 
 
 def lib():
@@ -140,7 +141,8 @@ class _RaceArgs:
         self.arrays = [f(race[k]) for k in ("d0", "mu", "sigma", "rho", "P", "theta", "prev0")]
         d0, mu, sigma, rho, P, theta, prev0 = self.arrays
         self.s = _Race(int(race["n"]), float(race["L"]), _ptr(d0), _ptr(mu), _ptr(sigma), _ptr(rho), _ptr(P),
-                       _ptr(theta), _ptr(prev0), int(race.get("dist", DIST_NORMAL)))
+                       _ptr(theta), _ptr(prev0), int(race.get("dist", DIST_NORMAL)), int(race.get("law", LAW_POSITION)),
+                       float(race.get("t0", 0.0)), float(race.get("T", 1.0)))
 
 
 def rollout(race: dict, seed: int, r: int, k: int, max_steps: int = MAX_STEPS_DEFAULT, traj_cap: int = 0):

@@ -22,7 +22,9 @@
  *   kappa = 0.2f, S_floor = 1e-3f, theta default = 1.0f, max_steps default = 2^20.
  *   invL    = 1 / L
  *   kr_c    = kappa * ((2 * rho_c) - 1)
- *   R_c     = fmaf(kr_c, fmaf(d_c, invL, -0.5f), 1.0f)              responsiveness
+ *   R_c     = fmaf(kr_c, fmaf(d_c, invL, -0.5f), 1.0f)              responsiveness (position law)
+ *   or, with the time law and invT = 1 / T,
+ *   u       = min(1, (t0 + (float)t) * invT),  R_c = fmaf(kr_c, u - 0.5f, 1.0f)
  *   i+      = argmin_{i != c, d_i > d_c} d_i   (equal d_i: lowest i)  nearest in front
  *   blocked = i+ exists and not (d_{i+} - d_c > theta_c)             Eq. 1 "otherwise"
  *   S_c     = blocked ? R_c * min(prev_c, prev_{i+})                  Eq. 1, delta_min
@@ -181,11 +183,22 @@ float bbe_oracle_z(int dist, uint64_t seed, uint32_t r, uint32_t k, uint32_t t, 
 /* -------------------------------------------------------------- race simulation */
 
 /* Responsiveness R_c(t, d) of Eq. 1.  Section 3 gives only its purpose (fast start and
- * fade, or slow start and fast finish); this library's reading is a linear law in the
- * fraction of the track covered: R = 1 + kappa (2 rho - 1) (d / L - 1/2). */
+ * fade, or slow start and fast finish) and writes it as a function of time and distance.
+ * Two readings, each linear and centred on the middle of the race:
+ *   position law: R = 1 + kappa (2 rho - 1) (d / L - 1/2), the fraction of the track covered;
+ *   time law:     R = 1 + kappa (2 rho - 1) (u - 1/2), u = min(1, (t0 + t) / T), the fraction
+ *                 of the race's expected duration T elapsed (t0 steps before the state, t in
+ *                 the dry-run), held at its end value once T has passed. */
 static float responsiveness(float kr, float d, float invL)
 {
     return fmaf(kr, fmaf(d, invL, -0.5f), 1.0f);
+}
+
+static float responsiveness_time(float kr, float t0, uint32_t t, float invT)
+{
+    float u = (t0 + (float)t) * invT;
+    if (u > 1.0f) u = 1.0f;
+    return fmaf(kr, u - 0.5f, 1.0f);
 }
 
 /* One step of Section 3 for every competitor, reading only the time-t state
@@ -195,8 +208,10 @@ static void race_step(const bbe_oracle_race *race, const float *kr, float invL,
                       uint32_t k, uint32_t t, float *S_out)
 {
     int n = race->n;
+    float invT = race->law == BBE_ORACLE_LAW_TIME ? 1.0f / race->T : 0.0f;
     for (int c = 0; c < n; ++c) {
-        float R_c = responsiveness(kr[c], d[c], invL);
+        float R_c = race->law == BBE_ORACLE_LAW_TIME ? responsiveness_time(kr[c], race->t0, t, invT)
+                                                     : responsiveness(kr[c], d[c], invL);
         /* i+ : nearest competitor strictly in front of c; equal distance -> lowest i */
         int i_plus = -1;
         for (int i = 0; i < n; ++i) {

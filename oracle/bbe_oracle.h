@@ -14,6 +14,8 @@
 #define BBE_ORACLE_KAPPA 0x1.99999ap-3f   /* 0.2f */
 #define BBE_ORACLE_S_FLOOR 0x1.0624dep-10f /* 1e-3f */
 #define BBE_ORACLE_STEP_LIMIT (-5)
+#define BBE_ORACLE_LAW_POSITION 0
+#define BBE_ORACLE_LAW_TIME 1
 
 /* One race of Section 3: n competitors on a track of length L; per competitor the
  * position d0, the step distribution's mean mu and spread sigma, responsiveness rho,
@@ -29,6 +31,9 @@ typedef struct {
     const float *theta;
     const float *prev0; /* nullable: mu * P */
     int dist;
+    int law;            /* responsiveness law: BBE_ORACLE_LAW_POSITION or BBE_ORACLE_LAW_TIME */
+    float t0;           /* time law: steps elapsed before the state (a mid-race snapshot) */
+    float T;            /* time law: the race's expected duration in steps, > 0 */
 } bbe_oracle_race;
 
 void bbe_oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

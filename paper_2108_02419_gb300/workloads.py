@@ -43,6 +43,10 @@ class RaceBatch:
     race_id0: int = 0  # id of race 0 in the random stream
     name: str = "custom"
     meta: dict = field(default_factory=dict)
+    # the time law of responsiveness (both per race, float32), or None for the position law:
+    # steps elapsed before the state, and the race's expected duration in steps
+    elapsed: np.ndarray | None = None
+    horizon: np.ndarray | None = None
 
     @property
     def n_races(self) -> int:
@@ -72,6 +76,8 @@ class RaceBatch:
             R=int(self.rollouts[r]),
             race_id=self.race_id0 + r,
         )
+        if self.horizon is not None:
+            out.update(law=1, t0=0.0 if self.elapsed is None else float(self.elapsed[r]), T=float(self.horizon[r]))
         return out
 
     def slice(self, a: int, b: int) -> "RaceBatch":
@@ -82,9 +88,11 @@ class RaceBatch:
         def take(x):
             return None if x is None else np.ascontiguousarray(x[lo:hi])
 
+        per_race = lambda x: None if x is None else x[a:b].copy()
         return RaceBatch(off, self.L[a:b].copy(), self.rollouts[a:b].copy(), take(self.d0), take(self.mu),
                          take(self.sigma), take(self.rho), take(self.P), take(self.theta), take(self.prev0),
-                         self.seed, self.dist, self.race_id0 + a, f"{self.name}[{a}:{b}]", dict(self.meta))
+                         self.seed, self.dist, self.race_id0 + a, f"{self.name}[{a}:{b}]", dict(self.meta),
+                         per_race(self.elapsed), per_race(self.horizon))
 
 
 def _params(rng: np.random.Generator, n: int):
@@ -152,6 +160,16 @@ def from_arrays(sizes, L, rollouts, d0, mu, sigma, rho, P=None, theta=None, prev
     L = np.broadcast_to(np.asarray(L, np.float32), sizes.shape).copy()
     rollouts = np.broadcast_to(np.asarray(rollouts, np.int64), sizes.shape).copy()
     return _assemble(sizes, L, rollouts, f(d0), f(mu), f(sigma), f(rho), seed, name, dist, f(P), f(theta), f(prev0))
+
+
+def with_time_law(rb: RaceBatch, elapsed, horizon) -> RaceBatch:
+    """The same batch under the time law of responsiveness: per race the steps elapsed before
+    the state and the expected duration in steps (scalars broadcast)."""
+    out = rb.slice(0, rb.n_races)
+    out.race_id0 = rb.race_id0
+    out.elapsed = np.broadcast_to(np.asarray(elapsed, np.float32), (rb.n_races,)).copy()
+    out.horizon = np.broadcast_to(np.asarray(horizon, np.float32), (rb.n_races,)).copy()
+    return out
 
 
 def concat(batches) -> RaceBatch:

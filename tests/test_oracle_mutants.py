@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes: each mutant below is a copy of
 oracle/bbe_oracle.c with one deliberate error (in the oracle, on the CPU); the pin suites
 (tests/test_oracle_rng.py, tests/test_oracle_race.py, tests/test_oracle_places.py,
-tests/test_oracle_trajectory.py, tests/test_oracle_preference.py, tests/test_oracle_orders.py) must fail
+tests/test_oracle_trajectory.py, tests/test_oracle_preference.py, tests/test_oracle_orders.py,
+tests/test_oracle_time_law.py) must fail
 against every mutant."""
 import os
 import subprocess
@@ -46,6 +47,10 @@ MUTANTS = {
         "            if (dn[c] >= race->L) all_in = 1;"),
     "preference_unclamped": ("if (m > 1.0f) m = 1.0f;", ";"),
     "preference_additive": ("p = p * (1.0f - weights[i] * m);", "p = p - weights[i] * m;"),
+    "time_law_sign": ("return fmaf(kr, u - 0.5f, 1.0f);", "return fmaf(kr, 0.5f - u, 1.0f);"),
+    "time_law_uncapped": ("    if (u > 1.0f) u = 1.0f;\n    return fmaf(kr, u - 0.5f", "    return fmaf(kr, u - 0.5f"),
+    "time_law_ignores_elapsed": ("float u = (t0 + (float)t) * invT;", "float u = (float)t * invT;"),
+    "time_law_uses_position": ("? responsiveness_time(kr[c], race->t0, t, invT)", "? responsiveness(kr[c], d[c], invL)"),
     "order_tuple_reversed": ("for (int j = 0; j < kk; ++j) code = code * n + order[j];",
                              "for (int j = kk - 1; j >= 0; --j) code = code * n + order[j];"),
 }
@@ -63,6 +68,7 @@ def test_pins_catch_mutant(tmp_path, name):
     # the quick suites first: -x stops at the first failing pin
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_preference.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_time_law.py"),
                           os.path.join(ROOT, "tests", "test_oracle_trajectory.py"),
                           os.path.join(ROOT, "tests", "test_oracle_orders.py"),
                           os.path.join(ROOT, "tests", "test_oracle_race.py"),
