@@ -69,6 +69,20 @@ typedef enum {
     BBE_DIST_TWO_POINT = 2 /* z = -1 or +1 with probability 1/2 each */
 } bbe_dist;
 
+/* Law of the responsiveness R_c(t, d) of Eq. 1.  Section 3 gives only its purpose (a
+ * competitor that starts fast and fades, or starts slowly and finishes strongly), written as
+ * a function of time and distance; each law below is one reading of it, linear and centred on
+ * the middle of the race:
+ *   POSITION: R_c = 1 + 0.2 (2 rho_c - 1) (d_c / L - 1/2)  (the fraction of the track covered);
+ *   TIME:     R_c = 1 + 0.2 (2 rho_c - 1) (u - 1/2), u = min(1, (t0 + t) / T), the fraction of
+ *             the race's expected duration T elapsed, t0 the steps run before the state (a
+ *             mid-race snapshot) and t the dry-run's step; in binary32,
+ *             u = min(1, (t0 + (float)t) * (1 / T)), R = fma(0.2 (2 rho - 1), u - 0.5, 1). */
+typedef enum {
+    BBE_LAW_POSITION = 0,
+    BBE_LAW_TIME = 1
+} bbe_law;
+
 #define BBE_MAX_COMPETITORS 32
 #define BBE_MAX_ORDER_PLACES 3 /* ordered places tallied by bbe_order_counts (n^3 <= 32768 per race) */
 #define BBE_THETA_DEFAULT 1.0f
@@ -253,6 +267,20 @@ BBE_API bbe_status bbe_bettor_predictions(const bbe_batch *src, int32_t race, co
                                           const float *step_sizes, const int32_t *n_steps, int32_t cap, int32_t every,
                                           int32_t n_snapshots, int32_t linex_window, float ud_gap, uint32_t zi_stream,
                                           int32_t *predictions, void *cuda_stream);
+
+/* bbe_batch_set_law -- choose the responsiveness law of a staged batch (bbe_law above; a
+ * batch starts with BBE_LAW_POSITION).
+ *   law         BBE_LAW_POSITION (elapsed and horizon are ignored) or BBE_LAW_TIME.
+ *   elapsed     float[n_races], t0 >= 0 per race (finite), or NULL (all 0); host or device.
+ *   horizon     float[n_races], T > 0 per race (finite); required for BBE_LAW_TIME; host or
+ *               device.  The library keeps its own copy.
+ *   cuda_stream stream for the copies; the call synchronises it before returning.
+ * bbe_rollout_batch, bbe_race_trajectory and bbe_snapshot_batch (whose snapshots carry
+ * elapsed = t0 + the snapshot's step and the same horizon) follow the law.  Place and order
+ * tallies and the surrogate take position-law batches only (BBE_ERR_UNSUPPORTED otherwise).  Errors: BBE_ERR_ARG (bad law, missing or invalid values),
+ * BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_batch_set_law(bbe_batch *batch, bbe_law law, const float *elapsed, const float *horizon,
+                                     void *cuda_stream);
 
 /* bbe_batch_status -- synchronise cuda_stream and return the batch's device status from
  * the last bbe_rollout_batch or bbe_place_counts: BBE_OK, BBE_ERR_STEP_LIMIT, or

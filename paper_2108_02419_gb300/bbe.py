@@ -68,6 +68,7 @@ def lib():
             "bbe_batch_get_cfg": [vp, C.POINTER(bbe_launch_cfg)],
             "bbe_batch_autotune": [vp, vp, C.c_double, vp],
             "bbe_batch_layout": [vp, vp],
+            "bbe_batch_set_law": [vp, C.c_int, vp, vp, vp],
             "bbe_batch_set_layout": [vp, vp],
             "bbe_batch_info": [vp, vp, vp, vp, vp],
             "bbe_batch_launches": [vp, vp],
@@ -224,6 +225,14 @@ def bbe_batch_autotune(batch: int, win_counts, budget_ms: float = 2000.0, stream
     return bbe_batch_get_cfg(batch)
 
 
+LAW_POSITION, LAW_TIME = 0, 1
+
+
+def bbe_batch_set_law(batch: int, law: int, elapsed=None, horizon=None, stream=None) -> None:
+    _check(lib().bbe_batch_set_law(batch, int(law), _ptr(elapsed, np.float32), _ptr(horizon, np.float32),
+                                   _stream(stream)), "bbe_batch_set_law")
+
+
 def bbe_batch_layout(batch: int) -> np.ndarray:
     out = np.zeros(BBE_MAX_COMPETITORS + 1, np.int32)
     _check(lib().bbe_batch_layout(batch, out.ctypes.data), "bbe_batch_layout")
@@ -280,6 +289,14 @@ class Batch:
         self.rb = rb
         self.handle = bbe_race_init(rb.n_races, rb.race_off, rb.L, rb.rollouts, rb.d0, rb.mu, rb.sigma, rb.rho, rb.P,
                                     rb.theta, rb.prev0, rb.seed, rb.dist, rb.race_id0, stream)
+        if getattr(rb, "horizon", None) is not None:
+            el = getattr(rb, "elapsed", None)
+            try:
+                bbe_batch_set_law(self.handle, LAW_TIME, None if el is None else np.ascontiguousarray(el, np.float32),
+                                  np.ascontiguousarray(rb.horizon, np.float32), stream)
+            except BaseException:
+                bbe_destroy_batch(self.handle)
+                raise
 
     def new_outputs(self, device="cuda"):
         import torch

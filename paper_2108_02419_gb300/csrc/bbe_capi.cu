@@ -599,6 +599,10 @@ namespace {
 bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, int32_t *orders,
                           int64_t *steps_total, cudaStream_t s)
 {
+    if (b->dev.law != BBE_LAW_POSITION) {
+        set_error("place and order tallies take position-law batches only");
+        return BBE_ERR_UNSUPPORTED;
+    }
     if (place_counts)
         BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
     if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));
@@ -732,6 +736,53 @@ bbe_status bbe_place_probs(const bbe_batch *b, int32_t places, const int32_t *pl
     }
     BBE_CUDA_TRY(bbe::launch_place_probs(b->dev, places, place_counts, top, probs, as_stream(cuda_stream)));
     BBE_CUDA_TRY(bbe::note_use(b, as_stream(cuda_stream)));
+    return BBE_OK;
+}
+
+bbe_status bbe_batch_set_law(bbe_batch *b, bbe_law law, const float *elapsed, const float *horizon,
+                             void *cuda_stream)
+{
+    if (!b || (law != BBE_LAW_POSITION && law != BBE_LAW_TIME) || (law == BBE_LAW_TIME && !horizon)) {
+        set_error("bbe_batch_set_law: batch is NULL, the law is unknown, or the time law has no horizon");
+        return BBE_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    if (law == BBE_LAW_POSITION) {
+        b->dev.law = BBE_LAW_POSITION;
+        b->h_t0.clear();
+        b->h_T.clear();
+        free_graph(b);
+        return BBE_OK;
+    }
+    const size_t nr = size_t(b->n_races);
+    std::vector<float> t0(nr, 0.0f), T(nr);
+    bbe_status st;
+    if ((elapsed && (st = copy_in(t0.data(), elapsed, nr * sizeof(float), s, "elapsed"))) ||
+        (st = copy_in(T.data(), horizon, nr * sizeof(float), s, "horizon")))
+        return st;
+    BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<float> inv(nr);
+    for (size_t r = 0; r < nr; ++r) {
+        if (!finite(t0[r]) || !(t0[r] >= 0.0f) || !finite(T[r]) || !(T[r] > 0.0f)) {
+            set_error("bbe_batch_set_law: race " + std::to_string(r) + " needs a finite elapsed >= 0 and horizon > 0");
+            return BBE_ERR_ARG;
+        }
+        inv[r] = 1.0f / T[r];  // binary32 division, round to nearest
+    }
+    void *mem = nullptr;
+    BBE_CUDA_TRY(cudaMallocAsync(&mem, 2 * nr * sizeof(float), s));
+    float *d_t0 = static_cast<float *>(mem), *d_inv = d_t0 + nr;
+    BBE_CUDA_TRY(cudaMemcpyAsync(d_t0, t0.data(), nr * sizeof(float), cudaMemcpyHostToDevice, s));
+    BBE_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), nr * sizeof(float), cudaMemcpyHostToDevice, s));
+    BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    BBE_CUDA_TRY(free_behind_uses(b, b->law_mem));
+    b->law_mem = mem;
+    b->h_t0 = std::move(t0);
+    b->h_T = std::move(T);
+    b->dev.law = BBE_LAW_TIME;
+    b->dev.t0 = d_t0;
+    b->dev.invT = d_inv;
+    free_graph(b);  // the captured launch parameters change
     return BBE_OK;
 }
 
@@ -877,6 +928,15 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
             st = bbe::stage_batch(&sub, int32_t(pick.size()), off.data(), L.data(), R.data(), d0.data(), mu.data(),
                                   sg.data(), rho.data(), P.data(), th.data(), nullptr, b->seed, bbe_dist(b->dist),
                                   0u, nullptr, s);
+            if (st == BBE_OK && b->dev.law == BBE_LAW_TIME) {
+                std::vector<float> el, hz;
+                for (int32_t r : pick) {
+                    el.push_back(b->h_t0[size_t(r)]);
+                    hz.push_back(b->h_T[size_t(r)]);
+                }
+                st = bbe_batch_set_law(sub, BBE_LAW_TIME, el.data(), hz.data(), s);
+                if (st) bbe_destroy_batch(sub);
+            }
             if (st) break;
             int32_t *sc = nullptr;
             if (cudaMallocAsync(&sc, d0.size() * sizeof(int32_t), s) != cudaSuccess) {
@@ -977,7 +1037,7 @@ void bbe_destroy_batch(bbe_batch *b)
     // for nothing and no other stream is held up.  Streams and events still in use are released
     // by CUDA when their work completes.
     free_graph(b);
-    for (void *p : {static_cast<void *>(b->d_items), static_cast<void *>(b->d_order_off), b->arena}) {
+    for (void *p : {static_cast<void *>(b->d_items), static_cast<void *>(b->d_order_off), b->arena, b->law_mem}) {
         if (p && free_behind_uses(b, p) != cudaSuccess) {
             // no free stream could be made: wait for this batch's uses on the host instead
             cudaGetLastError();

@@ -24,7 +24,24 @@ struct DevBatch {
     uint32_t race_id0;
     uint32_t seed_lo, seed_hi;
     int32_t dist;
+    int32_t law;              // responsiveness law: BBE_LAW_POSITION or BBE_LAW_TIME
+    const float *t0;          // time law: [n_races] steps elapsed before the state
+    const float *invT;        // time law: [n_races] 1 / expected duration in steps
 };
+
+// Responsiveness R_c of Eq. 1 at the start of step t of a dry-run (binary32, the oracle's
+// operation order): the position law from the fraction of the track covered, the time law
+// from the fraction of the expected duration elapsed, held at 1 once it is over.
+template <int LAW>
+__device__ __forceinline__ float responsiveness(float kr, float d, float invL, float t0, int t, float invT)
+{
+    if constexpr (LAW == BBE_LAW_TIME) {
+        const float u = fminf(__fmul_rn(__fadd_rn(t0, __int2float_rn(t)), invT), 1.0f);
+        return __fmaf_rn(kr, __fadd_rn(u, -0.5f), 1.0f);
+    } else {
+        return __fmaf_rn(kr, __fmaf_rn(d, invL, -0.5f), 1.0f);
+    }
+}
 
 // A unit of the persistent kernel's work queue: rollouts k_begin .. k_begin+k_count-1
 // of one race.
@@ -101,6 +118,8 @@ struct bbe_batch {
     std::vector<float> h_prev;      // empty when the default previous step is used
     std::vector<int32_t> h_race_ids;  // empty when race r has stream id race_id0 + r
     std::vector<int64_t> h_k0;        // first rollout index of each race; empty when all are 0
+    std::vector<float> h_t0, h_T;     // time law: elapsed steps and expected duration per race (empty: position law)
+    void *law_mem = nullptr;          // time law: device t0[n_races], invT[n_races]
 
     // library-owned device memory
     void *arena = nullptr;

@@ -44,7 +44,8 @@ __device__ __forceinline__ void lane_draw_block(float (&zc)[4], int c, int t, ui
 template <int DIST>
 __device__ __forceinline__ float lane_step(float d, float prev, const LaneComp &cp, int n, int segbase,
                                            bool lane_used, bool running, int c, int t, uint32_t k, uint32_t rid,
-                                           float invL, float (&zc)[4], const uint32_t (&rk)[20])
+                                           float invL, float (&zc)[4], const uint32_t (&rk)[20], int law = BBE_LAW_POSITION,
+                                           float t0 = 0.0f, float invT = 0.0f)
 {
     const int lane = threadIdx.x & 31;
     float fd = INFINITY, fp = 0.0f;
@@ -62,7 +63,8 @@ __device__ __forceinline__ float lane_step(float d, float prev, const LaneComp &
     if (running && (t & 3) == 0) lane_draw_block<DIST>(zc, c, t, k, rid, rk);
     const int ph = t & 3;
     const float z = ph == 0 ? zc[0] : (ph == 1 ? zc[1] : (ph == 2 ? zc[2] : zc[3]));
-    const float Rc = __fmaf_rn(cp.kr, __fmaf_rn(d, invL, -0.5f), 1.0f);
+    const float Rc = law == BBE_LAW_TIME ? responsiveness<BBE_LAW_TIME>(cp.kr, d, invL, t0, t, invT)
+                                         : responsiveness<BBE_LAW_POSITION>(cp.kr, d, invL, t0, t, invT);
     const bool blocked = hf && !(__fsub_rn(fd, d) > cp.theta);
     const float S = blocked ? __fmul_rn(Rc, fminf(prev, fp)) : __fmul_rn(__fmul_rn(Rc, cp.P), __fmaf_rn(cp.sigma, z, cp.mu));
     return fmaxf(S, kStepFloor);

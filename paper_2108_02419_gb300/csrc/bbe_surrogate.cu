@@ -2220,6 +2220,10 @@ bbe_status bbe_surrogate_grad(bbe_surrogate *s, const bbe_batch *b, const float 
         bbe::set_error("surrogate, batch, target or grad is NULL");
         return BBE_ERR_ARG;
     }
+    if (b->dev.law != BBE_LAW_POSITION) {
+        bbe::set_error("the surrogate takes position-law batches only (its inputs carry no elapsed time)");
+        return BBE_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     bbe_status e;
     if ((e = ensure_attrs())) return e;
@@ -2243,6 +2247,10 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
         !(cfg->eps > 0.0f) || !(cfg->weight_decay >= 0.0f)) {
         bbe::set_error("bbe_surrogate_train: bad arguments");
         return BBE_ERR_ARG;
+    }
+    if (b->dev.law != BBE_LAW_POSITION) {
+        bbe::set_error("the surrogate takes position-law batches only (its inputs carry no elapsed time)");
+        return BBE_ERR_UNSUPPORTED;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     bbe_status e;
@@ -2302,6 +2310,10 @@ bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *b, float *pr
         bbe::set_error("surrogate, batch or probs is NULL");
         return BBE_ERR_ARG;
     }
+    if (b->dev.law != BBE_LAW_POSITION) {
+        bbe::set_error("the surrogate takes position-law batches only (its inputs carry no elapsed time)");
+        return BBE_ERR_UNSUPPORTED;
+    }
     std::vector<int32_t> order(b->n_races);
     std::iota(order.begin(), order.end(), 0);
     return forward_all(s, b, order, probs, reinterpret_cast<cudaStream_t>(cuda_stream));
@@ -2313,6 +2325,10 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
     if (!s || !b || !probs) {
         bbe::set_error("surrogate, batch or probs is NULL");
         return BBE_ERR_ARG;
+    }
+    if (b->dev.law != BBE_LAW_POSITION) {
+        bbe::set_error("the surrogate takes position-law batches only (its inputs carry no elapsed time)");
+        return BBE_ERR_UNSUPPORTED;
     }
     if (!s->ranges.valid) {
         bbe::set_error("bbe_surrogate_infer: the network has no training ranges (train or load it first)");

@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(128) trajectory_kernel(TrajLaunch l)
             if (lane == 0) atomicOr(l.status, kStatusStepLimit);
             break;
         }
-        const float S = lane_step<DIST>(d, prev, cp, n, 0, used, used, lane, t, l.k, rid, invL, zc, l.round_key);
+        const float S = lane_step<DIST>(d, prev, cp, n, 0, used, used, lane, t, l.k, rid, invL, zc, l.round_key, b.law,
+                                        b.law == BBE_LAW_TIME ? b.t0[r] : 0.0f, b.law == BBE_LAW_TIME ? b.invT[r] : 0.0f);
         const float dn = __fadd_rn(d, S);
         if (used && t < l.cap) {
             pos[size_t(t) * n + lane] = dn;
@@ -289,6 +290,18 @@ bbe_status bbe_snapshot_batch(bbe_batch **out, const bbe_batch *src, int32_t rac
                                     sg.data(), rho.data(), P.data(), th.data(), pv.data(), src->seed,
                                     bbe_dist(src->dist), race_id0, ids.data(), s);
     if (e) return e;
+    if (src->dev.law == BBE_LAW_TIME) {
+        // a snapshot taken ts steps into the actual race has run t0 + ts steps; same horizon
+        std::vector<float> el(nr), hz(nr, src->h_T[size_t(race)]);
+        for (size_t si = 0; si < times.size(); ++si)
+            for (int bt = 0; bt < bettors; ++bt)
+                el[si * size_t(bettors) + size_t(bt)] = src->h_t0[size_t(race)] + float(times[si]);
+        if ((e = bbe_batch_set_law(*out, BBE_LAW_TIME, el.data(), hz.data(), s))) {
+            bbe_destroy_batch(*out);
+            *out = nullptr;
+            return e;
+        }
+    }
     *n_snapshots = int32_t(times.size());
     return BBE_OK;
 }
