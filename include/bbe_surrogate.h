@@ -101,6 +101,16 @@ BBE_API bbe_status bbe_surrogate_forward(bbe_surrogate *s, const bbe_batch *stat
 BBE_API bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *states, float *probs, uint8_t *used_mc,
                                        void *cuda_stream);
 
+/* bbe_surrogate_set_inputs -- which input columns the network sees: BBE_SURROGATE_INPUTS_DERIVED
+ * (14, the default: the five raw quantities and the nine values derived from them per race) or
+ * BBE_SURROGATE_INPUTS_RAW (5: position, remaining distance and the three parameters mu, sigma,
+ * rho, with the derived columns zero, i.e. the encoder of the surrogate workload's stated
+ * configuration).  Set it before training; it is saved with the checkpoint.  Errors:
+ * BBE_ERR_ARG. */
+#define BBE_SURROGATE_INPUTS_RAW 5
+#define BBE_SURROGATE_INPUTS_DERIVED 14
+BBE_API bbe_status bbe_surrogate_set_inputs(bbe_surrogate *s, int32_t inputs);
+
 /* bbe_surrogate_set_gate -- confidence gate of bbe_surrogate_infer: a race whose network output
  * has a second-largest probability above runner_up_max (a contest the network does not call
  * with near-certainty) is simulated with plain Monte Carlo instead.  runner_up_max in [0, 1];
@@ -149,9 +159,12 @@ BBE_API bbe_status bbe_surrogate_status(bbe_surrogate *s, void *cuda_stream);
  * in flight and the context stays usable.  Asynchronous.  Errors: BBE_ERR_ARG, BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_surrogate_wait_probe(bbe_surrogate *s, int64_t limit_ns, void *cuda_stream);
 
-/* bbe_surrogate_save / load -- checkpoint: parameters, Adam state, step count, epoch
- * position and training ranges, in a little-endian binary file.  load creates a handle on
- * the current device.  Errors: BBE_ERR_ARG (bad file), BBE_ERR_CUDA. */
+/* bbe_surrogate_save / load -- checkpoint: parameters, Adam state, step count, epoch and the
+ * position in it, input mode and training ranges, in a little-endian binary file.  load
+ * creates a handle on the current device; its first bbe_surrogate_train call continues the
+ * saved epoch (the epoch's race order is regenerated from the configuration's shuffle seed), so
+ * saving, loading and training on gives the parameters of an uninterrupted run with the same
+ * configuration and batch.  Errors: BBE_ERR_ARG (bad file), BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_surrogate_save(const bbe_surrogate *s, const char *path);
 BBE_API bbe_status bbe_surrogate_load(bbe_surrogate **out, const char *path);
 

@@ -86,15 +86,15 @@ static uint32_t bits_from_f32(float f) { uint32_t b; memcpy(&b, &f, 4); return b
 /* Natural log of a positive normal binary32 x.
  * x = 2^e * m with m in (sqrt(1/2), sqrt(2)];  f = m - 1 is exact (Sterbenz);
  * log m = f * g(f) with g(f) ~ log(1 + f) / f a degree-9 polynomial on [sqrt(1/2) - 1, sqrt(2) - 1]
- * (coefficients fitted by least squares on Chebyshev nodes, reweighted towards the minimax
- * relative error, 4e-9 before rounding to binary32), evaluated by Horner's rule with fused
+ * (coefficients from oracle/fit_log.py: Lawson's minimax iteration of least squares on 512
+ * Chebyshev nodes, relative error 4.1e-9 before rounding to binary32), evaluated by Horner's rule with fused
  * multiply-adds; log x = e ln2 + log m with ln2 split into a 16-bit head and a tail
  * (Cody & Waite). */
 float bbe_oracle_log(float x)
 {
     static const float G[10] = {
-        0x1.000000p+0f, -0x1.fffff8p-2f, 0x1.555552p-2f, -0x1.000428p-2f, 0x1.99a2f8p-3f,
-        -0x1.542678p-3f, 0x1.228226p-3f, -0x1.0f4ebcp-3f, 0x1.07eecap-3f, -0x1.36ee94p-4f,
+        0x1.000000p+0f, -0x1.fffff8p-2f, 0x1.555550p-2f, -0x1.000428p-2f, 0x1.99a402p-3f,
+        -0x1.542748p-3f, 0x1.227092p-3f, -0x1.0f3768p-3f, 0x1.084e42p-3f, -0x1.383dfep-4f,
     };
     const float LN2_HI = 0x1.62e4p-1f;
     const float LN2_LO = 0x1.7f7d1cp-20f;

@@ -3,9 +3,10 @@
 The network maps a race state to a win-probability vector, permutation-equivariantly:
 
   per competitor c of a race (n competitors, track length L), features: the raw quantities
-    [ d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1 ] and six values derived
-    from them per race (expected finish time and its spread, lag behind the race's fastest
-    expected finisher, gap to the competitor ahead, 1/n; see features())
+    [ d_c / L, (L - d_c) / 5000, mu_c - 16, sigma_c - 1, 2 rho_c - 1 ] and nine values derived
+    from them per race (expected finish time and its spread, the lag behind the race's fastest
+    expected finisher and its z-score, the gaps to the competitors ahead and behind, 1/n, and
+    the two catch-up shares; see features()); the five-input network sees the raw five alone
   encoder (3 layers, width 128, ReLU):  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)
   context: g = mean over the race's competitors of h3
   head:    u_c = relu(W4 [h3_c ; g] + b4)        (256 -> 128)
@@ -15,9 +16,9 @@ The network maps a race state to a win-probability vector, permutation-equivaria
            averaged over the races of a batch.
 
 Parameters live in one flat float vector in this order (row-major [out][in] matrices; W1 is
-stored with its input dimension padded from 5 to 16 with zeros):
+stored with its input dimension padded from 14 to 16 with zeros):
   W1 [128][16], b1 [128], W2 [128][128], b2, W3 [128][128], b3, W4 [128][256], b4, w5 [128], b5 [1].
-W1's columns 14..15 multiply zero inputs.
+W1's columns 14..15 multiply zero inputs (and columns 5..13 too in the five-input network).
 
 With ``bf16=True`` the forward pass rounds to bfloat16 (round to nearest even) exactly where a
 mixed-precision implementation keeps bfloat16 values: the weight matrices, the features, and

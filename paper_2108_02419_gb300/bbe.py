@@ -412,6 +412,7 @@ def _sg():
             "bbe_surrogate_infer": [vp, vp, vp, vp, vp],
             "bbe_surrogate_status": [vp, vp],
             "bbe_surrogate_wait_probe": [vp, C.c_int64, vp],
+            "bbe_surrogate_set_inputs": [vp, C.c_int32],
             "bbe_surrogate_set_gate": [vp, C.c_float],
             "bbe_surrogate_set_fallback": [vp, C.c_int64, C.c_double],
             "bbe_surrogate_fallback_budget": [C.c_int32, vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)],
@@ -474,6 +475,13 @@ def bbe_surrogate_forward(s: int, batch: int, probs, stream=None) -> None:
 def bbe_surrogate_infer(s: int, batch: int, probs, used_mc=None, stream=None) -> None:
     _check(_sg().bbe_surrogate_infer(s, batch, _ptr(probs, np.float32), _ptr(used_mc, np.uint8), _stream(stream)),
            "bbe_surrogate_infer")
+
+
+SURROGATE_INPUTS_RAW, SURROGATE_INPUTS_DERIVED = 5, 14
+
+
+def bbe_surrogate_set_inputs(s: int, inputs: int) -> None:
+    _check(_sg().bbe_surrogate_set_inputs(s, int(inputs)), "bbe_surrogate_set_inputs")
 
 
 def bbe_surrogate_set_gate(s: int, runner_up_max: float) -> None:

@@ -10,8 +10,9 @@
 //
 //   log x:  x = 2^e m, m in (sqrt(1/2), sqrt(2)], f = m - 1 (exact),
 //           log m = f g(f), g a degree-9 fit of log(1 + f) / f on [sqrt(1/2) - 1, sqrt(2) - 1]
-//           (least squares on Chebyshev nodes reweighted towards the minimax relative
-//           error) [Horner, fma], log x = e ln2_hi + (e ln2_lo + log m).
+//           (Lawson's minimax iteration of least squares on 512 Chebyshev nodes, 50 rounds,
+//           constant term 1, coefficients rounded to binary32) [Horner, fma],
+//           log x = e ln2_hi + (e ln2_lo + log m).
 //   sqrt:   correctly rounded (see sqrt_f32x2).
 //   sincos: u = m24 2^-24, q = round(4u) by integer arithmetic, f = u - q/4 exactly,
 //           Taylor series of sin(2 pi f) to degree 9 and cos(2 pi f) to degree 10 in f
@@ -64,13 +65,13 @@ __device__ __forceinline__ float2 log_f32x2(float2 x)
     ea = ha ? ea + 1 : ea;
     eb = hb ? eb + 1 : eb;
     const float2 f = __fadd2_rn(make_float2(__uint_as_float(ma), __uint_as_float(mb)), splat2(-1.0f));
-    float2 g = __ffma2_rn(f, splat2(-0x1.36ee94p-4f), splat2(0x1.07eecap-3f));
-    g = __ffma2_rn(f, g, splat2(-0x1.0f4ebcp-3f));
-    g = __ffma2_rn(f, g, splat2(0x1.228226p-3f));
-    g = __ffma2_rn(f, g, splat2(-0x1.542678p-3f));
-    g = __ffma2_rn(f, g, splat2(0x1.99a2f8p-3f));
+    float2 g = __ffma2_rn(f, splat2(-0x1.383dfep-4f), splat2(0x1.084e42p-3f));
+    g = __ffma2_rn(f, g, splat2(-0x1.0f3768p-3f));
+    g = __ffma2_rn(f, g, splat2(0x1.227092p-3f));
+    g = __ffma2_rn(f, g, splat2(-0x1.542748p-3f));
+    g = __ffma2_rn(f, g, splat2(0x1.99a402p-3f));
     g = __ffma2_rn(f, g, splat2(-0x1.000428p-2f));
-    g = __ffma2_rn(f, g, splat2(0x1.555552p-2f));
+    g = __ffma2_rn(f, g, splat2(0x1.555550p-2f));
     g = __ffma2_rn(f, g, splat2(-0x1.fffff8p-2f));
     g = __ffma2_rn(f, g, splat2(1.0f));
     const float2 logm = __fmul2_rn(f, g);

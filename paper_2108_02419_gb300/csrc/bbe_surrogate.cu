@@ -115,6 +115,8 @@ struct SgArgs {
     float *logits;         // forward: per-tile-row logits
     int *status;           // set to 1 when a bounded device wait gave up
     long long wait_ns;     // limit of each wait
+    int32_t raw_only;      // 1: the five raw inputs only (the derived columns are zero)
+    float *b5_part;        // training: per tile, the sum of its d loss / d logit (the b5 gradient's terms)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -593,12 +595,14 @@ __global__ void __launch_bounds__(TILE) sg_prep(SgArgs a)
     __shared__ RowMap m;
     __shared__ FeatScratch fs;
     const int tid = threadIdx.x, ti = blockIdx.x;
-    // training: the b5 gradient is accumulated by the chain kernel and starts at zero
-    if (a.train && ti == 0 && tid == 0) a.grad[OFF_B5] = 0.0f;
     const SgTile t = a.tiles[ti];
     build_rowmap(m, a, t, tid, BlockSync{});
     float f[KIN];
     tile_features(f, fs, a, m, tid, BlockSync{});
+    if (a.raw_only) {
+#pragma unroll
+        for (int k = RAW; k < KIN; ++k) f[k] = 0.0f;
+    }
     const uint4 lo = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
                                 pack_bf16x2(f[6], f[7]));
     const uint4 hi = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]), pack_bf16x2(f[12], f[13]),
@@ -1064,9 +1068,10 @@ __global__ void __launch_bounds__(256, 1) sg_backward_chain(SgArgs a, int n_tile
             }
         }
         if (tid == 0 && in_ok) {
+            // this tile's term of the b5 gradient; the reduction adds the tiles in order
             float sdl = 0.0f;
             for (int q = 0; q < TILE; ++q) sdl += in.dlogit[q];
-            atomicAdd(a.grad + OFF_B5, sdl);
+            a.b5_part[ti] = sdl;
         }
         fence_async_smem();
         tc_before_sync();
@@ -1418,10 +1423,19 @@ __device__ __forceinline__ int param_of_stored(int s)
 
 // gradient = sum over the owning group's blocks of their partials, in block order (b5 is
 // accumulated by the chain kernel and left alone); reads in stored order, writes by parameter
-__global__ void sg_reduce_grad(float *grad, const float *partial, int wgroups)
+// The b5 gradient: the tiles' sums of d loss / d logit added in tile order (deterministic).
+__device__ float b5_gradient(const float *b5_part, int n_tiles)
+{
+    float g = 0.0f;
+    for (int i = 0; i < n_tiles; ++i) g += b5_part[i];
+    return g;
+}
+
+__global__ void sg_reduce_grad(float *grad, const float *partial, int wgroups, const float *b5_part, int n_tiles)
 {
     pdl_enter();
     const int si = blockIdx.x * blockDim.x + threadIdx.x;
+    if (si == OFF_B5) grad[OFF_B5] = b5_gradient(b5_part, n_tiles);
     if (si >= N_PARAMS || si == OFF_B5) return;
     const int group = (si >= OFF_W4 && si < OFF_B5) ? 0 : 1;
     const float *src = partial + size_t(group) * wgroups * N_PARAMS + si;
@@ -1486,7 +1500,8 @@ constexpr int RA_MATRIX_BLOCKS = RA_TILES_W1 + 2 * RA_TILES_W2 + RA_TILES_W4;
 constexpr int RA_VECTOR_BLOCKS = (5 * H + 1 + 255) / 256;  // b1, b2, b3, b4, w5, b5
 
 __global__ void __launch_bounds__(256) sg_reduce_adam(float *grad, const float *partial, int wgroups, float *w,
-                                                      float *m, float *v, bf16 *wb, bf16 *wc, AdamStep h)
+                                                      float *m, float *v, bf16 *wb, bf16 *wc, AdamStep h,
+                                                      const float *b5_part, int n_tiles)
 {
     pdl_enter();
     __shared__ float tile[16][17];
@@ -1504,7 +1519,8 @@ __global__ void __launch_bounds__(256) sg_reduce_adam(float *grad, const float *
         }
         float g;
         if (pidx == OFF_B5) {
-            g = grad[OFF_B5];
+            g = b5_gradient(b5_part, n_tiles);
+            grad[OFF_B5] = g;
         } else {
             const int group = pidx >= OFF_W4 ? 0 : 1;
             const float *src = partial + size_t(group) * wgroups * N_PARAMS + pidx;
@@ -1653,6 +1669,7 @@ struct bbe_surrogate {
     size_t order_cap = 0;
     unsigned char *ws = nullptr;  // training workspace, WS_TILE bytes per tile
     float *ws_dlogit = nullptr;
+    float *ws_b5 = nullptr;       // per-tile terms of the b5 gradient
     size_t ws_tiles = 0;
     float *d_partial = nullptr;   // weight-gradient partials of the backward's blocks
     size_t partial_cap = 0;
@@ -1666,6 +1683,7 @@ struct bbe_surrogate {
     std::vector<uint8_t> iplan_flag;
     // confidence gate: runner-up probability above which a race goes to Monte Carlo
     float gate = 1.0f;
+    int32_t raw_only = 0;  // 1: the network sees the five raw inputs only
     uint8_t *d_gate = nullptr;
     size_t gate_cap = 0;
     // two-stage fallback (pilot 0: each race's own budget) and the last call's fallback totals
@@ -1732,11 +1750,14 @@ bbe_status ensure_ws(bbe_surrogate *s, size_t tiles)
     if (tiles <= s->ws_tiles && s->ws) return BBE_OK;
     if (s->ws) cudaFree(s->ws);
     if (s->ws_dlogit) cudaFree(s->ws_dlogit);
+    if (s->ws_b5) cudaFree(s->ws_b5);
     s->ws = nullptr;
     s->ws_dlogit = nullptr;
+    s->ws_b5 = nullptr;
     s->ws_tiles = 0;
     SG_TRY(cudaMalloc(&s->ws, tiles * WS_TILE));
     SG_TRY(cudaMalloc(&s->ws_dlogit, tiles * TILE * sizeof(float)));
+    SG_TRY(cudaMalloc(&s->ws_b5, tiles * sizeof(float)));
     s->ws_tiles = tiles;
     return BBE_OK;
 }
@@ -1752,7 +1773,19 @@ SgArgs base_args(const bbe_surrogate *s, const bbe_batch *b)
     a.b = b->dev;
     a.tiles = s->d_tiles;
     a.order = s->d_order;
+    a.raw_only = s->raw_only;
     return a;
+}
+
+// The shuffled race order of training epoch e (1, 2, ...): a permutation of the batch's races
+// drawn from the configuration's shuffle seed and e alone, so that a handle loaded from a
+// checkpoint continues the epoch it was saved in.
+void epoch_permutation(std::vector<int32_t> &order, int32_t n_races, uint64_t shuffle_seed, uint64_t e)
+{
+    order.resize(size_t(n_races));
+    std::iota(order.begin(), order.end(), 0);
+    std::mt19937_64 rng(shuffle_seed ^ (0x9E3779B97F4A7C15ull * e));
+    std::shuffle(order.begin(), order.end(), rng);
 }
 
 // Launch with programmatic stream serialization: the kernel may be scheduled while the one
@@ -1852,6 +1885,7 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.grad = s->grad;
     a.ws = s->ws;
     a.ws_dlogit = s->ws_dlogit;
+    a.b5_part = s->ws_b5;
     a.train = 1;
     int dev = 0, sms = 0;
     SG_TRY(cudaGetDevice(&dev));
@@ -1860,15 +1894,17 @@ bbe_status train_pass(bbe_surrogate *s, const bbe_batch *b, const float *target,
     a.wgroups = int32_t(std::max<int64_t>(1, std::min<int64_t>(nt, std::max(1, sms / 2))));
     if ((e = ensure_buf(s->d_partial, s->partial_cap, size_t(2) * a.wgroups * N_PARAMS))) return e;
     a.partial = s->d_partial;
-    if ((e = launch_forward(s, a, nt, st))) return e;  // sg_prep zeroes the b5 gradient
+    if ((e = launch_forward(s, a, nt, st))) return e;
     SG_TRY(launch_pdl(sg_backward_chain, unsigned(std::min<int64_t>(nt, sms)), 256, chain_smem(), st, a, int(nt)));
     SG_TRY(launch_pdl(sg_backward_wgrad, unsigned(2 * a.wgroups), 128, wgrad_smem(), st, a, int(nt)));
     if (adam)
         SG_TRY(launch_pdl(sg_reduce_adam, unsigned(RA_MATRIX_BLOCKS + RA_VECTOR_BLOCKS), 256, 0, st, s->grad,
-                          static_cast<const float *>(s->d_partial), a.wgroups, s->w, s->m, s->v, s->wb, s->wc, *adam));
+                          static_cast<const float *>(s->d_partial), a.wgroups, s->w, s->m, s->v, s->wb, s->wc, *adam,
+                          static_cast<const float *>(s->ws_b5), int(nt)));
     else
         SG_TRY(launch_pdl(sg_reduce_grad, unsigned((N_PARAMS + 255) / 256), 256, 0, st, s->grad,
-                          static_cast<const float *>(s->d_partial), a.wgroups));
+                          static_cast<const float *>(s->d_partial), a.wgroups, static_cast<const float *>(s->ws_b5),
+                          int(nt)));
     return BBE_OK;
 }
 
@@ -1980,7 +2016,7 @@ void free_surrogate(bbe_surrogate *s)
 {
     for (void *p : {(void *)s->w, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->wb, (void *)s->wc,
                     (void *)s->d_status, (void *)s->d_xbuf, (void *)s->d_meta, (void *)s->d_logits, (void *)s->d_tiles,
-                    (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->d_loss, (void *)s->d_itiles,
+                    (void *)s->d_order, (void *)s->ws, (void *)s->ws_dlogit, (void *)s->ws_b5, (void *)s->d_loss, (void *)s->d_itiles,
                     (void *)s->d_iorder, (void *)s->d_gate, (void *)s->d_partial})
         if (p) cudaFree(p);
 }
@@ -2260,9 +2296,13 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
         s->ranges_version += 1;
     }
     if (s->plan_batch != b || int64_t(s->epoch_order.size()) != b->n_races) {
+        // a handle loaded from a checkpoint (no batch seen yet, in the middle of an epoch)
+        // continues that epoch; any other change of batch starts a new one
+        const bool resume = s->plan_batch == nullptr && s->epoch > 0 && s->cursor > 0 && s->cursor < b->n_races;
         s->plan_batch = b;
         s->epoch_order.clear();
-        s->cursor = 0;
+        if (resume) epoch_permutation(s->epoch_order, b->n_races, cfg->shuffle_seed, s->epoch);
+        else s->cursor = 0;
     }
     if (loss_log) SG_TRY(cudaMemsetAsync(loss_log, 0, size_t(cfg->steps) * sizeof(float), st));
     // plan every step of the call on the host first (per-epoch shuffle, tile packing), upload
@@ -2273,11 +2313,8 @@ bbe_status bbe_surrogate_train(bbe_surrogate *s, const bbe_batch *b, const float
     int64_t max_nt = 0;
     for (int32_t k = 0; k < cfg->steps; ++k) {
         if (s->epoch_order.empty() || s->cursor >= int64_t(s->epoch_order.size())) {
-            s->epoch_order.resize(b->n_races);
-            std::iota(s->epoch_order.begin(), s->epoch_order.end(), 0);
-            std::mt19937_64 rng(cfg->shuffle_seed ^ (0x9E3779B97F4A7C15ull * (s->epoch + 1)));
-            std::shuffle(s->epoch_order.begin(), s->epoch_order.end(), rng);
             s->epoch += 1;
+            epoch_permutation(s->epoch_order, b->n_races, cfg->shuffle_seed, s->epoch);
             s->cursor = 0;
         }
         const int64_t take = std::min<int64_t>(cfg->batch_states, int64_t(s->epoch_order.size()) - s->cursor);
@@ -2399,6 +2436,17 @@ bbe_status bbe_surrogate_infer(bbe_surrogate *s, const bbe_batch *b, float *prob
     return BBE_OK;
 }
 
+bbe_status bbe_surrogate_set_inputs(bbe_surrogate *s, int32_t inputs)
+{
+    if (!s || (inputs != BBE_SURROGATE_INPUTS_RAW && inputs != BBE_SURROGATE_INPUTS_DERIVED)) {
+        bbe::set_error("bbe_surrogate_set_inputs: surrogate is NULL or inputs is not 5 or 14");
+        return BBE_ERR_ARG;
+    }
+    s->raw_only = inputs == BBE_SURROGATE_INPUTS_RAW ? 1 : 0;
+    s->iplan_serial = 0;
+    return BBE_OK;
+}
+
 bbe_status bbe_surrogate_set_gate(bbe_surrogate *s, float runner_up_max)
 {
     if (!s || !(runner_up_max >= 0.0f && runner_up_max <= 1.0f)) {
@@ -2490,9 +2538,10 @@ bbe_status bbe_surrogate_save(const bbe_surrogate *s, const char *path)
         bbe::set_error(std::string("cannot open ") + path);
         return BBE_ERR_ARG;
     }
-    const char magic[8] = {'B', 'B', 'E', 'S', 'G', '0', '0', '1'};
+    const char magic[8] = {'B', 'B', 'E', 'S', 'G', '0', '0', '2'};
     const int64_t n = N_PARAMS;
     bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&n, 8, 1, f) == 1 &&
+              std::fwrite(&s->raw_only, 4, 1, f) == 1 &&
               std::fwrite(&s->step, 8, 1, f) == 1 && std::fwrite(&s->epoch, 8, 1, f) == 1 &&
               std::fwrite(&s->cursor, 8, 1, f) == 1 && std::fwrite(&s->ranges, sizeof(SgRanges), 1, f) == 1 &&
               std::fwrite(w.data(), 4, n, f) == size_t(n) && std::fwrite(m.data(), 4, n, f) == size_t(n) &&
@@ -2522,8 +2571,12 @@ bbe_status bbe_surrogate_load(bbe_surrogate **out, const char *path)
     uint64_t epoch = 0;
     SgRanges ranges;
     std::vector<float> w(N_PARAMS), m(N_PARAMS), v(N_PARAMS);
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "BBESG001", 8) == 0 &&
-              std::fread(&n, 8, 1, f) == 1 && n == N_PARAMS && std::fread(&step, 8, 1, f) == 1 &&
+    int32_t raw_only = 0;
+    // version 2 adds the input mode after the parameter count; version 1 files are read too
+    bool ok = std::fread(magic, 1, 8, f) == 8 &&
+              (std::memcmp(magic, "BBESG001", 8) == 0 || std::memcmp(magic, "BBESG002", 8) == 0) &&
+              std::fread(&n, 8, 1, f) == 1 && n == N_PARAMS &&
+              (magic[7] == '1' || std::fread(&raw_only, 4, 1, f) == 1) && std::fread(&step, 8, 1, f) == 1 &&
               std::fread(&epoch, 8, 1, f) == 1 && std::fread(&cursor, 8, 1, f) == 1 &&
               std::fread(&ranges, sizeof(SgRanges), 1, f) == 1 && std::fread(w.data(), 4, n, f) == size_t(n) &&
               std::fread(m.data(), 4, n, f) == size_t(n) && std::fread(v.data(), 4, n, f) == size_t(n);
@@ -2551,6 +2604,7 @@ bbe_status bbe_surrogate_load(bbe_surrogate **out, const char *path)
     s->step = step;
     s->epoch = epoch;
     s->cursor = cursor;
+    s->raw_only = raw_only ? 1 : 0;
     s->ranges = ranges;
     s->ranges_version += 1;
     *out = s;

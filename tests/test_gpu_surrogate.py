@@ -108,10 +108,20 @@ def test_gradient_matches_reference(bbe):
     want = S.backward(params.astype(np.float64), x, rb.race_off, target.astype(np.float64), bf16=True)
     want_loss = S.loss(params.astype(np.float64), x, rb.race_off, target.astype(np.float64), bf16=True)
     assert abs(lv - want_loss) < 1e-3 * abs(want_loss)
+    assert_gradient_close(g, want)
+
+
+def assert_gradient_close(g, want):
+    """Element by element: |gpu - ref| <= 3 % of the element plus 0.5 % of its block's largest
+    element.  The GPU sums bfloat16-rounded du, da and pooled dz where the reference sums the
+    unrounded values (bias gradients, the context's gradient): bfloat16 carries 8 significant
+    bits (a relative rounding of 2^-9), so those sums differ by a few parts per thousand where
+    their terms cancel, which the block-relative term absorbs."""
     for name, _ in S.SHAPES[:-1]:  # b5's gradient is ~0 (targets sum to 1)
         gu, wu = S.unpack(g)[name].ravel(), S.unpack(want)[name].ravel()
-        rel = np.linalg.norm(gu - wu) / np.linalg.norm(wu)
-        assert rel < 2e-2, (name, rel)
+        bound = 3e-2 * np.abs(wu) + 5e-3 * np.abs(wu).max()
+        worst = np.max(np.abs(gu - wu) / bound)
+        assert worst <= 1.0, (name, worst, int(np.argmax(np.abs(gu - wu) / bound)))
 
 
 def test_first_adam_step_follows_the_reference_gradient(bbe):
@@ -343,3 +353,54 @@ def test_relabelling_competitors_relabels_output(bbe):
     finally:
         bbe.bbe_surrogate_destroy(s)
     assert np.allclose(outs[1], outs[0][perm], atol=2e-3)
+
+
+def test_raw_inputs_forward_matches_reference(bbe):
+    # the five-input network: derived columns zero on both sides
+    rb = W.uneven_batch(seed=46, n_races=200, rollouts=10)
+    params = S.init_params(7).astype(np.float32)
+    s = bbe.bbe_surrogate_create(0)
+    try:
+        bbe.bbe_surrogate_set_params(s, params)
+        bbe.bbe_surrogate_set_inputs(s, bbe.SURROGATE_INPUTS_RAW)
+        with bbe.Batch(rb) as b:
+            probs = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
+            bbe.bbe_surrogate_forward(s, b.handle, probs)
+            bbe.bbe_surrogate_status(s)
+            got = probs.cpu().numpy().astype(np.float64)
+    finally:
+        bbe.bbe_surrogate_destroy(s)
+    L = np.repeat(rb.L.astype(np.float64), rb.sizes())
+    want, _ = S.forward(params.astype(np.float64), S.features(rb.d0, L, rb.mu, rb.sigma, rb.rho), rb.race_off,
+                        bf16=True)
+    err = np.abs(got - want)
+    assert err.max() < 5e-3 and err.mean() < 3e-4, (err.max(), err.mean())
+
+
+def test_training_resumes_from_a_checkpoint(bbe, tmp_path):
+    # save in the middle of an epoch, load into a new handle, train on: the parameters equal
+    # those of the run that was never interrupted (the epoch's order is regenerated, Adam's
+    # moments and step count are restored)
+    rb = W.uneven_batch(seed=47, n_races=700, n_lo=2, n_hi=12, rollouts=300)
+    kw = dict(lr=2e-3, batch_states=128, shuffle_seed=11)
+    path = str(tmp_path / "mid.bin")
+    with bbe.Batch(rb) as b:
+        counts, _ = b.rollout()
+        probs, _ = b.win_probs(counts)
+        a = bbe.bbe_surrogate_create(3)
+        try:
+            bbe.bbe_surrogate_train(a, b.handle, probs, steps=9, **kw)  # 9 x 128 races: into epoch 2
+            bbe.bbe_surrogate_save(a, path)
+            bbe.bbe_surrogate_train(a, b.handle, probs, steps=8, **kw)
+            torch.cuda.synchronize()
+            want = bbe.bbe_surrogate_get_params(a)
+        finally:
+            bbe.bbe_surrogate_destroy(a)
+        c = bbe.bbe_surrogate_load(path)
+        try:
+            bbe.bbe_surrogate_train(c, b.handle, probs, steps=8, **kw)
+            torch.cuda.synchronize()
+            got = bbe.bbe_surrogate_get_params(c)
+        finally:
+            bbe.bbe_surrogate_destroy(c)
+    assert np.array_equal(got, want)

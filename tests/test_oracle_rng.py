@@ -160,3 +160,10 @@ def test_stream_keyed_by_all_four_coordinates(oracle_lib, dist):
         assert (a != b).mean() > 0.4
     else:
         assert all(o != base for o in others)
+
+
+def test_log_constants_are_the_committed_fit():
+    # oracle/fit_log.py reproduces the ten binary32 coefficients of the log polynomial
+    from oracle import fit_log
+
+    assert fit_log.main(["--check"]) == 0

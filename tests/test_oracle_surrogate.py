@@ -116,3 +116,33 @@ def test_derived_features_worked_example():
     perm = [2, 0, 1]
     xp = S.features(d[perm], L, mu[perm], sig[perm], rho[perm], [0, 3])
     assert np.allclose(xp, x[perm])
+
+
+def test_worked_example_by_hand():
+    """A two-competitor race through hand-set weights, computed by hand.
+
+    A: d/L = 0.2, mu - 16 = 0.5;  B: d/L = 0.6, mu - 16 = -0.5 (sigma 1, rho 1/2: columns 3, 4 zero).
+    W1 picks column 0 into unit 0 and column 2 into unit 1; W2, W3 pass units 0, 1 on:
+      h3_A = (0.2, 0.5), h3_B = (0.6, 0)             (ReLU clips B's -0.5)
+      g = mean = (0.4, 0.25)
+    W4 row 0 = 3 h3_0 - 2 g_0, row 1 = 2 h3_1 + g_1 (b4 = 0):
+      u_A = (relu(0.6 - 0.8), relu(1.0 + 0.25)) = (0, 1.25)
+      u_B = (relu(1.8 - 0.8), relu(0 + 0.25))   = (1.0, 0.25)
+    w5 = (1.5, 1.0), b5 = 0.2:  logit_A = 1.25 + 0.2 = 1.45, logit_B = 1.5 + 0.25 + 0.2 = 1.95
+      q_A = 1 / (1 + e^0.5), q_B = 1 / (1 + e^-0.5).
+    Pooling by sum (g = (0.8, 0.5)) would give logits 1.7 and 1.0, concatenating [g; h3]
+    instead of [h3; g] or dropping a ReLU other values still."""
+    p = {k: np.zeros(shp) for k, shp in S.SHAPES}
+    p["W1"][0, 0] = 1.0
+    p["W1"][1, 2] = 1.0
+    for k in ("W2", "W3"):
+        p[k][0, 0] = p[k][1, 1] = 1.0
+    p["W4"][0, 0], p["W4"][0, 128] = 3.0, -2.0
+    p["W4"][1, 1], p["W4"][1, 129] = 2.0, 1.0
+    p["w5"][0], p["w5"][1] = 1.5, 1.0
+    p["b5"][0] = 0.2
+    x = S.features([1000.0, 3000.0], [5000.0, 5000.0], [16.5, 15.5], [1.0, 1.0], [0.5, 0.5])
+    q, c = S.forward(S.pack(p), x, [0, 2])
+    assert np.allclose(c["g"][0, :2], [0.4, 0.25], atol=1e-15)
+    assert np.allclose(c["logit"], [1.45, 1.95], atol=1e-14)
+    assert np.allclose(q, [1.0 / (1.0 + np.exp(0.5)), 1.0 / (1.0 + np.exp(-0.5))], atol=1e-15)
