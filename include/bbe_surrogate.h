@@ -146,6 +146,12 @@ BBE_API bbe_status bbe_surrogate_fallback_budget(int32_t n, const int32_t *count
  * 0 when the call failed).  Either pointer may be NULL.  Errors: BBE_ERR_ARG. */
 BBE_API bbe_status bbe_surrogate_fallback_stats(const bbe_surrogate *s, int64_t *races, int64_t *rollouts);
 
+/* bbe_surrogate_fallback_times -- host wall time of the last bbe_surrogate_infer's Monte Carlo
+ * fallback, by phase, into seconds[5]: staging the fallback races, the pilot (or the whole
+ * budget without one: its rollouts and their read-back), the budget rule, staging the top-up,
+ * and the top-up with the final probabilities.  Errors: BBE_ERR_ARG. */
+BBE_API bbe_status bbe_surrogate_fallback_times(const bbe_surrogate *s, double *seconds);
+
 /* bbe_surrogate_status -- synchronise cuda_stream and report whether a kernel launched on
  * this handle gave up a bounded device wait since the last call (the flag is then cleared;
  * the outputs of the affected calls are undefined).  Errors: BBE_ERR_TIMEOUT, BBE_ERR_ARG,

@@ -417,6 +417,7 @@ def _sg():
             "bbe_surrogate_set_fallback": [vp, C.c_int64, C.c_double],
             "bbe_surrogate_fallback_budget": [C.c_int32, vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)],
             "bbe_surrogate_fallback_stats": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "bbe_surrogate_fallback_times": [vp, vp],
             "bbe_surrogate_save": [vp, C.c_char_p],
             "bbe_surrogate_load": [C.POINTER(vp), C.c_char_p],
         }
@@ -502,6 +503,12 @@ def bbe_surrogate_fallback_budget(counts, pilot: int, cap: int, max_sd: float) -
     _check(_sg().bbe_surrogate_fallback_budget(int(c.size), c.ctypes.data_as(C.c_void_p), int(pilot), int(cap),
                                                float(max_sd), C.byref(out)), "bbe_surrogate_fallback_budget")
     return out.value
+
+
+def bbe_surrogate_fallback_times(s: int) -> np.ndarray:
+    out = np.zeros(5, np.float64)
+    _check(_sg().bbe_surrogate_fallback_times(s, out.ctypes.data), "bbe_surrogate_fallback_times")
+    return out
 
 
 def bbe_surrogate_fallback_stats(s: int) -> tuple:

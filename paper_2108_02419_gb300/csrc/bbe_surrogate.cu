@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1690,6 +1691,7 @@ struct bbe_surrogate {
     int64_t fb_pilot = 0;
     double fb_sd = 0.0;
     int64_t fb_races = 0, fb_rollouts = 0;
+    double fb_times[5] = {0, 0, 0, 0, 0};  // last fallback: staging, pilot, budget, top-up staging, top-up and finish (s)
     int64_t iplan_tiles = 0;
     SgTile *d_itiles = nullptr;
     size_t itiles_cap = 0;
@@ -2132,6 +2134,14 @@ bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     FallbackScratch sc;
     sc.st = st;
     const size_t m = mc.size();
+    using clk = std::chrono::steady_clock;
+    auto t_mark = clk::now();
+    auto lap = [&](int slot) {
+        const auto now = clk::now();
+        s->fb_times[slot] += std::chrono::duration<double>(now - t_mark).count();
+        t_mark = now;
+    };
+    for (double &t : s->fb_times) t = 0.0;
     std::vector<int64_t> cap(m), R1(m);
     for (size_t i = 0; i < m; ++i) {
         cap[i] = b->h_R[size_t(mc[i])];
@@ -2141,6 +2151,7 @@ bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     bbe_batch *sub1 = nullptr;
     std::vector<int32_t> dst1;
     if ((e = stage_subset(b, mc, R1, nullptr, sc, &sub1, dst1))) return e;
+    lap(0);
     const size_t n1 = dst1.size();
     int32_t *c1 = nullptr, *d_dst = nullptr;
     int64_t *d_total = nullptr;
@@ -2151,6 +2162,7 @@ bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
         std::vector<int32_t> h1(n1);
         SG_TRY(cudaMemcpyAsync(h1.data(), c1, n1 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         if ((e = bbe_batch_status(sub1, st))) return e;  // synchronises the stream
+        lap(1);
         std::vector<int32_t> races2, map2;
         std::vector<int64_t> R2, k2;
         for (size_t i = 0; i < m; ++i) {
@@ -2163,10 +2175,12 @@ bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
                 for (int j = a0; j < a1; ++j) map2.push_back(j);
             }
         }
+        lap(2);
         if (!races2.empty()) {
             bbe_batch *sub2 = nullptr;
             std::vector<int32_t> src2;
             if ((e = stage_subset(b, races2, R2, &k2, sc, &sub2, src2))) return e;
+            lap(3);
             const size_t n2 = map2.size();
             int32_t *c2 = nullptr, *d_map = nullptr;
             if ((e = sc.alloc(&c2, n2)) || (e = sc.alloc(&d_map, n2))) return e;
@@ -2182,6 +2196,7 @@ bbe_status mc_fallback(bbe_surrogate *s, const bbe_batch *b, const std::vector<i
     fallback_probs<<<unsigned((n1 + 255) / 256), 256, 0, st>>>(c1, sub1->dev.comp_race, d_total, d_dst, probs, int(n1));
     SG_TRY(cudaGetLastError());
     if ((e = bbe_batch_status(sub1, st))) return e;  // synchronises: host vectors stay alive until here
+    lap(4);
     int64_t sum = 0;
     for (int64_t t : total) sum += t;
     s->fb_rollouts = sum;
@@ -2479,6 +2494,16 @@ bbe_status bbe_surrogate_fallback_budget(int32_t n, const int32_t *counts, int64
         return BBE_ERR_ARG;
     }
     *budget = fallback_budget(n, counts, pilot, cap, max_sd);
+    return BBE_OK;
+}
+
+bbe_status bbe_surrogate_fallback_times(const bbe_surrogate *s, double *seconds)
+{
+    if (!s || !seconds) {
+        bbe::set_error("surrogate or seconds is NULL");
+        return BBE_ERR_ARG;
+    }
+    for (int i = 0; i < 5; ++i) seconds[i] = s->fb_times[i];
     return BBE_OK;
 }
 
