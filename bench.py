@@ -231,20 +231,28 @@ def measured_peaks() -> dict:
     return {}
 
 
+# the sources of the win-count rollout kernel (a traffic record applies while they hash the same)
+KERNEL_SOURCES = ("bbe_win.cuh", "bbe_win.cu", "bbe_rng.cuh", "bbe_internal.h")
+
+
+def kernel_sources_sha16() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_02419_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(workload: str, races: int):
     """DRAM bytes per rollout launch from the committed ncu record, or None when the kernel
     sources changed since the counters were taken (or the workload is not the recorded one)."""
-    import hashlib
-
     path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.json")
     if races or not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256()
-    for f in ("bbe_win.cu", "bbe_rng.cuh"):
-        with open(os.path.join(ROOT, "paper_2108_02419_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
+    if kernel_sources_sha16() != rec.get("kernel_sources_sha256_16"):
         return None
     w = rec.get("workloads", {}).get(workload)
     return None if w is None else w["dram_bytes_per_launch"]

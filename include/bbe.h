@@ -295,10 +295,11 @@ BBE_API bbe_status bbe_batch_get_cfg(const bbe_batch *batch, bbe_launch_cfg *cfg
 /* bbe_batch_autotune -- pick this batch's launch by timing it (the batching workload asks for
  * block shapes and rollouts per warp chosen by measurement).  First, for each competitor count
  * present, a sample of up to 64 of its races is run once per layout (1 to 4 competitors per
- * lane) and the fastest layout is kept for that count (ties within 1 % keep two); then block
- * shapes (warps per block x blocks per SM, capped by occupancy: 4 x 16, 8 x 8, 2 x 32) and
- * work-item sizes (16, 32, 64 rollouts per lane) are each timed (the better of two full passes
- * with that per-count layout); the starting shape stays unless another is at least 1 % faster.
+ * lane) and another layout replaces the default of two for that count only when at least 5 %
+ * faster; then block shapes (warps per block x blocks per SM, capped by occupancy: 4 x 16, 8 x 8,
+ * 2 x 32) and work-item sizes (16, 32, 64 rollouts per lane) are each timed (the best of three
+ * full passes with that per-count layout); the starting shape stays unless another is at least
+ * 2 % faster.
  * win_counts (device int32[sum n]) is scratch.
  * Stops early once `budget_ms` of GPU time is spent (the per-count layouts not reached keep
  * the default).  Counts do not depend on the launch shape.  Synchronous; allocates (sample

@@ -898,8 +898,8 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     float best_ms = INFINITY;
     {
         // 1. competitors per lane, for each competitor count of the batch: a sample of up to 64 of
-        // its races (spread over the batch), one pass per layout, the fastest kept (ties within
-        // 1 % stay with the default of two)
+        // its races (spread over the batch), one pass per layout; another layout replaces the
+        // default of two only when at least 5 % faster
         std::vector<std::vector<int32_t>> by_n(BBE_MAX_COMPETITORS + 1);
         for (int r = 0; r < b->n_races; ++r) by_n[size_t(b->h_off[r + 1] - b->h_off[r])].push_back(r);
         for (int n = 1; n <= BBE_MAX_COMPETITORS && st == BBE_OK && spent < budget_ms; ++n) {
@@ -955,9 +955,10 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
                 if ((st = time_pass(sub, sc, ms))) break;
                 t_v[v] = ms;
             }
+            // another layout replaces the default of two only when clearly faster on the sample
             int vbest = 2;
             for (int v = 1; v <= 4; ++v)
-                if (t_v[v] < t_v[vbest] * 0.99f) vbest = v;
+                if (t_v[v] < t_v[vbest] * (vbest == 2 ? 0.95f : 1.0f)) vbest = v;
             tab[n] = int8_t(vbest);
             cudaFreeAsync(sc, s);
             bbe_destroy_batch(sub);
@@ -965,8 +966,8 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     }
     if (st == BBE_OK) {
         // 2. block shape and work-item size with that layout, each timed on the whole batch (the
-        // better of two passes); the starting shape is the first candidate and stays unless
-        // another is at least 1 % faster
+        // best of three passes); the starting shape is the first candidate and stays unless
+        // another is at least 2 % faster
         std::memcpy(b->slots_by_n, tab, sizeof(tab));
         st = build_items(b);
         bbe_launch_cfg first = start;
@@ -980,12 +981,12 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
             if (i > 0 && spent >= budget_ms) break;
             if ((st = bbe_batch_set_cfg(b, &cands[i]))) break;
             float t = INFINITY;
-            for (int rep = 0; rep < 2 && st == BBE_OK; ++rep) {
+            for (int rep = 0; rep < 3 && st == BBE_OK; ++rep) {
                 if ((st = time_pass(b, win_counts, ms))) break;
                 t = std::min(t, ms);
             }
             if (i == 0) first_ms = t;
-            if (t < best_ms && (i == 0 || t < 0.99f * first_ms)) {
+            if (t < best_ms && (i == 0 || t < 0.98f * first_ms)) {
                 best_ms = t;
                 best = cands[i];
             }
