@@ -1,26 +1,20 @@
-// bbe_rollout.cu -- the Monte Carlo rollout kernel and the win-probability finaliser.
+// bbe_rollout.cu -- the place-count rollout kernel and the probability finalisers.
 //
-// One warp runs the rollouts of one race at a time.  A race of n competitors occupies a
-// segment of ceil(n / V) lanes, each lane holding V consecutive ranks (V = 1, 2 or 4), and a
-// warp packs floor(32 / lanes) segments, each running its own sequence of rollouts of the
-// same race (Section 3 dry-runs).  Warps pull work items (race, rollout range) from a
-// global queue: one persistent launch per V covers races of any size mix.  The race's
-// parameters are staged in shared memory per warp.
+// The place-count kernel (include/bbe.h: bbe_place_counts, bbe_order_counts) runs every rollout
+// of Section 3's dry-runs to the K-th finisher.  One warp runs the rollouts of one race at a
+// time: a race of n competitors occupies a segment of ceil(n / V) lanes, each lane holding V
+// consecutive ranks (V = 1, 2 or 4), and a warp packs floor(32 / lanes) segments, each running
+// its own sequence of rollouts of the same race.  Warps pull work items (race, rollout range)
+// from a global queue; the race's parameters are staged in shared memory per warp.
 //
-// Per step every slot evaluates Eq. 1 for the competitor it holds.  Slots keep the
-// competitors in rank order (ascending position, then index), so the nearest competitor
-// strictly in front (i+) is the next slot: a register (same lane) or one shuffle (next
-// lane).  Finishing is detected with a ballot; the winner (least within-step crossing time,
-// lowest index on ties) comes from the ballot mask, or from a shuffle reduction when several
-// cross in the same step.  Wins are counted per slot in registers (one or two slots per lane)
-// or per warp in shared memory (four), and reach the global counts once per work item.  The
-// hot loop keeps branches few: one per lane for the normal draws (a Philox block at the first
-// step of four, else cached normals), and in win mode the advance by select, with the restart
-// of a finished segment the only branch of the common path's tail.  The same kernel in place mode
-// runs every rollout to the K-th finisher (include/bbe.h: bbe_place_counts): finished
-// competitors keep moving in their rank slots, the finishers of a step are placed by repeated
-// argmin of (crossing time, index), the lane of place j records its competitor, and completed
-// rollouts are tallied in a per-warp [competitor][place] table in shared memory.
+// Per step every slot evaluates Eq. 1 for the competitor it holds.  Slots keep the competitors
+// in rank order (ascending position, then index), so the nearest competitor strictly in front
+// (i+) is the next slot: a register (same lane) or one shuffle (next lane).  Finishing is
+// detected with a ballot; finished competitors keep moving in their rank slots, the finishers
+// of a step are placed by repeated argmin of (crossing time, index), the lane of place j
+// records its competitor, and completed rollouts are tallied in a per-warp [competitor][place]
+// table in shared memory that reaches the global counts once per work item.  (Win counts,
+// K = 1, come from the dedicated kernel in bbe_win.cuh.)
 //
 // The arithmetic is pinned to binary32 round-to-nearest with explicit intrinsics, and this
 // file is compiled with --fmad=false, so the counts are bit-identical to any
@@ -47,7 +41,6 @@ struct WarpStage {
     float kr[32];
     float d0[32], prev0[32];
     int init_c[32];
-    int wins[32];   // win mode with four slots per lane: wins of each competitor in the work item
     float zc[3][128];
 };
 
@@ -96,21 +89,19 @@ __device__ __forceinline__ float draw_z(WarpStage &st, int zi, int c, int t, uin
     return z0;
 }
 
-// MODE 0: win counts (the rollout ends at the first finisher).  MODE 1: place counts (the
-// rollout ends when K = min(places, n) competitors have crossed; competitors past the line keep
-// moving and keep their rank slots; a competitor has finished exactly when its position is at
-// least L, since positions only grow).
+// Place counts: the rollout ends when K = min(places, n) competitors have crossed;
+// competitors past the line keep moving and keep their rank slots (a competitor has finished
+// exactly when its position is at least L, since positions only grow).
 //
-// Launch bounds: the win mode with one or two competitors per lane keeps the compiler's own
-// register choice (64); the place mode, which holds its finishing order in registers, and four
-// competitors per lane may use up to 128 rather than spill (each measured faster on GB300).
-template <int DIST, int V, int MODE>
-__global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kernel(RolloutLaunch l)
+// Launch bounds: the finishing order lives in registers, so the kernel may use up to 128 rather
+// than spill (measured faster on GB300).
+template <int DIST, int V>
+__global__ void __launch_bounds__(512, 1) rollout_kernel(RolloutLaunch l)
 {
     extern __shared__ WarpStage stage_all[];
     WarpStage &st = stage_all[threadIdx.x >> 5];
-    // place mode: a [competitor][place] count table per warp after the stages
-    int *cnt = MODE == 1 ? reinterpret_cast<int *>(stage_all + (blockDim.x >> 5)) + (threadIdx.x >> 5) * 1024 : nullptr;
+    // a [competitor][place] count table per warp after the stages
+    int *cnt = reinterpret_cast<int *>(stage_all + (blockDim.x >> 5)) + (threadIdx.x >> 5) * 1024;
     const DevBatch &b = l.b;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -147,7 +138,6 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
             st.kr[lane] = __fmul_rn(kKappa, __fsub_rn(__fmul_rn(2.0f, b.rho[ci]), 1.0f));
             st.d0[lane] = my_d0;
             st.prev0[lane] = b.prev0 ? b.prev0[ci] : __fmul_rn(mu, P);
-            st.wins[lane] = 0;
         }
         int rank = 0;
         for (int i = 0; i < n; ++i) {
@@ -155,9 +145,8 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
             rank += (di < my_d0 || (di == my_d0 && i < lane)) ? 1 : 0;
         }
         if (lane < n) st.init_c[rank] = lane;
-        const int K = MODE == 1 ? min(l.places, n) : 1;
-        if (MODE == 1)
-            for (int i = lane; i < n * K; i += 32) cnt[i] = 0;
+        const int K = min(l.places, n);
+        for (int i = lane; i < n * K; i += 32) cnt[i] = 0;
         __syncwarp();
 
         const float L = b.L[r];
@@ -169,33 +158,27 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
         bool active = lane_used && k < kend;
         int t = 0;
         unsigned gstep = 0;
-        // Win counting: with one or two slots per lane each slot counts, in registers, the wins
-        // of the competitor that starts every rollout in it (home); with four, whose registers
-        // are scarcer, the segment's first lane adds each winner to the warp's table in shared
-        // memory (measured faster for four, slower for one and two).
-        constexpr bool kSmemWins = V == 4;
-        int home[V], wins[V];
+        int home[V];  // the competitor that starts every rollout in each slot
         Slot s[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             home[v] = valid[v] ? st.init_c[rank0 + v] : 0;
-            wins[v] = 0;
             s[v].c = home[v];
             s[v].d = valid[v] ? st.d0[home[v]] : INFINITY;
             s[v].prev = st.prev0[home[v]];
         }
         long long steps = 0;
         bool hit_limit = false;
-        int placed = 0;      // place mode: competitors placed in the segment's current rollout
-        int my_ord[V];       // place mode: competitor in place ql + m * nl
+        int placed = 0;      // competitors placed in the segment's current rollout
+        int my_ord[V];       // competitor in place ql + m * nl
 #pragma unroll
         for (int m = 0; m < V; ++m) my_ord[m] = 0;
 
-        // place mode: every work item starts with an active segment, and segments change state
-        // only at a finish or a step-limit abort, so the warp checks for remaining work only
-        // after such a step (measured faster there; the win mode keeps the check per step)
-        while (MODE == 1 || __any_sync(kFull, active)) {
-            bool fired = false;  // place mode: a segment finished or was cut off in this step
+        // every work item starts with an active segment, and segments change state only at a
+        // finish or a step-limit abort, so the warp checks for remaining work only after such a
+        // step (measured faster)
+        for (;;) {
+            bool fired = false;  // a segment finished or was cut off in this step
             __syncwarp();  // z-cache writes of earlier steps are visible to every lane
             const bool running = active && t >= 0;
             // i+: the next rank (same lane, or slot 0 of the next lane).  The same shuffles
@@ -329,23 +312,8 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
 #pragma unroll
             for (int v = 0; v < V; ++v) z[v] = 0.0f;
             // one branch per lane for all its slots: a Philox block at the first step of four,
-            // else the cached normals (an invalid slot reads a harmless entry of its segment).
-            // In win mode every rollout starts on the warp's common 4-step phase, so the step
-            // within the Philox block follows the warp's step counter and the branch is one the
-            // whole warp takes (measured faster there, slower in place mode).
-            if constexpr (MODE == 0) {
-                const unsigned phase = gstep & 3u;
-                if (phase == 0u) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if (running && valid[v])
-                            z[v] = draw_z<DIST>(st, zbase + s[v].c, s[v].c, t, uint32_t(k), rid, l.round_key);
-                } else {
-                    const float *zrow = st.zc[phase - 1u] + zbase;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) z[v] = zrow[s[v].c];
-                }
-            } else if (running) {
+            // else the cached normals (an invalid slot reads a harmless entry of its segment)
+            if (running) {
                 if ((t & 3) == 0) {
 #pragma unroll
                     for (int v = 0; v < V; ++v)
@@ -371,14 +339,16 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                 Sv = fmaxf(Sv, kStepFloor);
                 S[v] = Sv;
                 dn[v] = __fadd_rn(s[v].d, Sv);
-                fin[v] = running && valid[v] && !aborted && dn[v] >= L && (MODE == 0 || s[v].d < L);
+                fin[v] = running && valid[v] && !aborted && dn[v] >= L && s[v].d < L;
                 any_fin |= fin[v];
             }
             // finish: least within-step crossing time, ties to the lowest competitor index
             bool seg_fin = false, seg_done = false;
-            if constexpr (MODE == 0) {
-                if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
-                    const unsigned amask = __ballot_sync(kFull, aborted);
+            // place this step's new finishers of each segment, earliest crossing first
+            if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
+                fired = true;
+                const unsigned amask = __ballot_sync(kFull, aborted);
+                for (;;) {
                     unsigned fm[V];
                     int nfin = 0;
 #pragma unroll
@@ -386,8 +356,7 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                         fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
                         nfin += __popc(fm[v]);
                     }
-                    seg_fin = nfin > 0;
-                    seg_done = seg_fin || (amask & segmask) != 0u;
+                    if (!__any_sync(kFull, nfin > 0)) break;
                     int wl = lane, wv = 0;
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -425,145 +394,57 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                         const int cu = __shfl_sync(kFull, s[u].c, wl);
                         cw = wv == u ? cu : cw;
                     }
-                    if constexpr (kSmemWins) {
-                        if (seg_fin && ql == 0) atomicAdd(&st.wins[cw], 1);
-                    } else {
+                    if (nfin > 0) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            if (seg_fin && valid[v] && home[v] == cw) ++wins[v];
-                    }
-                }
-
-            } else {
-                // place this step's new finishers of each segment, earliest crossing first
-                if (__ballot_sync(kFull, any_fin || aborted) != 0u) {
-                    fired = true;
-                    const unsigned amask = __ballot_sync(kFull, aborted);
-                    for (;;) {
-                        unsigned fm[V];
-                        int nfin = 0;
+                        for (int m = 0; m < V; ++m)
+                            if (placed == ql + m * nl) my_ord[m] = cw;
+                        ++placed;
+                        if (lane == wl) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            fm[v] = __ballot_sync(kFull, fin[v]) & segmask;
-                            nfin += __popc(fm[v]);
-                        }
-                        if (!__any_sync(kFull, nfin > 0)) break;
-                        int wl = lane, wv = 0;
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            if (fm[v] != 0u) {
-                                wl = __ffs(fm[v]) - 1;
-                                wv = v;
-                            }
-                        }
-                        if (__any_sync(kFull, nfin > 1)) {
-                            float best = INFINITY;
-                            int bestc = 1 << 30, bl = wl, bv = wv;
-                            for (int j = 0; j < nl; ++j) {
-                                const int src = lane_used ? segbase + j : lane;
-#pragma unroll
-                                for (int u = 0; u < V; ++u) {
-                                    const float tau = fin[u] ? __fdiv_rn(__fsub_rn(L, s[u].d), S[u]) : INFINITY;
-                                    const float tj = __shfl_sync(kFull, tau, src);
-                                    const int cj = __shfl_sync(kFull, s[u].c, src);
-                                    if (tj < best || (tj == best && tj < INFINITY && cj < bestc)) {
-                                        best = tj;
-                                        bestc = cj;
-                                        bl = src;
-                                        bv = u;
-                                    }
-                                }
-                            }
-                            if (nfin > 1) {
-                                wl = bl;
-                                wv = bv;
-                            }
-                        }
-                        int cw = 0;
-#pragma unroll
-                        for (int u = 0; u < V; ++u) {
-                            const int cu = __shfl_sync(kFull, s[u].c, wl);
-                            cw = wv == u ? cu : cw;
-                        }
-                        if (nfin > 0) {
-#pragma unroll
-                            for (int m = 0; m < V; ++m)
-                                if (placed == ql + m * nl) my_ord[m] = cw;
-                            ++placed;
-                            if (lane == wl) {
-#pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                    if (v == wv) fin[v] = false;
-                            }
+                            for (int v = 0; v < V; ++v)
+                                if (v == wv) fin[v] = false;
                         }
                     }
-                    seg_fin = placed >= K;
-                    seg_done = seg_fin || (amask & segmask) != 0u;
                 }
+                seg_fin = placed >= K;
+                seg_done = seg_fin || (amask & segmask) != 0u;
             }
 
             // advance, or start the segment's next rollout
-            if constexpr (MODE == 0) {
-                // win mode: the common case (advance) without branches; a slot that does not
-                // hold a competitor stays at +infinity (its step is floored or infinite)
-                const bool adv = running && !seg_done;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    s[v].d = adv ? dn[v] : s[v].d;
-                    s[v].prev = adv ? S[v] : s[v].prev;
-                }
-                t += (active && !seg_done) ? 1 : 0;
-                if (seg_done) {
-                    steps += seg_fin ? (t + 1) : t;
-                    hit_limit |= !seg_fin;
-                    k += nseg;
-                    active = k < kend;
-                    // every rollout starts on the warp's common 4-step phase
-                    t = -int((4u - ((gstep + 1u) & 3u)) & 3u);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int hc = kSmemWins ? (valid[v] ? st.init_c[rank0 + v] : 0) : home[v];
-                        s[v].c = hc;
-                        s[v].d = valid[v] ? st.d0[hc] : INFINITY;
-                        s[v].prev = st.prev0[hc];
-                    }
-                }
-            } else if (active) {
+            if (active) {
                 if (running) {
                     if (seg_done) {
-                        if constexpr (MODE == 1) {
-                            // one count per place of a completed rollout (a cut-off one counts for nobody)
+                        // one count per place of a completed rollout (a cut-off one counts for nobody)
 #pragma unroll
-                            for (int m = 0; m < V; ++m) {
-                                const int j = ql + m * nl;
-                                if (seg_fin && j < K) atomicAdd(&cnt[my_ord[m] * K + j], 1);
-                            }
-                            if (l.orders != nullptr && seg_fin) {
-                                // the ordered top K as one base-n number, gathered from the lanes
-                                // holding places 0 .. K-1 into the segment's first lane
-                                int code = 0;
-                                for (int j = 0; j < K; ++j) {
-                                    const int mj = j / nl;
-                                    int mine = my_ord[0];
-#pragma unroll
-                                    for (int m = 1; m < V; ++m)
-                                        if (m == mj) mine = my_ord[m];
-                                    code = code * n + __shfl_sync(segmask, mine, segbase + (j - mj * nl));
-                                }
-                                if (ql == 0) atomicAdd(&l.orders[l.order_off[r] + code], 1);
-                            }
-                            placed = 0;
+                        for (int m = 0; m < V; ++m) {
+                            const int j = ql + m * nl;
+                            if (seg_fin && j < K) atomicAdd(&cnt[my_ord[m] * K + j], 1);
                         }
+                        if (l.orders != nullptr && seg_fin) {
+                            // the ordered top K as one base-n number, gathered from the lanes
+                            // holding places 0 .. K-1 into the segment's first lane
+                            int code = 0;
+                            for (int j = 0; j < K; ++j) {
+                                const int mj = j / nl;
+                                int mine = my_ord[0];
+#pragma unroll
+                                for (int m = 1; m < V; ++m)
+                                    if (m == mj) mine = my_ord[m];
+                                code = code * n + __shfl_sync(segmask, mine, segbase + (j - mj * nl));
+                            }
+                            if (ql == 0) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                        }
+                        placed = 0;
                         steps += seg_fin ? (t + 1) : t;
                         hit_limit |= !seg_fin;
                         k += nseg;
                         active = k < kend;
-                        // packed segments (in win mode, all) start rollouts on a common 4-step
-                        // phase so the warp draws its Philox blocks together
-                        t = (MODE == 0 || nseg > 1) ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
+                        // packed segments start rollouts on a common 4-step phase so the
+                        // warp draws its Philox blocks together
+                        t = nseg > 1 ? -int((4u - ((gstep + 1u) & 3u)) & 3u) : 0;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            const int hc = kSmemWins ? (valid[v] ? st.init_c[rank0 + v] : 0) : home[v];
+                            const int hc = home[v];
                             s[v].c = hc;
                             s[v].d = valid[v] ? st.d0[hc] : INFINITY;
                             s[v].prev = st.prev0[hc];
@@ -583,31 +464,13 @@ __global__ void __launch_bounds__(512, MODE == 1 || V == 4 ? 1 : 0) rollout_kern
                 }
             }
             ++gstep;
-            if constexpr (MODE == 1) {
-                if (fired && !__any_sync(kFull, active)) break;
-            }
+            if (fired && !__any_sync(kFull, active)) break;
         }
-        if constexpr (MODE == 0) {
-            if constexpr (kSmemWins) {
-                // one flush of the work item's win table
-                __syncwarp();
-                if (lane < n && st.wins[lane] != 0) atomicAdd(&l.counts[off + lane], st.wins[lane]);
-            } else {
-                // one reduction per work item: wins of each home competitor summed over segments
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    int total = 0;
-                    for (int s2 = 0; s2 < nseg; ++s2) total += __shfl_sync(kFull, wins[v], s2 * nl + (lane_used ? ql : 0));
-                    if (seg == 0 && valid[v] && total != 0) atomicAdd(&l.counts[off + home[v]], total);
-                }
-            }
-        } else {
-            // one flush of the place table per work item
-            __syncwarp();
-            for (int i = lane; i < n * K && l.counts != nullptr; i += 32) {
-                const int c = cnt[i];
-                if (c != 0) atomicAdd(&l.counts[(off + i / K) * l.places + i % K], c);
-            }
+        // one flush of the place table per work item
+        __syncwarp();
+        for (int i = lane; i < n * K && l.counts != nullptr; i += 32) {
+            const int c = cnt[i];
+            if (c != 0) atomicAdd(&l.counts[(off + i / K) * l.places + i % K], c);
         }
         unsigned long long stp = (lane_used && ql == 0) ? (unsigned long long)steps : 0ull;
         for (int o = 16; o > 0; o >>= 1) stp += __shfl_xor_sync(kFull, stp, o);
@@ -638,39 +501,36 @@ __global__ void place_probs_kernel(DevBatch b, int places, const int32_t *__rest
     probs[i] = __fdiv_rn(__ll2float_rn(s), __ll2float_rn(b.R[b.comp_race[i]]));
 }
 
-template <int MODE>
-size_t stage_bytes(int block)
-{
-    return size_t(block / 32) * (sizeof(WarpStage) + (MODE == 1 ? 1024 * sizeof(int) : 0));
-}
+// per warp: its stage and its [competitor][place] count table
+size_t stage_bytes(int block) { return size_t(block / 32) * (sizeof(WarpStage) + 1024 * sizeof(int)); }
 
-template <int V, int MODE>
+template <int V>
 cudaError_t launch_v(const RolloutLaunch &l, cudaStream_t stream)
 {
-    const size_t smem = stage_bytes<MODE>(l.block);
+    const size_t smem = stage_bytes(l.block);
     switch (l.b.dist) {
-    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
-    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
-    default: rollout_kernel<BBE_DIST_TWO_POINT, V, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_NORMAL: rollout_kernel<BBE_DIST_NORMAL, V><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_UNIFORM: rollout_kernel<BBE_DIST_UNIFORM, V><<<l.grid, l.block, smem, stream>>>(l); break;
+    default: rollout_kernel<BBE_DIST_TWO_POINT, V><<<l.grid, l.block, smem, stream>>>(l); break;
     }
     return cudaGetLastError();
 }
 
-template <int V, int MODE>
+template <int V>
 int resident_v(int dist, int block)
 {
-    const size_t smem = stage_bytes<MODE>(block);
+    const size_t smem = stage_bytes(block);
     int nb = 0;
     cudaError_t e;
     switch (dist) {
     case BBE_DIST_NORMAL:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL, V, MODE>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_NORMAL, V>, block, smem);
         break;
     case BBE_DIST_UNIFORM:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM, V, MODE>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_UNIFORM, V>, block, smem);
         break;
     default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT, V, MODE>, block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_kernel<BBE_DIST_TWO_POINT, V>, block, smem);
         break;
     }
     return e == cudaSuccess ? nb : 1;
@@ -681,20 +541,20 @@ int resident_v(int dist, int block)
 cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
     switch (slots_per_lane) {
-    case 4: return launch_v<4, 1>(l, stream);
+    case 4: return launch_v<4>(l, stream);
     case 3:
-    case 2: return launch_v<2, 1>(l, stream);
-    default: return launch_v<1, 1>(l, stream);
+    case 2: return launch_v<2>(l, stream);
+    default: return launch_v<1>(l, stream);
     }
 }
 
 int place_resident_blocks(int dist, int slots_per_lane, int block)
 {
     switch (slots_per_lane) {
-    case 4: return resident_v<4, 1>(dist, block);
+    case 4: return resident_v<4>(dist, block);
     case 3:
-    case 2: return resident_v<2, 1>(dist, block);
-    default: return resident_v<1, 1>(dist, block);
+    case 2: return resident_v<2>(dist, block);
+    default: return resident_v<1>(dist, block);
     }
 }
 
