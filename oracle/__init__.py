@@ -14,6 +14,7 @@ import ctypes as C
 import os
 import subprocess
 import threading
+from collections import Counter
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -83,6 +84,8 @@ def lib():
             L.bbe_oracle_race_places.restype = C.c_int
             L.bbe_oracle_race_orders.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
             L.bbe_oracle_race_orders.restype = C.c_int
+            L.bbe_oracle_race_order_list.argtypes = [C.POINTER(_Race), u64, u32, i64, i64, C.c_int, i64, vp, vp]
+            L.bbe_oracle_race_order_list.restype = C.c_int
             L.bbe_oracle_trajectory.argtypes = [C.POINTER(_Race), u64, u32, u32, i64, vp, vp, vp, i64]
             L.bbe_oracle_trajectory.restype = C.c_int
             L.bbe_oracle_preference.argtypes = [C.c_int, vp, C.c_int, vp, vp, vp, vp]
@@ -211,6 +214,42 @@ def race_orders(race: dict, seed: int, places: int, r: int | None = None, R: int
     steps = np.zeros(1, np.int64)
     st = lib().bbe_oracle_race_orders(C.byref(a.s), seed, r, k_begin, R, places, max_steps, _ptr(counts), _ptr(steps))
     return counts, int(steps[0]), int(st)
+
+
+def race_order_histogram(race: dict, seed: int, places: int, r: int | None = None, R: int | None = None,
+                         k_begin: int = 0, max_steps: int = MAX_STEPS_DEFAULT):
+    """Distribution of finishing orders of one race (Section 3): a Counter from each ordered
+    tuple of the first kk = min(places, n) finishers to the number of rollouts that ended in it
+    (cut-off rollouts count for nobody), the steps total and the status."""
+    a = _RaceArgs(race)
+    r = race["race_id"] if r is None else r
+    R = race["R"] if R is None else R
+    kk = min(places, race["n"])
+    orders = np.empty((R, kk), np.int32)
+    steps = np.zeros(1, np.int64)
+    st = lib().bbe_oracle_race_order_list(C.byref(a.s), seed, r, k_begin, R, places, max_steps, _ptr(orders),
+                                          _ptr(steps))
+    hist = Counter(tuple(int(c) for c in row) for row in orders if row[0] >= 0)
+    return hist, int(steps[0]), int(st)
+
+
+def batch_order_histograms(batch, places: int, races=None, threads: int | None = None,
+                           max_steps: int = MAX_STEPS_DEFAULT):
+    """race_order_histogram for the given races of a RaceBatch (a thread pool over races):
+    (list of Counters in the order given, steps int64 [len(races)], status)."""
+    races = list(range(batch.n_races)) if races is None else [int(x) for x in races]
+    threads = threads or os.cpu_count() or 1
+
+    def one(r):
+        return race_order_histogram(batch.race(r), batch.seed, places, max_steps=max_steps)
+
+    if threads <= 1 or len(races) <= 1:
+        res = [one(r) for r in races]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(one, races))
+    status = next((st for _, _, st in res if st != 0), 0)
+    return [h for h, _, _ in res], np.array([s for _, s, _ in res], np.int64), status
 
 
 def batch_orders(batch, places: int, races=None, threads: int | None = None, max_steps: int = MAX_STEPS_DEFAULT,

@@ -438,6 +438,31 @@ int bbe_oracle_race_orders(const bbe_oracle_race *race, uint64_t seed, uint32_t 
     return status;
 }
 
+/* The finishing order of each of rollouts k_begin .. k_begin + R - 1 of race r, run to the
+ * kk-th finisher, kk = min(places, n) (Section 3: the dry-runs give the distribution of
+ * outcomes): orders[i * kk + j] = the competitor in place j of rollout k_begin + i, or -1 in
+ * the whole row of a rollout cut off at max_steps.  The histogram of the rows is the order
+ * distribution.  Returns 0, or BBE_ORACLE_STEP_LIMIT if some rollout was cut off. */
+int bbe_oracle_race_order_list(const bbe_oracle_race *race, uint64_t seed, uint32_t r, int64_t k_begin, int64_t R,
+                               int places, int64_t max_steps, int32_t *orders, int64_t *steps_total)
+{
+    int n = race->n;
+    int kk = places < n ? places : n;
+    int status = 0;
+    int64_t total = 0;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t i = 0; i < R; ++i) {
+        int64_t steps = 0;
+        int st = bbe_oracle_rollout_order(race, seed, r, (uint32_t)(k_begin + i), kk, max_steps, &steps, order);
+        total += steps;
+        if (st != 0) status = st;
+        for (int j = 0; j < kk; ++j) orders[i * kk + j] = st != 0 ? -1 : order[j];
+    }
+    if (steps_total) *steps_total = total;
+    free(order);
+    return status;
+}
+
 /* One full run of race r (rollout k of its stream): every competitor moves under Eq. 1 until
  * the last one has crossed the line (Section 3) or max_steps steps pass; the space-time series
  * of the race (Section 6 plots one).  For t < min(steps, cap): d_traj[t * n + c] = d_c after

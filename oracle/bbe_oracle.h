@@ -53,6 +53,8 @@ int bbe_oracle_race_places(const bbe_oracle_race *race, uint64_t seed, uint32_t 
 int bbe_oracle_race_orders(const bbe_oracle_race *race, uint64_t seed, uint32_t r,
                            int64_t k_begin, int64_t R, int places, int64_t max_steps,
                            int32_t *counts, int64_t *steps_total);
+int bbe_oracle_race_order_list(const bbe_oracle_race *race, uint64_t seed, uint32_t r, int64_t k_begin, int64_t R,
+                               int places, int64_t max_steps, int32_t *orders, int64_t *steps_total);
 int bbe_oracle_trajectory(const bbe_oracle_race *race, uint64_t seed, uint32_t r, uint32_t k, int64_t max_steps,
                           int64_t *steps, float *d_traj, float *s_traj, int64_t cap);
 void bbe_oracle_preference(int n_races, const int32_t *race_off, int F, const float *factors, const float *prefs,
