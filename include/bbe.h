@@ -192,6 +192,49 @@ BBE_API bbe_status bbe_order_counts(bbe_batch *batch, int32_t places, int32_t *o
  * Errors: BBE_ERR_ARG. */
 BBE_API bbe_status bbe_order_table_size(const bbe_batch *batch, int32_t places, int64_t *entries);
 
+/* bbe_order_histogram -- the distribution of finishing orders as a histogram (Section 3: the
+ * dry-runs estimate the distribution of outcomes; a race's full outcome is the order of all n_r
+ * finishers, one of n_r! permutations, so no dense table holds it).  The rollouts are
+ * bbe_place_counts's (same stream, same readings), run to the K_r-th finisher with
+ * K_r = min(places, n_r) (places >= n_r: the full order); each completed rollout adds one to
+ * the count of its order key in race r's hash table.
+ * Order key of the ordered tuple (o_0, .., o_{K-1}) of a race of n: the mixed-radix number
+ * with digits a_0 .. a_{K-1}, a_j in 0 .. n-j-1 (radix n - j) and a_0 the most significant,
+ * where a_j counts the competitors of lower index than o_j that are not among o_0 .. o_{j-1};
+ * keys run over 0 .. n!/(n-K)! - 1 (bbe_order_key_encode / _decode convert).  Every race needs
+ * n_r!/(n_r-K_r)! <= 2^64 - 1: the full order for n_r <= 20, the first 16 places of 24, the
+ * first 13 of 32.
+ *   places       1 .. BBE_MAX_COMPETITORS.
+ *   keys         device uint64[entries of bbe_order_histogram_layout], overwritten: race r's
+ *                table is entries table_off[r] .. table_off[r+1]-1; an unused entry holds
+ *                2^64 - 1 (UINT64_MAX) and count 0.
+ *   counts       device int32[entries], overwritten: the rollouts that ended in that order.
+ *   place_counts nullable device int32[sum n * places]: bbe_place_counts's table, same pass.
+ *   steps_total  nullable device int64[n_races].
+ * Which entry holds a key depends on the timing of the rollouts; the set of (key, count) pairs
+ * of each race does not, and is bit-identical to the tally of the oracle's dry-runs.  A race's
+ * table holds a power of two of entries, at least twice min(R_r, n_r!/(n_r-K_r)!), so a free
+ * entry is always found (were none found, the batch status would report BBE_ERR_RANGE).
+ * Asynchronous on cuda_stream (a call with a new `places` uploads the layout first).  Cut-off
+ * rollouts count for nobody and set BBE_ERR_STEP_LIMIT.  Position-law batches only.  Errors:
+ * BBE_ERR_ARG, BBE_ERR_RANGE (a race whose keys exceed 64 bits, named in bbe_last_error),
+ * BBE_ERR_UNSUPPORTED (time-law batch), BBE_ERR_CUDA. */
+BBE_API bbe_status bbe_order_histogram(bbe_batch *batch, int32_t places, uint64_t *keys, int32_t *counts,
+                                       int32_t *place_counts, int64_t *steps_total, void *cuda_stream);
+
+/* bbe_order_histogram_layout -- the hash-table layout bbe_order_histogram uses for `places`
+ * (host; no GPU work): table_off (nullable host int64[n_races + 1]) gets each race's first entry
+ * and the total, entries (nullable) the total.  Errors: BBE_ERR_ARG, BBE_ERR_RANGE (as above). */
+BBE_API bbe_status bbe_order_histogram_layout(const bbe_batch *batch, int32_t places, int64_t *table_off,
+                                              int64_t *entries);
+
+/* bbe_order_key_encode / bbe_order_key_decode -- between an ordered tuple order[0 .. K-1]
+ * (K = min(places, n), distinct competitors in 0 .. n-1; host int32) and its order key (see
+ * bbe_order_histogram).  Host only.  Errors: BBE_ERR_ARG (a repeated or out-of-range
+ * competitor, a key >= n!/(n-K)!, or n!/(n-K)! > 2^64 - 1). */
+BBE_API bbe_status bbe_order_key_encode(int32_t n, int32_t places, const int32_t *order, uint64_t *key);
+BBE_API bbe_status bbe_order_key_decode(int32_t n, int32_t places, uint64_t key, int32_t *order);
+
 /* bbe_place_probs -- probability of finishing in the first `top` places (a place market
  * paying on the first `top` places; top = 1 is the win probability):
  *   probs[i] = (sum over j < top of place_counts[i * places + j]) / R_r.
@@ -295,15 +338,18 @@ BBE_API bbe_status bbe_batch_get_cfg(const bbe_batch *batch, bbe_launch_cfg *cfg
 /* bbe_batch_autotune -- pick this batch's launch by timing it (the batching workload asks for
  * block shapes and rollouts per warp chosen by measurement).  First, for each competitor count
  * present, a sample of up to 64 of its races is run once per layout (1 to 4 competitors per
- * lane) and another layout replaces the default of two for that count only when at least 5 %
- * faster; then block shapes (warps per block x blocks per SM, capped by occupancy: 4 x 16, 8 x 8,
- * 2 x 32) and work-item sizes (16, 32, 64 rollouts per lane) are each timed (the best of three
- * full passes with that per-count layout); the starting shape stays unless another is at least
- * 2 % faster.
+ * lane) and another layout becomes that count's candidate only when at least 5 % faster on the
+ * sample.  Second, the whole batch is timed (the best of three passes) with the candidate
+ * per-count layout and with the starting one; every distinct layout is a launch of its own, so
+ * the candidate is kept only if the whole batch runs at least 2 % faster with it.  Third, block
+ * shapes (warps per block x blocks per SM, capped by occupancy: 4 x 16, 8 x 8, 2 x 32) and
+ * work-item sizes (16, 32, 64 rollouts per lane) are each timed the same way; the starting shape
+ * stays unless another is at least 2 % faster.
  * win_counts (device int32[sum n]) is scratch.
- * Stops early once `budget_ms` of GPU time is spent (the per-count layouts not reached keep
- * the default).  Counts do not depend on the launch shape.  Synchronous; allocates (sample
- * batches).  Errors: BBE_ERR_ARG, BBE_ERR_CUDA (the batch keeps its previous launch). */
+ * Once `budget_ms` of GPU time is spent the per-count samples not reached keep the default and
+ * no further shape is tried (the whole-batch layout check always runs).  Counts do not depend
+ * on the launch.  Synchronous; allocates (sample batches).  Errors: BBE_ERR_ARG, BBE_ERR_CUDA
+ * (the batch keeps its previous launch). */
 BBE_API bbe_status bbe_batch_autotune(bbe_batch *batch, int32_t *win_counts, double budget_ms, void *cuda_stream);
 
 /* bbe_batch_layout -- competitors per lane used for a race of n competitors, n = 1..32, into

@@ -56,6 +56,10 @@ def lib():
             "bbe_place_counts": [vp, C.c_int32, vp, vp, vp],
             "bbe_order_counts": [vp, C.c_int32, vp, vp, vp, vp],
             "bbe_order_table_size": [vp, C.c_int32, C.POINTER(C.c_int64)],
+            "bbe_order_histogram": [vp, i32, vp, vp, vp, vp, vp],
+            "bbe_order_histogram_layout": [vp, i32, vp, vp],
+            "bbe_order_key_encode": [i32, i32, vp, vp],
+            "bbe_order_key_decode": [i32, i32, u64, vp],
             "bbe_race_trajectory": [vp, C.c_uint32, C.c_int32, vp, vp, vp, vp],
             "bbe_preference_coefficients": [C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp],
             "bbe_snapshot_batch": [C.POINTER(vp), vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32,
@@ -155,6 +159,33 @@ def bbe_place_counts(batch: int, places: int, place_counts, steps_total=None, st
 def bbe_order_counts(batch: int, places: int, order_counts, place_counts=None, steps_total=None, stream=None) -> None:
     _check(lib().bbe_order_counts(batch, int(places), _ptr(order_counts, np.int32), _ptr(place_counts, np.int32),
                                   _ptr(steps_total, np.int64), _stream(stream)), "bbe_order_counts")
+
+
+def bbe_order_histogram(batch: int, places: int, keys, counts, place_counts=None, steps_total=None,
+                        stream=None) -> None:
+    _check(lib().bbe_order_histogram(batch, int(places), _ptr(keys, np.uint64), _ptr(counts, np.int32),
+                                     _ptr(place_counts, np.int32), _ptr(steps_total, np.int64), _stream(stream)),
+           "bbe_order_histogram")
+
+
+def bbe_order_histogram_layout(batch: int, places: int, n_races: int) -> np.ndarray:
+    """Each race's first hash-table entry and the total: int64 [n_races + 1]."""
+    off = np.zeros(n_races + 1, np.int64)
+    _check(lib().bbe_order_histogram_layout(batch, int(places), _ptr(off), None), "bbe_order_histogram_layout")
+    return off
+
+
+def bbe_order_key_encode(n: int, places: int, order) -> int:
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    out = C.c_uint64(0)
+    _check(lib().bbe_order_key_encode(int(n), int(places), _ptr(o), C.byref(out)), "bbe_order_key_encode")
+    return int(out.value)
+
+
+def bbe_order_key_decode(n: int, places: int, key: int) -> np.ndarray:
+    out = np.empty(min(int(places), int(n)), np.int32)
+    _check(lib().bbe_order_key_decode(int(n), int(places), int(key), _ptr(out)), "bbe_order_key_decode")
+    return out
 
 
 def bbe_order_table_size(batch: int, places: int) -> int:
@@ -341,6 +372,21 @@ class Batch:
         steps = torch.empty(self.rb.n_races, dtype=torch.int64, device="cuda")
         bbe_order_counts(self.handle, places, counts, pc, steps, stream)
         return counts[:total], pc, steps
+
+    def order_histogram(self, places: int, with_places: bool = False, stream=None):
+        """Finishing-order hash tables (device uint64 keys and int32 counts; race r's table is
+        entries off[r] .. off[r+1]-1, unused entries hold key 2^64 - 1 and count 0), the layout
+        off (host int64), optionally the place counts of the same pass, and steps per race."""
+        import torch
+
+        off = bbe_order_histogram_layout(self.handle, places, self.rb.n_races)
+        total = int(off[-1])
+        keys = torch.empty(total, dtype=torch.uint64, device="cuda")
+        counts = torch.empty(total, dtype=torch.int32, device="cuda")
+        pc = torch.empty((self.rb.n_total, places), dtype=torch.int32, device="cuda") if with_places else None
+        steps = torch.empty(self.rb.n_races, dtype=torch.int64, device="cuda")
+        bbe_order_histogram(self.handle, places, keys, counts, pc, steps, stream)
+        return keys, counts, off, pc, steps
 
     def place_probs(self, counts, top: int, probs=None, stream=None):
         import torch

@@ -597,7 +597,8 @@ namespace {
 // The rollout kernel in place mode over the whole batch: place table (nullable) and, with
 // `orders`, the ordered top-`places` tallies at b->d_order_off.
 bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, int32_t *orders,
-                          int64_t *steps_total, cudaStream_t s)
+                          int64_t *steps_total, cudaStream_t s, unsigned long long *hist_keys = nullptr,
+                          int32_t *hist_counts = nullptr)
 {
     if (b->dev.law != BBE_LAW_POSITION) {
         set_error("place and order tallies take position-law batches only");
@@ -614,6 +615,9 @@ bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, i
         l.places = places;
         l.orders = orders;
         l.order_off = orders ? b->d_order_off : nullptr;
+        l.hist_keys = hist_keys;
+        l.hist_counts = hist_counts;
+        l.hist_off = hist_keys ? b->d_hist_off : nullptr;
         const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block);
         l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
         BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
@@ -632,6 +636,40 @@ void order_layout(const bbe_batch *b, int32_t places, std::vector<int64_t> &off)
         for (int j = 0; j < std::min(places, n); ++j) cells *= n;
         off[size_t(r) + 1] = off[size_t(r)] + cells;
     }
+}
+// Number of ordered tuples of K distinct competitors out of n, n! / (n - K)!, or 0 when it
+// exceeds 2^64 - 1 (the order keys would not fit in 64 bits beside the empty marker).
+uint64_t ordered_tuples(int n, int K)
+{
+    uint64_t f = 1;
+    for (int j = 0; j < K; ++j) {
+        const uint64_t m = uint64_t(n - j);
+        if (f > (~0ull) / m) return 0;
+        f *= m;
+    }
+    return f;
+}
+
+// per-race hash tables of the finishing-order histogram for `places`: the least power of two
+// at least twice the most distinct orders the race can show, min(R_r, n_r! / (n_r - K_r)!), and
+// at least 2; false (with the error set) for a race whose order keys do not fit in 64 bits
+bool hist_layout(const bbe_batch *b, int32_t places, std::vector<int64_t> &off)
+{
+    off.assign(size_t(b->n_races) + 1, 0);
+    for (int r = 0; r < b->n_races; ++r) {
+        const int n = b->h_off[r + 1] - b->h_off[r];
+        const uint64_t f = ordered_tuples(n, std::min(places, n));
+        if (f == 0) {
+            set_error("race " + std::to_string(r) + ": the orders of its first " + std::to_string(std::min(places, n)) +
+                      " of " + std::to_string(n) + " competitors exceed 2^64 - 1 keys; ask for fewer places");
+            return false;
+        }
+        const uint64_t most = std::min<uint64_t>(f, uint64_t(b->h_R[r]));
+        int64_t cap = 2;
+        while (uint64_t(cap) < 2 * most) cap *= 2;
+        off[size_t(r) + 1] = off[size_t(r)] + cap;
+    }
+    return true;
 }
 }  // namespace
 
@@ -681,6 +719,101 @@ bbe_status bbe_order_counts(bbe_batch *b, int32_t places, int32_t *order_counts,
     }
     BBE_CUDA_TRY(cudaMemsetAsync(order_counts, 0, size_t(b->h_order_off.back()) * sizeof(int32_t), s));
     return run_place_mode(b, places, place_counts, order_counts, steps_total, s);
+}
+
+bbe_status bbe_order_histogram_layout(const bbe_batch *b, int32_t places, int64_t *table_off, int64_t *entries)
+{
+    if (!b || places < 1 || places > BBE_MAX_COMPETITORS) {
+        set_error("bbe_order_histogram_layout: batch is NULL, or places outside 1..BBE_MAX_COMPETITORS");
+        return BBE_ERR_ARG;
+    }
+    std::vector<int64_t> off;
+    if (!hist_layout(b, places, off)) return BBE_ERR_RANGE;
+    if (table_off) std::copy(off.begin(), off.end(), table_off);
+    if (entries) *entries = off.back();
+    return BBE_OK;
+}
+
+bbe_status bbe_order_histogram(bbe_batch *b, int32_t places, uint64_t *keys, int32_t *counts, int32_t *place_counts,
+                               int64_t *steps_total, void *cuda_stream)
+{
+    cudaStream_t s = as_stream(cuda_stream);
+    if (!b || !keys || !counts || places < 1 || places > BBE_MAX_COMPETITORS) {
+        set_error("bbe_order_histogram: batch, keys or counts is NULL, or places outside 1..BBE_MAX_COMPETITORS");
+        return BBE_ERR_ARG;
+    }
+    if (b->hist_places != places || !b->d_hist_off) {
+        std::vector<int64_t> off;
+        if (!hist_layout(b, places, off)) return BBE_ERR_RANGE;
+        BBE_CUDA_TRY(free_behind_uses(b, b->d_hist_off));
+        b->d_hist_off = nullptr;
+        b->hist_places = 0;
+        BBE_CUDA_TRY(cudaMallocAsync(&b->d_hist_off, off.size() * sizeof(int64_t), s));
+        BBE_CUDA_TRY(cudaMemcpyAsync(b->d_hist_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        BBE_CUDA_TRY(cudaStreamSynchronize(s));  // `off` is pageable and goes out of scope
+        b->h_hist_off = std::move(off);
+        b->hist_places = places;
+    }
+    const size_t entries = size_t(b->h_hist_off.back());
+    BBE_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, entries * sizeof(uint64_t), s));
+    BBE_CUDA_TRY(cudaMemsetAsync(counts, 0, entries * sizeof(int32_t), s));
+    return run_place_mode(b, places, place_counts, nullptr, steps_total, s,
+                          reinterpret_cast<unsigned long long *>(keys), counts);
+}
+
+bbe_status bbe_order_key_encode(int32_t n, int32_t places, const int32_t *order, uint64_t *key)
+{
+    const int K = std::min(places, n);
+    if (!order || !key || n < 1 || n > BBE_MAX_COMPETITORS || places < 1 || ordered_tuples(n, K) == 0) {
+        set_error("bbe_order_key_encode: order or key is NULL, n outside 1..BBE_MAX_COMPETITORS, places < 1, or the "
+                  "orders exceed 2^64 - 1 keys");
+        return BBE_ERR_ARG;
+    }
+    uint32_t taken = 0;
+    uint64_t k = 0;
+    for (int j = 0; j < K; ++j) {
+        const int c = order[j];
+        if (c < 0 || c >= n || (taken >> c) & 1u) {
+            set_error("bbe_order_key_encode: order holds a competitor outside 0..n-1 or the same competitor twice");
+            return BBE_ERR_ARG;
+        }
+        int below = 0;  // competitors with a lower index not yet placed
+        for (int i = 0; i < c; ++i) below += ((taken >> i) & 1u) ? 0 : 1;
+        k = k * uint64_t(n - j) + uint64_t(below);
+        taken |= 1u << c;
+    }
+    *key = k;
+    return BBE_OK;
+}
+
+bbe_status bbe_order_key_decode(int32_t n, int32_t places, uint64_t key, int32_t *order)
+{
+    const int K = std::min(places, n);
+    const uint64_t f = (n >= 1 && n <= BBE_MAX_COMPETITORS && places >= 1) ? ordered_tuples(n, K) : 0;
+    if (!order || f == 0 || key >= f) {
+        set_error("bbe_order_key_decode: order is NULL, n outside 1..BBE_MAX_COMPETITORS, places < 1, or key outside "
+                  "0 .. n!/(n-K)! - 1");
+        return BBE_ERR_ARG;
+    }
+    // the digits from the last (radix n - K + 1) to the first (radix n)
+    int digit[BBE_MAX_COMPETITORS];
+    for (int j = K - 1; j >= 0; --j) {
+        const uint64_t radix = uint64_t(n - j);
+        digit[j] = int(key % radix);
+        key /= radix;
+    }
+    uint32_t taken = 0;
+    for (int j = 0; j < K; ++j) {
+        int c = 0, seen = 0;  // the digit[j]-th (from 0) competitor not yet placed
+        for (;; ++c) {
+            if ((taken >> c) & 1u) continue;
+            if (seen == digit[j]) break;
+            ++seen;
+        }
+        order[j] = c;
+        taken |= 1u << c;
+    }
+    return BBE_OK;
 }
 
 namespace {
@@ -796,6 +929,10 @@ bbe_status bbe_batch_status(bbe_batch *b, void *cuda_stream)
     int32_t flags = 0;
     BBE_CUDA_TRY(cudaMemcpyAsync(&flags, b->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags & bbe::kStatusTableFull) {
+        set_error("a finishing-order hash table had no free entry");
+        return BBE_ERR_RANGE;
+    }
     if (flags & bbe::kStatusStepLimit) {
         set_error("a rollout reached max_steps without a finisher");
         return BBE_ERR_STEP_LIMIT;
@@ -895,7 +1032,7 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
     int8_t tab[BBE_MAX_COMPETITORS + 1] = {};
     bbe_launch_cfg best = start;
     best.slots_per_lane = 0;
-    float best_ms = INFINITY;
+    float best_ms = INFINITY;  // of `best`, the best of three whole-batch passes
     {
         // 1. competitors per lane, for each competitor count of the batch: a sample of up to 64 of
         // its races (spread over the batch), one pass per layout; another layout replaces the
@@ -964,29 +1101,52 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
             bbe_destroy_batch(sub);
         }
     }
+    // the best of three whole-batch passes with the batch's current layout and shape
+    auto best_of_three = [&](float &t) -> bbe_status {
+        t = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            const bbe_status e = time_pass(b, win_counts, ms);
+            if (e) return e;
+            t = std::min(t, ms);
+        }
+        return BBE_OK;
+    };
+    bbe_launch_cfg first = start;
+    first.slots_per_lane = 0;
+    float first_ms = INFINITY;
     if (st == BBE_OK) {
-        // 2. block shape and work-item size with that layout, each timed on the whole batch (the
-        // best of three passes); the starting shape is the first candidate and stays unless
-        // another is at least 2 % faster
-        std::memcpy(b->slots_by_n, tab, sizeof(tab));
-        st = build_items(b);
-        bbe_launch_cfg first = start;
-        first.slots_per_lane = 0;
-        const bbe_launch_cfg cands[] = {first,
-                                        {4, 16, 32, start.max_steps, 0}, {8, 8, 32, start.max_steps, 0},
+        // 2. the per-count layout against the starting one on the whole batch: each layout group
+        // is a launch of its own with its own tail, which the per-count samples do not see, so
+        // the new table stays only if the whole batch runs at least 2 % faster with it
+        st = bbe_batch_set_cfg(b, &first);
+        if (st == BBE_OK) st = build_items(b);
+        if (st == BBE_OK) st = best_of_three(first_ms);
+        if (st == BBE_OK && std::memcmp(tab, start_tab, sizeof(tab)) != 0) {
+            std::memcpy(b->slots_by_n, tab, sizeof(tab));
+            float t_tab = INFINITY;
+            if ((st = build_items(b)) == BBE_OK && (st = best_of_three(t_tab)) == BBE_OK) {
+                if (t_tab < 0.98f * first_ms) {
+                    first_ms = t_tab;
+                } else {
+                    std::memcpy(b->slots_by_n, start_tab, sizeof(start_tab));
+                    st = build_items(b);
+                }
+            }
+        }
+    }
+    if (st == BBE_OK) {
+        // 3. block shape and work-item size with that layout, each timed on the whole batch (the
+        // best of three passes); the starting shape stays unless another is at least 2 % faster
+        best_ms = first_ms;
+        const bbe_launch_cfg cands[] = {{4, 16, 32, start.max_steps, 0}, {8, 8, 32, start.max_steps, 0},
                                         {2, 32, 32, start.max_steps, 0}, {4, 16, 16, start.max_steps, 0},
                                         {4, 16, 64, start.max_steps, 0}, {8, 8, 16, start.max_steps, 0}};
-        float first_ms = INFINITY;
-        for (size_t i = 0; i < sizeof(cands) / sizeof(cands[0]) && st == BBE_OK; ++i) {
-            if (i > 0 && spent >= budget_ms) break;
+        for (size_t i = 0; i < sizeof(cands) / sizeof(cands[0]) && st == BBE_OK && spent < budget_ms; ++i) {
+            if (std::memcmp(&cands[i], &first, sizeof(first)) == 0) continue;
             if ((st = bbe_batch_set_cfg(b, &cands[i]))) break;
             float t = INFINITY;
-            for (int rep = 0; rep < 3 && st == BBE_OK; ++rep) {
-                if ((st = time_pass(b, win_counts, ms))) break;
-                t = std::min(t, ms);
-            }
-            if (i == 0) first_ms = t;
-            if (t < best_ms && (i == 0 || t < 0.98f * first_ms)) {
+            if ((st = best_of_three(t))) break;
+            if (t < best_ms && t < 0.98f * first_ms) {
                 best_ms = t;
                 best = cands[i];
             }
@@ -1038,7 +1198,8 @@ void bbe_destroy_batch(bbe_batch *b)
     // for nothing and no other stream is held up.  Streams and events still in use are released
     // by CUDA when their work completes.
     free_graph(b);
-    for (void *p : {static_cast<void *>(b->d_items), static_cast<void *>(b->d_order_off), b->arena, b->law_mem}) {
+    for (void *p : {static_cast<void *>(b->d_items), static_cast<void *>(b->d_order_off), static_cast<void *>(b->d_hist_off), b->arena,
+                    b->law_mem}) {
         if (p && free_behind_uses(b, p) != cudaSuccess) {
             // no free stream could be made: wait for this batch's uses on the host instead
             cudaGetLastError();

@@ -66,7 +66,13 @@ struct RolloutLaunch {
     int32_t places;          // place-count kernel: places per competitor in `counts` (null: no place table)
     int32_t *orders;         // place-count kernel, or null: ordered top-`places` tallies, n^places per race
     const int64_t *order_off;  // [n_races]: first entry of each race's tally table in `orders`
+    unsigned long long *hist_keys;  // place-count kernel, or null: finishing-order hash tables (keys)
+    int32_t *hist_counts;           // the count beside each key
+    const int64_t *hist_off;        // [n_races + 1]: each race's table (a power of two of entries)
 };
+
+// An empty entry of a finishing-order hash table (no order key reaches it: keys < 2^64 - 1).
+constexpr unsigned long long kEmptyOrderKey = ~0ull;
 
 // Philox4x32-10 key schedule: round i uses (seed_lo + i * 0x9E3779B9, seed_hi + i * 0xBB67AE85).
 inline void fill_round_keys(RolloutLaunch &l)
@@ -79,6 +85,7 @@ inline void fill_round_keys(RolloutLaunch &l)
 
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;
+constexpr int32_t kStatusTableFull = 2;  // a finishing-order hash table had no free entry
 
 // slots_per_lane: competitors held per lane (1 to 4; the place-count kernel takes 1, 2 or 4).
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
@@ -143,6 +150,10 @@ struct bbe_batch {
     int32_t order_places = 0;
     std::vector<int64_t> h_order_off;  // [n_races + 1]
     int64_t *d_order_off = nullptr;
+    // finishing-order histogram layout (bbe_order_histogram): each race's hash table
+    int32_t hist_places = 0;
+    std::vector<int64_t> h_hist_off;  // [n_races + 1]
+    int64_t *d_hist_off = nullptr;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int32_t *g_counts = nullptr;

@@ -44,6 +44,33 @@ struct WarpStage {
     float zc[3][128];
 };
 
+// One count for `key` in a hash table of `cap` entries (a power of two, at least twice the keys
+// it will hold, so a free entry is always found): MurmurHash3's 64-bit finaliser (Appleby)
+// picks the first entry, linear probing the next ones; an entry is claimed by compare-and-swap
+// from empty.  Where a key lands depends on the order of insertion; the set of (key, count)
+// pairs does not.  The probe loop is bounded by the table size.
+__device__ __forceinline__ void hist_insert(unsigned long long *keys, int32_t *counts, int64_t cap,
+                                            unsigned long long key, int32_t *status)
+{
+    unsigned long long h = key;
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    const unsigned long long mask = (unsigned long long)(cap - 1);
+    unsigned long long i = h & mask;
+    for (int64_t probe = 0; probe < cap; ++probe) {
+        const unsigned long long prev = atomicCAS(keys + i, kEmptyOrderKey, key);
+        if (prev == kEmptyOrderKey || prev == key) {
+            atomicAdd(counts + i, 1);
+            return;
+        }
+        i = (i + 1) & mask;
+    }
+    atomicOr(status, kStatusTableFull);
+}
+
 // (da, ca) comes after (db, cb) in rank order
 __device__ __forceinline__ bool key_gt(float da, int ca, float db, int cb)
 {
@@ -420,19 +447,32 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(RolloutLaunch l)
                             const int j = ql + m * nl;
                             if (seg_fin && j < K) atomicAdd(&cnt[my_ord[m] * K + j], 1);
                         }
-                        if (l.orders != nullptr && seg_fin) {
-                            // the ordered top K as one base-n number, gathered from the lanes
-                            // holding places 0 .. K-1 into the segment's first lane
-                            int code = 0;
+                        if ((l.orders != nullptr || l.hist_keys != nullptr) && seg_fin) {
+                            // the ordered top K, gathered from the lanes holding places 0 .. K-1:
+                            // as one base-n number (the dense tables, K <= 3) and as the order
+                            // key, the mixed-radix number whose digit j (radix n - j) is the
+                            // place-j finisher's index among the competitors not yet placed
+                            unsigned code = 0u, taken = 0u;
+                            unsigned long long key = 0ull;
                             for (int j = 0; j < K; ++j) {
                                 const int mj = j / nl;
                                 int mine = my_ord[0];
 #pragma unroll
                                 for (int m = 1; m < V; ++m)
                                     if (m == mj) mine = my_ord[m];
-                                code = code * n + __shfl_sync(segmask, mine, segbase + (j - mj * nl));
+                                const int cj = __shfl_sync(segmask, mine, segbase + (j - mj * nl));
+                                code = code * unsigned(n) + unsigned(cj);
+                                key = key * unsigned(n - j) + unsigned(__popc(((1u << cj) - 1u) & ~taken));
+                                taken |= 1u << cj;
                             }
-                            if (ql == 0) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                            if (ql == 0) {
+                                if (l.orders != nullptr) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                                if (l.hist_keys != nullptr) {
+                                    const int64_t h0 = l.hist_off[r];
+                                    hist_insert(l.hist_keys + h0, l.hist_counts + h0, l.hist_off[r + 1] - h0, key,
+                                                l.status);
+                                }
+                            }
                         }
                         placed = 0;
                         steps += seg_fin ? (t + 1) : t;
