@@ -657,6 +657,27 @@ def run_places(dev, stream) -> dict:
         cs = float((rb.sizes() * steps.cpu().numpy()).sum())
         out["K3_orders"] = {"s": t, "table_entries": total, "competitor_steps_per_s": cs / t,
                             "tuples_counted": int(orders.sum().item())}
+        del orders, counts
+        # the full finishing order (K = 20 of 20: 20! possible orders) as per-race hash tables
+        off = bbe.bbe_order_histogram_layout(b.handle, 20, rb.n_races)
+        entries = int(off[-1])
+        keys = torch.empty(entries, dtype=torch.uint64, device=dev)
+        hc = torch.empty(entries, dtype=torch.int32, device=dev)
+        bbe.bbe_order_histogram(b.handle, 20, keys, hc, None, steps, stream)  # warm-up (uploads the layout)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bbe.bbe_order_histogram(b.handle, 20, keys, hc, None, steps, stream)
+        e1.record(stream)
+        e1.synchronize()
+        b.status(stream)
+        t = e0.elapsed_time(e1) / 1e3
+        cs = float((rb.sizes() * steps.cpu().numpy()).sum())
+        out["K20_histogram"] = {"s": t, "table_entries": entries, "table_bytes": entries * 12,
+                                "distinct_orders": int((hc > 0).sum().item()),
+                                "orders_counted": int(hc.sum(dtype=torch.int64).item()),
+                                "competitor_steps_per_s": cs / t,
+                                "alu_frac": cs / t * ALG_OPS_PER_COMPETITOR_STEP / peak}
+        del keys, hc
     return out
 
 

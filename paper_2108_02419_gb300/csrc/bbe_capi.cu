@@ -618,7 +618,8 @@ bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, i
         l.hist_keys = hist_keys;
         l.hist_counts = hist_counts;
         l.hist_off = hist_keys ? b->d_hist_off : nullptr;
-        const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block);
+        l.place_cells = b->max_n * std::min(places, b->max_n);
+        const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block, l.place_cells);
         l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
         BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
     }

@@ -64,6 +64,7 @@ struct RolloutLaunch {
     int32_t grid, block;
     uint32_t round_key[20];  // Philox round keys (k0, k1) of rounds 0..9, from the seed
     int32_t places;          // place-count kernel: places per competitor in `counts` (null: no place table)
+    int32_t place_cells;     // place-count kernel: ints of each warp's [competitor][place] table (>= n K)
     int32_t *orders;         // place-count kernel, or null: ordered top-`places` tallies, n^places per race
     const int64_t *order_off;  // [n_races]: first entry of each race's tally table in `orders`
     unsigned long long *hist_keys;  // place-count kernel, or null: finishing-order hash tables (keys)
@@ -87,6 +88,35 @@ inline void fill_round_keys(RolloutLaunch &l)
 constexpr int32_t kStatusStepLimit = 1;
 constexpr int32_t kStatusTableFull = 2;  // a finishing-order hash table had no free entry
 
+#ifdef __CUDACC__
+// One count for `key` in a hash table of `cap` entries (a power of two, at least twice the keys
+// it will hold, so a free entry is always found): MurmurHash3's 64-bit finaliser (Appleby)
+// picks the first entry, linear probing the next ones; an entry is claimed by compare-and-swap
+// from empty.  Where a key lands depends on the order of insertion; the set of (key, count)
+// pairs does not.  The probe loop is bounded by the table size.
+__device__ __forceinline__ void hist_insert(unsigned long long *keys, int32_t *counts, int64_t cap,
+                                            unsigned long long key, int32_t *status)
+{
+    unsigned long long h = key;
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    const unsigned long long mask = (unsigned long long)(cap - 1);
+    unsigned long long i = h & mask;
+    for (int64_t probe = 0; probe < cap; ++probe) {
+        const unsigned long long prev = atomicCAS(keys + i, kEmptyOrderKey, key);
+        if (prev == kEmptyOrderKey || prev == key) {
+            atomicAdd(counts + i, 1);
+            return;
+        }
+        i = (i + 1) & mask;
+    }
+    atomicOr(status, kStatusTableFull);
+}
+#endif
+
 // slots_per_lane: competitors held per lane (1 to 4; the place-count kernel takes 1, 2 or 4).
 cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
 // Blocks of `block` threads of the rollout kernel that fit on one SM at once.
@@ -95,7 +125,7 @@ cudaError_t launch_win_probs(const DevBatch &b, const int32_t *counts, float *pr
                              cudaStream_t stream);
 // The rollout kernel in place mode: counts [n_total][l.places], rollouts to the K-th finisher.
 cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
-int place_resident_blocks(int dist, int slots_per_lane, int block);
+int place_resident_blocks(int dist, int slots_per_lane, int block, int place_cells);
 cudaError_t launch_place_probs(const DevBatch &b, int places, const int32_t *counts, int top, float *probs,
                                cudaStream_t stream);
 

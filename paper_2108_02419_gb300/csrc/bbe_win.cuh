@@ -89,9 +89,9 @@ __device__ __forceinline__ void draw_block(uint32_t k, uint32_t blk, uint32_t c,
 // Registers per thread: enough for one or two slots per lane to run without spilling at 7 or 8
 // resident 4-warp blocks per SM (measured faster than the compiler's unbounded choice), and
 // for the register-lean three- and four-slot variants.
-template <int V>
+template <int V, int MODE>
 struct WinRegs {
-    static constexpr int value = V == 1 ? 48 : (V == 2 ? 72 : 80);
+    static constexpr int value = MODE == 0 ? (V == 1 ? 48 : (V == 2 ? 72 : 80)) : (V == 1 ? 48 : (V == 2 ? 72 : 80));
 };
 // Parameters read from shared memory each step instead of held in registers.
 template <int V>
@@ -99,8 +99,12 @@ struct WinLean {
     static constexpr bool value = V >= 3;
 };
 
-template <int DIST, int V, int LAW>
-__global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch l)
+// MODE 0: win counts, each rollout run to its first finisher.  MODE 1: place counts (and the
+// ordered tallies), each rollout run until K = min(l.places, n) competitors have crossed; the
+// finished ones keep moving and blocking, a competitor has crossed exactly when its position is
+// at least L (positions only grow), and the finishers of a step are placed in (tau, slot) order.
+template <int DIST, int V, int LAW, int MODE>
+__global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(RolloutLaunch l)
 {
     constexpr bool PS = WinLean<V>::value;
     using Stage = WinStage<V>;
@@ -110,6 +114,15 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
     extern __shared__ __align__(16) unsigned char win_smem[];
     Stage &st = reinterpret_cast<Stage *>(win_smem)[threadIdx.x >> 5];
     char *const posb = reinterpret_cast<char *>(&st.pos[0][0]);
+    // place mode, per warp after all the stages: the finisher of each place (by segment base +
+    // place), the places filled (by segment base), then the work item's [competitor][place] table
+    int *pl_ord = nullptr, *pl_n = nullptr, *pl_cnt = nullptr;
+    if constexpr (MODE == 1) {
+        pl_ord = reinterpret_cast<int *>(win_smem + (blockDim.x >> 5) * sizeof(Stage)) +
+                 (threadIdx.x >> 5) * (2 * NS + l.place_cells);
+        pl_n = pl_ord + NS;
+        pl_cnt = pl_ord + 2 * NS;
+    }
     const DevBatch &b = l.b;
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -153,6 +166,11 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
         for (int i = lane; i < NS; i += 32) {
             st.key[i] = kNoKey;
             st.flag[i] = 0;
+        }
+        const int K = MODE == 1 ? min(l.places, n) : 1;  // places run per rollout
+        if constexpr (MODE == 1) {
+            for (int i = lane; i < NS; i += 32) pl_n[i] = 0;
+            for (int i = lane; i < n * K; i += 32) pl_cnt[i] = 0;
         }
         if (lane == 0) st.next_k = unsigned(w.k_begin) + unsigned(nseg);
         __syncwarp();
@@ -318,6 +336,89 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
             if (__any_sync(kAll, again)) full_sort(pb, fd, fp);
         };
 
+        // Place mode: place the step's new finishers of each segment one at a time, least (tau,
+        // slot) first (slot order is competitor order within a segment), then end the rollouts
+        // of the segments whose K-th place is filled.
+        auto place_step = [&](int J, const float (&S)[V], const bool (&fv)[V]) {
+            unsigned long long fk[V];
+            bool more = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                fk[v] = kNoKey;
+                if (fv[v]) {
+                    const float tau = __fdiv_rn(__fsub_rn(L, d[v]), S[v]);
+                    fk[v] = (static_cast<unsigned long long>(__float_as_uint(tau)) << 32) | unsigned(32 * v + lane);
+                    more = true;
+                }
+            }
+            // one finisher per segment per round; a segment has at most n of them
+            for (int round = 0; round < NS && __any_sync(kAll, more); ++round) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (fk[v] != kNoKey) atomicMin(&st.key[sb[v]], fk[v]);
+                __syncwarp();
+                bool won[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    won[v] = fk[v] != kNoKey && st.key[sb[v]] == fk[v];
+                    if (won[v]) {
+                        const int p = pl_n[sb[v]];
+                        pl_ord[sb[v] + p] = 32 * v + lane - sb[v];
+                        pl_n[sb[v]] = p + 1;
+                    }
+                }
+                __syncwarp();
+                more = false;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (fk[v] != kNoKey) st.key[sb[v]] = kNoKey;
+                    if (won[v]) fk[v] = kNoKey;
+                    more |= fk[v] != kNoKey;
+                }
+                __syncwarp();
+            }
+            // a segment whose K-th place is filled ends its rollout; its places and order are
+            // tallied when it restarts
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!alive[v] || pl_n[sb[v]] < K) continue;
+                if (32 * v + lane == sb[v]) steps += (unsigned long long)(blk[v] * 4u + unsigned(J) + 1u);
+                alive[v] = false;
+                pend[v] = true;
+            }
+            __syncwarp();
+        };
+
+        // Place mode, at a block boundary: the segments that completed a rollout (K places filled;
+        // a rollout cut off at max_steps fills fewer and counts for nobody) add one count per
+        // place and, for the ordered tallies, their order: as one base-n number (the dense
+        // tables, K <= 3) and as the order key, the mixed-radix number whose digit j (radix
+        // n - j) is the place-j finisher's index among the competitors not yet placed.
+        auto tally_completed = [&]() {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!pend[v] || pl_n[sb[v]] < K) continue;
+                const int c = 32 * v + lane - sb[v];  // this slot's competitor
+                if (c < K) atomicAdd(&pl_cnt[pl_ord[sb[v] + c] * K + c], 1);
+                if (c == 0 && (l.orders != nullptr || l.hist_keys != nullptr)) {
+                    unsigned code = 0u, taken = 0u;
+                    unsigned long long key = 0ull;
+                    for (int j = 0; j < K; ++j) {
+                        const int cj = pl_ord[sb[v] + j];
+                        code = code * unsigned(n) + unsigned(cj);
+                        key = key * unsigned(n - j) + unsigned(__popc(((1u << cj) - 1u) & ~taken));
+                        taken |= 1u << cj;
+                    }
+                    if (l.orders != nullptr) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                    if (l.hist_keys != nullptr) {
+                        const int64_t h0 = l.hist_off[r];
+                        hist_insert(l.hist_keys + h0, l.hist_counts + h0, l.hist_off[r + 1] - h0, key, l.status);
+                    }
+                }
+            }
+            __syncwarp();
+        };
+
         // One step of every slot: sub-step J of the Philox block (its normal is z[v][J]); CHK
         // when some segment may reach max_steps within the block.
         auto step = [&](auto Jc, auto CHKc, const float (&z)[V][4]) {
@@ -378,10 +479,12 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
                 Sv = fmaxf(Sv, kStepFloor);
                 S[v] = Sv;
                 dn[v] = __fadd_rn(d[v], Sv);
-                fv[v] = alive[v] && dn[v] >= L;
+                fv[v] = alive[v] && dn[v] >= L && (MODE == 0 || d[v] < L);
                 fin |= fv[v];
             }
-            if (__any_sync(kAll, fin)) {
+            if constexpr (MODE == 1) {
+                if (__any_sync(kAll, fin)) place_step(J, S, fv);
+            } else if (__any_sync(kAll, fin)) {
                 // least (tau, slot) per segment; tau > 0, so its bit pattern orders like its value
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -428,9 +531,13 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
             }
             const unsigned state = __reduce_or_sync(kAll, (pany ? 1u : 0u) | (aany ? 2u : 0u));
             if (state & 1u) {
+                if constexpr (MODE == 1) tally_completed();
 #pragma unroll
                 for (int v = 0; v < V; ++v)
-                    if (pend[v] && 32 * v + lane == sb[v]) st.segk[sb[v]] = atomicAdd(&st.next_k, 1u);
+                    if (pend[v] && 32 * v + lane == sb[v]) {
+                        st.segk[sb[v]] = atomicAdd(&st.next_k, 1u);
+                        if constexpr (MODE == 1) pl_n[sb[v]] = 0;
+                    }
                 __syncwarp();
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -488,72 +595,86 @@ __global__ void __maxnreg__(WinRegs<V>::value) win_rollout_kernel(RolloutLaunch 
             for (int v = 0; v < V; ++v) ++blk[v];
         }
 
-        // one global atomic per competitor with wins, one per work item for the step total
+        // one global atomic per competitor with wins (per competitor and place in place mode), one
+        // per work item for the step total
         __syncwarp();
-        if (lane < n && st.wins[lane] != 0) atomicAdd(&l.counts[off + lane], st.wins[lane]);
+        if constexpr (MODE == 1) {
+            for (int i = lane; i < n * K && l.counts != nullptr; i += 32) {
+                const int cc = pl_cnt[i];
+                if (cc != 0) atomicAdd(&l.counts[(off + i / K) * l.places + i % K], cc);
+            }
+        } else {
+            if (lane < n && st.wins[lane] != 0) atomicAdd(&l.counts[off + lane], st.wins[lane]);
+        }
         for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(kAll, steps, o);
         if (lane == 0 && l.steps != nullptr) atomicAdd(l.steps + r, steps);
     }
     if (__any_sync(kAll, hit_limit) && lane == 0) atomicOr(l.status, kStatusStepLimit);
 }
 
-template <int V>
-size_t win_stage_bytes(int block)
+// Dynamic shared memory of a block: the warps' stages, then in place mode each warp's place
+// lists (2 x 32 V ints) and [competitor][place] table (place_cells ints).
+template <int V, int MODE>
+size_t win_stage_bytes(int block, int place_cells)
 {
-    return size_t(block / 32) * sizeof(WinStage<V>);
+    const size_t warps = size_t(block / 32);
+    return warps * sizeof(WinStage<V>) + (MODE == 1 ? warps * (2 * 32 * V + size_t(place_cells)) * sizeof(int) : 0);
 }
 
-template <int V, int LAW>
+// The largest place table a launch may ask for (32 competitors x 32 places).
+constexpr int kMaxPlaceCells = 32 * 32;
+
+template <int V, int LAW, int MODE>
 cudaError_t launch_win_vl(const RolloutLaunch &l, cudaStream_t stream)
 {
-    const size_t smem = win_stage_bytes<V>(l.block);
+    const size_t smem = win_stage_bytes<V, MODE>(l.block, l.place_cells);
     switch (l.b.dist) {
-    case BBE_DIST_NORMAL: win_rollout_kernel<BBE_DIST_NORMAL, V, LAW><<<l.grid, l.block, smem, stream>>>(l); break;
-    case BBE_DIST_UNIFORM: win_rollout_kernel<BBE_DIST_UNIFORM, V, LAW><<<l.grid, l.block, smem, stream>>>(l); break;
-    default: win_rollout_kernel<BBE_DIST_TWO_POINT, V, LAW><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_NORMAL: win_rollout_kernel<BBE_DIST_NORMAL, V, LAW, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
+    case BBE_DIST_UNIFORM: win_rollout_kernel<BBE_DIST_UNIFORM, V, LAW, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
+    default: win_rollout_kernel<BBE_DIST_TWO_POINT, V, LAW, MODE><<<l.grid, l.block, smem, stream>>>(l); break;
     }
     return cudaGetLastError();
 }
 
 // Blocks resident per SM.  Also lets the kernels take the dynamic shared memory of the largest
 // block (16 warps may need more than the default 48 KB); every launch path asks this first.
-template <int DIST, int V, int LAW>
-int win_resident_dvl(int block)
+template <int DIST, int V, int LAW, int MODE>
+int win_resident_dvl(int block, int place_cells)
 {
-    const void *fn = reinterpret_cast<const void *>(win_rollout_kernel<DIST, V, LAW>);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_stage_bytes<V>(512))) !=
-        cudaSuccess) {
+    const void *fn = reinterpret_cast<const void *>(win_rollout_kernel<DIST, V, LAW, MODE>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(win_stage_bytes<V, MODE>(512, MODE == 1 ? kMaxPlaceCells : 0))) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     int nb = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, win_rollout_kernel<DIST, V, LAW>, block,
-                                                                        win_stage_bytes<V>(block));
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, win_rollout_kernel<DIST, V, LAW, MODE>,
+                                                                        block, win_stage_bytes<V, MODE>(block, place_cells));
     return e == cudaSuccess ? nb : 1;
 }
 
-// The launch and the residency query of the kernels of one responsiveness law (each law's
-// kernels are compiled in a translation unit of their own).
-template <int LAW>
+// The launch and the residency query of the kernels of one responsiveness law and mode (each
+// law's kernels are compiled in a translation unit of their own).
+template <int LAW, int MODE>
 cudaError_t launch_law(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
     switch (slots_per_lane) {
-    case 4: return launch_win_vl<4, LAW>(l, stream);
-    case 3: return launch_win_vl<3, LAW>(l, stream);
-    case 2: return launch_win_vl<2, LAW>(l, stream);
-    default: return launch_win_vl<1, LAW>(l, stream);
+    case 4: return launch_win_vl<4, LAW, MODE>(l, stream);
+    case 3: return launch_win_vl<3, LAW, MODE>(l, stream);
+    case 2: return launch_win_vl<2, LAW, MODE>(l, stream);
+    default: return launch_win_vl<1, LAW, MODE>(l, stream);
     }
 }
 
-template <int LAW>
-int resident_law(int dist, int slots_per_lane, int block)
+template <int LAW, int MODE>
+int resident_law(int dist, int slots_per_lane, int block, int place_cells)
 {
     auto one = [&](auto Vc) {
         constexpr int V = decltype(Vc)::value;
         switch (dist) {
-        case BBE_DIST_NORMAL: return win_resident_dvl<BBE_DIST_NORMAL, V, LAW>(block);
-        case BBE_DIST_UNIFORM: return win_resident_dvl<BBE_DIST_UNIFORM, V, LAW>(block);
-        default: return win_resident_dvl<BBE_DIST_TWO_POINT, V, LAW>(block);
+        case BBE_DIST_NORMAL: return win_resident_dvl<BBE_DIST_NORMAL, V, LAW, MODE>(block, place_cells);
+        case BBE_DIST_UNIFORM: return win_resident_dvl<BBE_DIST_UNIFORM, V, LAW, MODE>(block, place_cells);
+        default: return win_resident_dvl<BBE_DIST_TWO_POINT, V, LAW, MODE>(block, place_cells);
         }
     };
     switch (slots_per_lane) {

@@ -1,0 +1,19 @@
+// bbe_win_place.cu -- the place-count rollout kernels (kernel code: bbe_win.cuh, MODE 1): every
+// rollout runs to the K-th finisher for bbe_place_counts, bbe_order_counts and
+// bbe_order_histogram (position law of responsiveness only); a translation unit of its own so
+// that the build compiles the three kernel families in parallel.
+#include "bbe_win.cuh"
+
+namespace bbe {
+
+cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
+{
+    return win::launch_law<BBE_LAW_POSITION, 1>(l, slots_per_lane, stream);
+}
+
+int place_resident_blocks(int dist, int slots_per_lane, int block, int place_cells)
+{
+    return win::resident_law<BBE_LAW_POSITION, 1>(dist, slots_per_lane, block, place_cells);
+}
+
+}  // namespace bbe

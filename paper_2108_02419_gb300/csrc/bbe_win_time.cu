@@ -8,12 +8,12 @@ namespace win {
 
 cudaError_t launch_time_law(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
-    return launch_law<BBE_LAW_TIME>(l, slots_per_lane, stream);
+    return launch_law<BBE_LAW_TIME, 0>(l, slots_per_lane, stream);
 }
 
 int resident_time_law(int dist, int slots_per_lane, int block)
 {
-    return resident_law<BBE_LAW_TIME>(dist, slots_per_lane, block);
+    return resident_law<BBE_LAW_TIME, 0>(dist, slots_per_lane, block, 0);
 }
 
 }  // namespace win
