@@ -62,7 +62,8 @@ struct WinStage {
     int rnk[NS];                        // rank of each slot
     int flag[NS];                       // by segment base + rank: the slot there swaps with its successor
     unsigned segk[NS];                  // by segment base: rollout index handed to a restart
-    unsigned long long key[NS];         // by segment base: least (tau, slot) of the step's finishers
+    unsigned long long key[NS];         // by segment base: least crossing key of the block (win mode)
+    unsigned long long fkey[NS];        // place mode: each slot's crossing key of the block, or none
     unsigned next_k;                    // next rollout index of the work item
 };
 
@@ -115,13 +116,15 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
     Stage &st = reinterpret_cast<Stage *>(win_smem)[threadIdx.x >> 5];
     char *const posb = reinterpret_cast<char *>(&st.pos[0][0]);
     // place mode, per warp after all the stages: the finisher of each place (by segment base +
-    // place), the places filled (by segment base), then the work item's [competitor][place] table
-    int *pl_ord = nullptr, *pl_n = nullptr, *pl_cnt = nullptr;
+    // place), the places filled and the sub-step of the K-th place (by segment base), then the
+    // work item's [competitor][place] table
+    int *pl_ord = nullptr, *pl_n = nullptr, *pl_kj = nullptr, *pl_cnt = nullptr;
     if constexpr (MODE == 1) {
         pl_ord = reinterpret_cast<int *>(win_smem + (blockDim.x >> 5) * sizeof(Stage)) +
-                 (threadIdx.x >> 5) * (2 * NS + l.place_cells);
+                 (threadIdx.x >> 5) * (3 * NS + l.place_cells);
         pl_n = pl_ord + NS;
-        pl_cnt = pl_ord + 2 * NS;
+        pl_kj = pl_ord + 2 * NS;
+        pl_cnt = pl_ord + 3 * NS;
     }
     const DevBatch &b = l.b;
     const int lane = threadIdx.x & 31;
@@ -169,7 +172,10 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         }
         const int K = MODE == 1 ? min(l.places, n) : 1;  // places run per rollout
         if constexpr (MODE == 1) {
-            for (int i = lane; i < NS; i += 32) pl_n[i] = 0;
+            for (int i = lane; i < NS; i += 32) {
+                pl_n[i] = 0;
+                st.fkey[i] = kNoKey;
+            }
             for (int i = lane; i < n * K; i += 32) pl_cnt[i] = 0;
         }
         if (lane == 0) st.next_k = unsigned(w.k_begin) + unsigned(nseg);
@@ -189,9 +195,10 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         float mu[V], sg[V], P[V], th[V], kr[V], d[V], pv[V];
         const float4 *pqa[V];  // register-lean variant: this slot's (mu, sigma, P, theta)
         const float *kra[V];   // register-lean variant: this slot's kappa (2 rho - 1)
-        bool alive[V], pend[V];
+        bool alive[V], pend[V], cut[V];  // running; rollout ended, to restart; stopped at max_steps
         unsigned long long steps = 0;
-        unsigned gblk = 0;  // blocks run in this work item (saturating)
+        unsigned gblk = 0;     // blocks run in this work item (saturating)
+        bool blk_fin = false;  // warp-uniform: some slot crossed the line in this block
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int slot = 32 * v + lane;
@@ -202,6 +209,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             kk[v] = unsigned(w.k_begin) + unsigned(seg);
             alive[v] = used && kk[v] < kend;
             pend[v] = false;
+            cut[v] = false;
             blk[v] = 0;
             if constexpr (PS) {
                 pqa[v] = &st.pq[c];
@@ -336,55 +344,71 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             if (__any_sync(kAll, again)) full_sort(pb, fd, fp);
         };
 
-        // Place mode: place the step's new finishers of each segment one at a time, least (tau,
-        // slot) first (slot order is competitor order within a segment), then end the rollouts
-        // of the segments whose K-th place is filled.
-        auto place_step = [&](int J, const float (&S)[V], const bool (&fv)[V]) {
-            unsigned long long fk[V];
-            bool more = false;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                fk[v] = kNoKey;
-                if (fv[v]) {
-                    const float tau = __fdiv_rn(__fsub_rn(L, d[v]), S[v]);
-                    fk[v] = (static_cast<unsigned long long>(__float_as_uint(tau)) << 32) | unsigned(32 * v + lane);
-                    more = true;
-                }
-            }
-            // one finisher per segment per round; a segment has at most n of them
-            for (int round = 0; round < NS && __any_sync(kAll, more); ++round) {
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (fk[v] != kNoKey) atomicMin(&st.key[sb[v]], fk[v]);
-                __syncwarp();
-                bool won[V];
+        // Place mode, the end of a Philox block in which some slot crossed the line or may have
+        // reached max_steps: the block's crossings of each segment take the next places one at
+        // a time in key order (sub-step, tau, slot), and a segment whose K-th place is filled
+        // ends its rollout (its places and order are tallied when it restarts); a rollout
+        // stopped at max_steps that did not end earlier counts for nobody.  Ending at the
+        // block's end costs nothing: a segment whose rollout ended waits for the next block in
+        // any case, and its slots record no further crossings (d < L fails past the line).
+        // (Measured slower for win counts, which end their rollouts within the step.)
+        auto block_end = [&]() {
+            __syncwarp();
+            {
+                unsigned long long fk[V];
+                bool more = false;
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    won[v] = fk[v] != kNoKey && st.key[sb[v]] == fk[v];
-                    if (won[v]) {
-                        const int p = pl_n[sb[v]];
-                        pl_ord[sb[v] + p] = 32 * v + lane - sb[v];
-                        pl_n[sb[v]] = p + 1;
+                    const int slot = 32 * v + lane;
+                    fk[v] = st.fkey[slot];
+                    if (fk[v] != kNoKey) {
+                        st.fkey[slot] = kNoKey;
+                        more = true;
                     }
                 }
-                __syncwarp();
-                more = false;
+                // one crossing per segment per round; a segment has at most n of them
+                for (int round = 0; round < NS && __any_sync(kAll, more); ++round) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (fk[v] != kNoKey) st.key[sb[v]] = kNoKey;
-                    if (won[v]) fk[v] = kNoKey;
-                    more |= fk[v] != kNoKey;
+                    for (int v = 0; v < V; ++v)
+                        if (fk[v] != kNoKey) atomicMin(&st.key[sb[v]], fk[v]);
+                    __syncwarp();
+                    bool won[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        won[v] = fk[v] != kNoKey && st.key[sb[v]] == fk[v];
+                        if (won[v]) {
+                            const int p = pl_n[sb[v]];
+                            pl_ord[sb[v] + p] = 32 * v + lane - sb[v];
+                            pl_n[sb[v]] = p + 1;
+                            if (p == K - 1) pl_kj[sb[v]] = int(fk[v] >> 40);
+                        }
+                    }
+                    __syncwarp();
+                    more = false;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (fk[v] != kNoKey) st.key[sb[v]] = kNoKey;
+                        if (won[v]) fk[v] = kNoKey;
+                        more |= fk[v] != kNoKey;
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
-            // a segment whose K-th place is filled ends its rollout; its places and order are
-            // tallied when it restarts
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                if (!alive[v] || pl_n[sb[v]] < K) continue;
-                if (32 * v + lane == sb[v]) steps += (unsigned long long)(blk[v] * 4u + unsigned(J) + 1u);
-                alive[v] = false;
-                pend[v] = true;
+                if (!alive[v] && !cut[v]) continue;
+                const int slot = 32 * v + lane;
+                const int jend = pl_n[sb[v]] >= K ? pl_kj[sb[v]] : -1;  // sub-step of the K-th place
+                if (jend >= 0) {
+                    if (slot == sb[v]) steps += (unsigned long long)(blk[v] * 4u + unsigned(jend) + 1u);
+                    pend[v] = true;
+                } else if (cut[v]) {
+                    if (slot == sb[v]) steps += (unsigned long long)l.max_steps;
+                    hit_limit = true;
+                    pend[v] = true;
+                }
+                alive[v] = alive[v] && !pend[v];
+                cut[v] = false;
             }
             __syncwarp();
         };
@@ -426,14 +450,19 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             constexpr bool CHK = decltype(CHKc)::value;
             constexpr int BO = (J & 1) * ROWB;
             if constexpr (CHK) {
-                // a rollout reaching step max_steps ends without a winner (it counts for nobody)
+                // a rollout reaching step max_steps stops there and counts for nobody (in place
+                // mode unless it ended earlier in the block, decided at the block's end)
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (alive[v] && int(blk[v]) * 4 + J >= l.max_steps) {
                         alive[v] = false;
-                        pend[v] = true;
-                        hit_limit = true;
-                        if (32 * v + lane == sb[v]) steps += (unsigned long long)l.max_steps;
+                        if constexpr (MODE == 0) {
+                            pend[v] = true;
+                            hit_limit = true;
+                            if (32 * v + lane == sb[v]) steps += (unsigned long long)l.max_steps;
+                        } else {
+                            cut[v] = true;
+                        }
                     }
                 }
             }
@@ -483,9 +512,25 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                 fin |= fv[v];
             }
             if constexpr (MODE == 1) {
-                if (__any_sync(kAll, fin)) place_step(J, S, fv);
+                // place mode: a crossing is recorded with its key (sub-step, within-step crossing
+                // time tau, slot) and placed at the block's end; tau > 0, so its bit pattern orders
+                // like its value, and key order is the order of finish with ties to the lower
+                // competitor index (the slot order within a segment)
+                if (__any_sync(kAll, fin)) {
+                    blk_fin = true;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (fv[v]) {
+                            const float tau = __fdiv_rn(__fsub_rn(L, d[v]), S[v]);
+                            st.fkey[32 * v + lane] = (static_cast<unsigned long long>(J) << 40) |
+                                                     (static_cast<unsigned long long>(__float_as_uint(tau)) << 8) |
+                                                     unsigned(32 * v + lane);
+                        }
+                    }
+                }
             } else if (__any_sync(kAll, fin)) {
-                // least (tau, slot) per segment; tau > 0, so its bit pattern orders like its value
+                // win mode: least (tau, slot) per segment, at once; tau > 0, so its bit pattern
+                // orders like its value
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (fv[v]) {
@@ -580,16 +625,21 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                 for (int v = 0; v < V; ++v) near_limit |= alive[v] && int(blk[v]) * 4 + 4 > l.max_steps;
             }
             gblk += gblk < (1u << 28) ? 1u : 0u;
+            blk_fin = false;
             if (__any_sync(kAll, near_limit)) {
                 step(std::integral_constant<int, 0>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 1>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 2>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 3>{}, std::true_type{}, z);
+                if constexpr (MODE == 1) block_end();
             } else {
                 step(std::integral_constant<int, 0>{}, std::false_type{}, z);
                 step(std::integral_constant<int, 1>{}, std::false_type{}, z);
                 step(std::integral_constant<int, 2>{}, std::false_type{}, z);
                 step(std::integral_constant<int, 3>{}, std::false_type{}, z);
+                if constexpr (MODE == 1) {
+                    if (blk_fin) block_end();
+                }
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) ++blk[v];
@@ -613,12 +663,12 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
 }
 
 // Dynamic shared memory of a block: the warps' stages, then in place mode each warp's place
-// lists (2 x 32 V ints) and [competitor][place] table (place_cells ints).
+// lists (3 x 32 V ints) and [competitor][place] table (place_cells ints).
 template <int V, int MODE>
 size_t win_stage_bytes(int block, int place_cells)
 {
     const size_t warps = size_t(block / 32);
-    return warps * sizeof(WinStage<V>) + (MODE == 1 ? warps * (2 * 32 * V + size_t(place_cells)) * sizeof(int) : 0);
+    return warps * sizeof(WinStage<V>) + (MODE == 1 ? warps * (3 * 32 * V + size_t(place_cells)) * sizeof(int) : 0);
 }
 
 // The largest place table a launch may ask for (32 competitors x 32 places).
