@@ -148,3 +148,17 @@ def test_rejects_keys_beyond_64_bits_and_time_law(bbe):
         with pytest.raises(bbe.BbeError) as ei:
             b.order_histogram(4)
         assert ei.value.status == -2
+
+
+@pytest.mark.parametrize("slots", [1, 3, 4])
+def test_other_layouts_match_oracle(bbe, slots):
+    rb = W.uneven_batch(seed=46, n_races=24, n_lo=1, n_hi=12, rollouts=250, rem_lo=100.0, rem_hi=1200.0)
+    with bbe.Batch(rb) as b:
+        b.set_cfg(slots_per_lane=slots)
+        keys, counts, off, _, steps = b.order_histogram(32)
+        b.status()
+        got = histograms(rb, keys.cpu().numpy(), counts.cpu().numpy(), off, 32)
+        steps = steps.cpu().numpy()
+    want, want_s, st = oracle.batch_order_histograms(rb, 32)
+    assert st == 0 and got == [dict(w) for w in want]
+    assert np.array_equal(steps, want_s)

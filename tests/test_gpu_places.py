@@ -162,3 +162,29 @@ def test_full_uniform_batch_sampled(bbe):
     rng = np.random.default_rng(2)
     sample = [0, rb.n_races - 1] + list(rng.choice(rb.n_races, 2, replace=False))
     assert_places_match(rb, 3, counts, steps, races=sample)
+
+
+@pytest.mark.parametrize("slots", [1, 2, 3, 4])
+def test_every_layout_matches_oracle(bbe, slots):
+    # each competitors-per-lane layout of the place mode (races smaller than the layout take two,
+    # or one for a lone competitor), to the third and to the last finisher, with heavy blocking
+    rng = np.random.default_rng(24 + slots)
+    sizes = [1, 2, 3, 5, 7, 11, 16, 20, 24, 32]
+    nt = sum(sizes)
+    rb = W.from_arrays(sizes, 300.0, 96, rng.uniform(0, 60, nt), rng.uniform(15, 17, nt), rng.uniform(0.5, 1.5, nt),
+                       rng.uniform(0, 1, nt), theta=rng.uniform(1.0, 6.0, nt), seed=77)
+    for places in (3, 32):
+        counts, steps = run_places(bbe, rb, places, cfg={"slots_per_lane": slots})
+        assert_places_match(rb, places, counts, steps)
+
+
+def test_mixed_layout_table_matches_oracle(bbe):
+    # a per-count layout table puts the races in four launches (one per layout) of the same pass
+    rb = W.uneven_batch(seed=25, n_races=60, n_lo=1, n_hi=24, rollouts=200, rem_lo=100.0, rem_hi=1500.0)
+    table = [0] + [1 + (n % 4) for n in range(1, 33)]
+    with bbe.Batch(rb) as b:
+        b.set_layout(table)
+        counts, steps = b.places(5)
+        b.status()
+        counts, steps = counts.cpu().numpy(), steps.cpu().numpy()
+    assert_places_match(rb, 5, counts, steps)
