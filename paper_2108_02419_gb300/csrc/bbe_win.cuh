@@ -197,8 +197,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         const float *kra[V];   // register-lean variant: this slot's kappa (2 rho - 1)
         bool alive[V], pend[V], cut[V];  // running; rollout ended, to restart; stopped at max_steps
         unsigned long long steps = 0;
-        unsigned gblk = 0;     // blocks run in this work item (saturating)
-        bool blk_fin = false;  // warp-uniform: some slot crossed the line in this block
+        bool blk_fin = false;  // warp-uniform: some slot crossed the line in this block (a finish)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int slot = 32 * v + lane;
@@ -531,6 +530,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             } else if (__any_sync(kAll, fin)) {
                 // win mode: least (tau, slot) per segment, at once; tau > 0, so its bit pattern
                 // orders like its value
+                blk_fin = true;
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (fv[v]) {
@@ -565,7 +565,14 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             }
         };
 
+        // blocks before one in which a rollout could reach max_steps (the check starts there)
+        unsigned left = l.max_steps >= 4 ? unsigned(l.max_steps - 4) / 4u + 1u : 0u;
+        // warp-uniform: the last block may have changed which slots run (a finish, a cut-off);
+        // after a block without either the reduction below would find nothing to do
+        bool blk_event = true;
         for (;;) {
+            if (blk_event) {
+            blk_event = false;
             // segments that finished in the last block start their next rollout; one reduction
             // says whether any did and whether anything still runs
             bool pany = false, aany = false;
@@ -611,22 +618,25 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             } else if (!(state & 2u)) {
                 break;
             }
+            }
 
             // the block's normals: one Philox4x32-10 output per slot, counter (k, t >> 2, c, race)
             float z[V][4];
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 draw_block<DIST>(kk[v], blk[v], uint32_t(32 * v + lane - sb[v]), rid, l.round_key, z[v]);
-            // no slot is further into its rollout than the work item's block count, so one
-            // warp-uniform compare rules out the step limit in all but the longest items
+            // no slot is further into its rollout than the blocks the work item has run, so a
+            // warp-uniform count-down rules out the step limit in all but the longest items
             bool near_limit = false;
-            if (gblk * 4u + 4u > unsigned(l.max_steps)) {
+            if (left == 0u) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) near_limit |= alive[v] && int(blk[v]) * 4 + 4 > l.max_steps;
+            } else {
+                --left;
             }
-            gblk += gblk < (1u << 28) ? 1u : 0u;
             blk_fin = false;
-            if (__any_sync(kAll, near_limit)) {
+            if (left == 0u && __any_sync(kAll, near_limit)) {
+                blk_event = true;
                 step(std::integral_constant<int, 0>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 1>{}, std::true_type{}, z);
                 step(std::integral_constant<int, 2>{}, std::true_type{}, z);
@@ -640,6 +650,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                 if constexpr (MODE == 1) {
                     if (blk_fin) block_end();
                 }
+                blk_event = blk_event || blk_fin;
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) ++blk[v];
