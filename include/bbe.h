@@ -97,9 +97,11 @@ typedef struct {
     int32_t rollouts_per_lane;  /* rollouts each warp segment runs per work item, 1..65536 (halved, down
                                    to 1, for a batch too small to give every warp slot an item) */
     int32_t max_steps;          /* step limit per rollout, 1..2^30 */
-    int32_t slots_per_lane;     /* competitors per lane, 0..4: 0 = automatic (two), 1..4 = that layout
-                                   for every race of at least that many competitors (smaller races
-                                   take two, or one for a lone competitor) */
+    int32_t slots_per_lane;     /* competitors per lane, 0..4: 0 = automatic (two; one for a batch too
+                                   small to give every warp slot an item even at one rollout per
+                                   lane), 1..4 = that layout for every race of at least that many
+                                   competitors (smaller races take two, or one for a lone
+                                   competitor) */
 } bbe_launch_cfg;
 
 /* bbe_race_init -- validate a batch of race states and stage it on the current device.
@@ -392,8 +394,8 @@ BBE_API void bbe_destroy_batch(bbe_batch *batch);
  * differences: every array must be memory of the current device (or managed memory; host
  * pointers and other devices' memory are rejected), pref and theta are required,
  * n_competitors = race_off[n_races] is the length of the per-competitor arrays, and the
- * launch shape is the library default (two competitors per lane, 4-warp blocks, 32
- * rollouts per lane and work item).  Counts and step totals are identical to
+ * launch shape is fixed: two competitors per lane (the library's automatic layout for a
+ * batch that fills the GPU), 4-warp blocks, 32 rollouts per lane and work item.  Counts and step totals are identical to
  * bbe_rollout_batch's for the same inputs.
  *
  * Synchronous: the call synchronises cuda_stream after validating the batch on the device

@@ -117,13 +117,15 @@ constexpr int kSlots[kGroups] = {1, 2, 3, 4};
 
 int group_of(int v) { return v - 1; }
 
-// Competitors per lane for a race of n.  Automatic choice: two, the layout measured fastest
-// on GB300 for the uneven mix of 2..24 competitors (3.13e11 competitor-steps/s against
+// Competitors per lane for a race of n.  Automatic choice (`dflt`): two, the layout measured
+// fastest on GB300 for the uneven mix of 2..24 competitors (3.13e11 competitor-steps/s against
 // 1.72e11 with one per lane up to 5 and four for 21..24, whose four-slot kernel runs short of
-// registers).  `mode` forces a layout.
-int slots_for(int n, int mode, const int8_t *by_n = nullptr)
+// registers); one for a batch too small to fill the GPU's warps (build_items), where the
+// latency of a warp's step decides (a 5-competitor race of 10^3 rollouts: 0.061 ms a pass
+// against 0.091).  `mode` forces a layout, `by_n` gives one per competitor count.
+int slots_for(int n, int mode, const int8_t *by_n = nullptr, int dflt = 2)
 {
-    const int v = mode != 0 ? mode : (by_n && by_n[n] ? by_n[n] : 2);  // forced, the per-count table, or two
+    const int v = mode != 0 ? mode : (by_n && by_n[n] ? by_n[n] : dflt);  // forced, the per-count table, or automatic
     return n >= v ? v : std::min(n, 2);  // a layout wider than the race falls back
 }
 
@@ -150,26 +152,32 @@ bbe_status build_items(bbe_batch *b)
     };
     auto nseg_of = [&](int r) {  // segments of a warp: floor(32 V / n) slots of n
         const int n = b->h_off[r + 1] - b->h_off[r];
-        return 32 * slots_for(n, b->cfg.slots_per_lane, b->slots_by_n) / n;
+        return 32 * slots_for(n, b->cfg.slots_per_lane, b->slots_by_n, b->default_slots) / n;
     };
     // A batch too small to give every warp the GPU can hold (64 per SM) a work item runs fewer
     // rollouts per lane, down to one: the chunking decides which warp runs a rollout, never its
     // result.  (An item holds at most 32 x per_lane rollouts, so large batches skip the count.)
     int64_t per_lane = b->cfg.rollouts_per_lane;
     const int64_t warp_slots = int64_t(std::max(1, b->num_sms)) * 64;
-    while (per_lane > 1 && total_rollouts < warp_slots * per_lane * 32) {
+    auto items_at = [&](int64_t pl) {  // items of the list at pl rollouts per lane, counted up to warp_slots
         int64_t items = 0;
         for (int r = 0; r < b->n_races && items < warp_slots; ++r) {
-            const int64_t chunk = chunk_of(r, per_lane, nseg_of(r));
+            const int64_t chunk = chunk_of(r, pl, nseg_of(r));
             items += (b->h_R[r] + chunk - 1) / chunk;
         }
-        if (items >= warp_slots) break;
+        return items;
+    };
+    b->default_slots = 2;
+    while (per_lane > 1 && total_rollouts < warp_slots * per_lane * 32) {
+        if (items_at(per_lane) >= warp_slots) break;
         per_lane = std::max<int64_t>(1, per_lane / 2);
     }
+    // still short of work for every warp at one rollout per lane: one competitor per lane
+    if (per_lane == 1 && total_rollouts < warp_slots * 32 && items_at(1) < warp_slots) b->default_slots = 1;
     size_t total = 0;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
-        const int v = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n);
+        const int v = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n, b->default_slots);
         const int nseg = nseg_of(r);
         const int64_t chunk = chunk_of(r, per_lane, nseg);
         const double st = est_steps(b, r);
@@ -238,8 +246,10 @@ bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *ste
     l.status = b->d_status;
     l.max_steps = b->cfg.max_steps;
     l.block = 32 * b->cfg.warps_per_block;
-    // persistent grid: never more blocks than can be resident at once
+    // persistent grid: never more blocks than can be resident at once, nor more warps than work
+    // items (a warp runs one item at a time; a small batch then launches and drains faster)
     l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, b->resident[g])));
+    l.grid = std::max(1, std::min(l.grid, (l.n_items + b->cfg.warps_per_block - 1) / b->cfg.warps_per_block));
     bbe::fill_round_keys(l);
     return l;
 }
@@ -621,6 +631,7 @@ bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, i
         l.place_cells = b->max_n * std::min(places, b->max_n);
         const int res = bbe::place_resident_blocks(b->dev.dist, kSlots[g], l.block, l.place_cells);
         l.grid = std::max(1, b->num_sms * std::min(b->cfg.blocks_per_sm, std::max(1, res)));
+        l.grid = std::max(1, std::min(l.grid, (l.n_items + b->cfg.warps_per_block - 1) / b->cfg.warps_per_block));
         BBE_CUDA_TRY(bbe::launch_place_rollout(l, kSlots[g], s));
     }
     BBE_CUDA_TRY(bbe::note_use(b, s));
@@ -979,7 +990,8 @@ bbe_status bbe_batch_layout(const bbe_batch *b, int32_t *slots_by_n)
         return BBE_ERR_ARG;
     }
     slots_by_n[0] = 0;
-    for (int n = 1; n <= BBE_MAX_COMPETITORS; ++n) slots_by_n[n] = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n);
+    for (int n = 1; n <= BBE_MAX_COMPETITORS; ++n)
+        slots_by_n[n] = slots_for(n, b->cfg.slots_per_lane, b->slots_by_n, b->default_slots);
     return BBE_OK;
 }
 

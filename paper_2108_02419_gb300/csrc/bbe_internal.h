@@ -168,6 +168,7 @@ struct bbe_batch {
 
     bbe_launch_cfg cfg{};
     int8_t slots_by_n[BBE_MAX_COMPETITORS + 1] = {};  // layout per competitor count (0: the default)
+    int8_t default_slots = 2;  // the automatic layout: two per lane, one for a batch too small to fill the GPU
     int32_t resident[4] = {1, 1, 1, 1};  // rollout-kernel blocks resident per SM, per group
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -276,6 +276,7 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
         l.max_steps = BBE_MAX_STEPS_DEFAULT;
         l.block = block;
         l.grid = sms * std::max(1, std::min(16, bbe::rollout_resident_blocks(int(dist), kSlots, block)));
+        l.grid = std::max(1, std::min(l.grid, (l.n_items + block / 32 - 1) / (block / 32)));  // no idle warps
         bbe::fill_round_keys(l);
         NA_TRY(bbe::launch_rollout(l, kSlots, s));
     }

@@ -288,3 +288,21 @@ def test_full_uneven_batch_sampled(bbe):
     rng = np.random.default_rng(1)
     sample = sorted(set(cheap.tolist() + rng.choice(rb.n_races, 2, replace=False).tolist()))
     assert_matches_oracle(rb, counts, steps, probs, races=sample)
+
+
+def test_automatic_layout_follows_batch_size(bbe):
+    # a batch too small to give every warp of the GPU an item runs one competitor per lane (its
+    # steps' latency decides); a large one runs two; the counts do not depend on it
+    small = W.single_race_start(seed=0)
+    with bbe.Batch(small) as b:
+        assert b.layout()[5] == 1
+        counts, steps = b.rollout()
+        b.status()
+        c1, s1 = counts.cpu().numpy(), steps.cpu().numpy()
+        b.set_cfg(slots_per_lane=2)
+        counts, steps = b.rollout()
+        b.status()
+        assert np.array_equal(counts.cpu().numpy(), c1) and np.array_equal(steps.cpu().numpy(), s1)
+    assert_matches_oracle(small, c1, s1)
+    with bbe.Batch(W.uniform_batch(seed=0, n_races=1024, rollouts=2000)) as b:
+        assert b.layout()[20] == 2
