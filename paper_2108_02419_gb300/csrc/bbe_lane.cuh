@@ -1,5 +1,6 @@
 // bbe_lane.cuh -- one step of Eq. 1 in the one-competitor-per-lane layout (the trajectory
-// kernel: one rollout per race, so the rank-ordered slots of the rollout kernel do not pay).
+// kernel: one rollout per race, so the rollout kernel's rank tables and packed segments do not
+// pay).
 //
 // A race of n competitors occupies a segment of n lanes (lane segbase + c holds competitor c
 // for the whole rollout).  i+ (the nearest competitor strictly in front, lowest index among
