@@ -145,14 +145,15 @@ bbe_status build_items(bbe_batch *b)
     int64_t total_rollouts = 0;
     for (int r = 0; r < b->n_races; ++r) total_rollouts += b->h_R[r];
     const int64_t min_chunk = (total_rollouts + kMaxItems - 1) / kMaxItems;
+    int64_t race_items = kMaxItemsPerRace;  // items per race at most (lifted for very small batches)
     auto chunk_of = [&](int r, int64_t per_lane, int nseg) {
-        // at least per_lane rollouts per segment, at most kMaxItemsPerRace items per race
-        return std::max<int64_t>(std::max<int64_t>(per_lane * nseg, (b->h_R[r] + kMaxItemsPerRace - 1) / kMaxItemsPerRace),
-                                 min_chunk);
+        // at least per_lane rollouts per segment, at most race_items items per race
+        return std::max<int64_t>(std::max<int64_t>(per_lane * nseg, (b->h_R[r] + race_items - 1) / race_items), min_chunk);
     };
     auto nseg_of = [&](int r) {  // segments of a warp: floor(32 V / n) slots of n
         const int n = b->h_off[r + 1] - b->h_off[r];
-        return 32 * slots_for(n, b->cfg.slots_per_lane, b->slots_by_n, b->default_slots) / n;
+        const int fit = 32 * slots_for(n, b->cfg.slots_per_lane, b->slots_by_n, b->default_slots) / n;
+        return b->seg_cap > 0 ? std::min(fit, b->seg_cap) : fit;
     };
     // A batch too small to give every warp the GPU can hold (64 per SM) a work item runs fewer
     // rollouts per lane, down to one: the chunking decides which warp runs a rollout, never its
@@ -168,12 +169,25 @@ bbe_status build_items(bbe_batch *b)
         return items;
     };
     b->default_slots = 2;
+    b->seg_cap = 0;
     while (per_lane > 1 && total_rollouts < warp_slots * per_lane * 32) {
         if (items_at(per_lane) >= warp_slots) break;
         per_lane = std::max<int64_t>(1, per_lane / 2);
     }
-    // still short of work for every warp at one rollout per lane: one competitor per lane
-    if (per_lane == 1 && total_rollouts < warp_slots * 32 && items_at(1) < warp_slots) b->default_slots = 1;
+    // still short of work for every warp at one rollout per lane: one competitor per lane, and
+    // as few concurrent rollouts per warp as keep the list within the warp slots (a warp's step
+    // then waits on fewer segments' rank repairs; a race may then take up to one item per warp
+    // slot, so that each segment runs one rollout)
+    if (per_lane == 1 && total_rollouts < warp_slots * 32 && items_at(1) < warp_slots) {
+        b->default_slots = 1;
+        race_items = warp_slots;
+        for (int32_t cap = 1; cap < 32; cap *= 2) {
+            b->seg_cap = cap;
+            if (items_at(1) < warp_slots) break;
+            b->seg_cap = 0;
+        }
+        if (b->seg_cap == 0) race_items = kMaxItemsPerRace;
+    }
     size_t total = 0;
     for (int r = 0; r < b->n_races; ++r) {
         const int n = b->h_off[r + 1] - b->h_off[r];
@@ -245,6 +259,7 @@ bbe::RolloutLaunch make_launch(const bbe_batch *b, int32_t *counts, int64_t *ste
     l.steps = reinterpret_cast<unsigned long long *>(steps);
     l.status = b->d_status;
     l.max_steps = b->cfg.max_steps;
+    l.seg_cap = b->seg_cap;
     l.block = 32 * b->cfg.warps_per_block;
     // persistent grid: never more blocks than can be resident at once, nor more warps than work
     // items (a warp runs one item at a time; a small batch then launches and drains faster)

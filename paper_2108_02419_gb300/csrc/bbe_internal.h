@@ -65,6 +65,7 @@ struct RolloutLaunch {
     uint32_t round_key[20];  // Philox round keys (k0, k1) of rounds 0..9, from the seed
     int32_t places;          // place-count kernel: places per competitor in `counts` (null: no place table)
     int32_t place_cells;     // place-count kernel: ints of each warp's [competitor][place] table (>= n K)
+    int32_t seg_cap;         // most segments (concurrent rollouts) per warp, or 0: as many as fit
     int32_t *orders;         // place-count kernel, or null: ordered top-`places` tallies, n^places per race
     const int64_t *order_off;  // [n_races]: first entry of each race's tally table in `orders`
     unsigned long long *hist_keys;  // place-count kernel, or null: finishing-order hash tables (keys)
@@ -169,6 +170,7 @@ struct bbe_batch {
     bbe_launch_cfg cfg{};
     int8_t slots_by_n[BBE_MAX_COMPETITORS + 1] = {};  // layout per competitor count (0: the default)
     int8_t default_slots = 2;  // the automatic layout: two per lane, one for a batch too small to fill the GPU
+    int32_t seg_cap = 0;       // segments per warp at most (0: as many as fit); set for very small batches
     int32_t resident[4] = {1, 1, 1, 1};  // rollout-kernel blocks resident per SM, per group
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

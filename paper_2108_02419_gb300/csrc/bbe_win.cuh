@@ -142,7 +142,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         const int r = w.race;
         const int off = b.race_off[r];
         const int n = b.race_off[r + 1] - off;
-        const int nseg = NS / n;
+        const int nseg = l.seg_cap > 0 ? min(NS / n, l.seg_cap) : NS / n;  // segments of this warp
 
         // stage the race: lane j < n loads competitor j (coalesced) and ranks it by (d0, j)
         __syncwarp();
