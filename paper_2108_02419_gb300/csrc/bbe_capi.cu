@@ -9,6 +9,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -71,6 +73,40 @@ bbe_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s, con
         return BBE_ERR_CUDA;
     }
     return BBE_OK;
+}
+
+// Device memory of staged batches comes from one stream-ordered pool per device owned by the
+// library, which keeps up to kPoolKeep bytes of freed memory for the next batch (the default
+// pool hands freed memory back at once, and mapping it again costs ~90 us per batch); it is
+// never the process's default pool, whose settings other libraries may rely on.
+constexpr uint64_t kPoolKeep = uint64_t(256) << 20;
+
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s)
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = pools.find(dev);
+        if (it == pools.end()) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+            uint64_t keep = kPoolKeep;
+            if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+            pools[dev] = pool;
+        } else {
+            pool = it->second;
+        }
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, s);
 }
 
 void free_graph(bbe_batch *b)
@@ -225,7 +261,7 @@ bbe_status build_items(bbe_batch *b)
     // work that may still read it
     bbe::WorkItem *fresh = nullptr;
     BBE_CUDA_TRY(ensure_free_stream(b));
-    BBE_CUDA_TRY(cudaMallocAsync(&fresh, std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), b->free_stream));
+    BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&fresh), std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), b->free_stream));
     BBE_CUDA_TRY(cudaMemcpyAsync(fresh, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice,
                                  b->free_stream));
     BBE_CUDA_TRY(cudaStreamSynchronize(b->free_stream));
@@ -487,7 +523,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     add(4 * kGroups); add(4);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) e = cudaMallocAsync(&b->arena, bytes, s);
+    if (e == cudaSuccess) e = pool_alloc(&b->arena, bytes, s);
     if (e != cudaSuccess) {
         set_error(std::string("device allocation: ") + cudaGetErrorString(e));
         return fail(BBE_ERR_CUDA);
@@ -503,25 +539,28 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_prev = carve<float>(p, nt);
     b->d_queue = carve<int32_t>(p, kGroups);
     b->d_status = carve<int32_t>(p, 1);
-    struct Up {
-        void *dst;
-        const void *src;
-        size_t n;
+    // the arena's contents are assembled on the host in its own layout and go up in one copy
+    // (one transfer instead of one per array; the queue heads and status are reset before use)
+    std::vector<char> img(bytes, 0);
+    auto put = [&](const void *dst, const void *src, size_t n) {
+        std::memcpy(img.data() + (static_cast<const char *>(dst) - static_cast<const char *>(b->arena)), src, n);
     };
-    Up ups[] = {{d_off, off.data(), off.size() * 4},       {d_L, b->h_L.data(), size_t(n_races) * 4},
-               {d_R, b->h_R.data(), size_t(n_races) * 8}, {d_cr, comp_race.data(), size_t(nt) * 4},
-               {d_d0, b->h_d0.data(), size_t(nt) * 4},   {d_mu, b->h_mu.data(), size_t(nt) * 4},
-               {d_sigma, h_sigma.data(), size_t(nt) * 4}, {d_rho, h_rho.data(), size_t(nt) * 4},
-               {d_P, h_P.data(), size_t(nt) * 4},         {d_theta, h_theta.data(), size_t(nt) * 4}};
-    std::vector<Up> all(std::begin(ups), std::end(ups));
-    if (prev_step) all.push_back({d_prev, h_prev.data(), size_t(nt) * 4});
-    if (race_ids) all.push_back({d_ids, b->h_race_ids.data(), size_t(n_races) * 4});
-    for (auto &u : all) {
-        cudaError_t ce = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, s);
-        if (ce != cudaSuccess) {
-            set_error(std::string("staging upload: ") + cudaGetErrorString(ce));
-            return fail(BBE_ERR_CUDA);
-        }
+    put(d_off, off.data(), off.size() * 4);
+    put(d_L, b->h_L.data(), size_t(n_races) * 4);
+    put(d_R, b->h_R.data(), size_t(n_races) * 8);
+    put(d_cr, comp_race.data(), size_t(nt) * 4);
+    put(d_d0, b->h_d0.data(), size_t(nt) * 4);
+    put(d_mu, b->h_mu.data(), size_t(nt) * 4);
+    put(d_sigma, h_sigma.data(), size_t(nt) * 4);
+    put(d_rho, h_rho.data(), size_t(nt) * 4);
+    put(d_P, h_P.data(), size_t(nt) * 4);
+    put(d_theta, h_theta.data(), size_t(nt) * 4);
+    if (prev_step) put(d_prev, h_prev.data(), size_t(nt) * 4);
+    if (race_ids) put(d_ids, b->h_race_ids.data(), size_t(n_races) * 4);
+    e = cudaMemcpyAsync(b->arena, img.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        set_error(std::string("staging upload: ") + cudaGetErrorString(e));
+        return fail(BBE_ERR_CUDA);
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -739,7 +778,7 @@ bbe_status bbe_order_counts(bbe_batch *b, int32_t places, int32_t *order_counts,
         BBE_CUDA_TRY(free_behind_uses(b, b->d_order_off));
         b->d_order_off = nullptr;
         b->order_places = 0;
-        BBE_CUDA_TRY(cudaMallocAsync(&b->d_order_off, b->h_order_off.size() * sizeof(int64_t), s));
+        BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&b->d_order_off), b->h_order_off.size() * sizeof(int64_t), s));
         BBE_CUDA_TRY(cudaMemcpyAsync(b->d_order_off, b->h_order_off.data(), b->h_order_off.size() * sizeof(int64_t),
                                      cudaMemcpyHostToDevice, s));  // the host copy lives with the batch
         b->order_places = places;
@@ -775,7 +814,7 @@ bbe_status bbe_order_histogram(bbe_batch *b, int32_t places, uint64_t *keys, int
         BBE_CUDA_TRY(free_behind_uses(b, b->d_hist_off));
         b->d_hist_off = nullptr;
         b->hist_places = 0;
-        BBE_CUDA_TRY(cudaMallocAsync(&b->d_hist_off, off.size() * sizeof(int64_t), s));
+        BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&b->d_hist_off), off.size() * sizeof(int64_t), s));
         BBE_CUDA_TRY(cudaMemcpyAsync(b->d_hist_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         BBE_CUDA_TRY(cudaStreamSynchronize(s));  // `off` is pageable and goes out of scope
         b->h_hist_off = std::move(off);
@@ -930,7 +969,7 @@ bbe_status bbe_batch_set_law(bbe_batch *b, bbe_law law, const float *elapsed, co
         inv[r] = 1.0f / T[r];  // binary32 division, round to nearest
     }
     void *mem = nullptr;
-    BBE_CUDA_TRY(cudaMallocAsync(&mem, 2 * nr * sizeof(float), s));
+    BBE_CUDA_TRY(pool_alloc(&mem, 2 * nr * sizeof(float), s));
     float *d_t0 = static_cast<float *>(mem), *d_inv = d_t0 + nr;
     BBE_CUDA_TRY(cudaMemcpyAsync(d_t0, t0.data(), nr * sizeof(float), cudaMemcpyHostToDevice, s));
     BBE_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), nr * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -1104,7 +1143,7 @@ bbe_status bbe_batch_autotune(bbe_batch *b, int32_t *win_counts, double budget_m
             }
             if (st) break;
             int32_t *sc = nullptr;
-            if (cudaMallocAsync(&sc, d0.size() * sizeof(int32_t), s) != cudaSuccess) {
+            if (pool_alloc(reinterpret_cast<void **>(&sc), d0.size() * sizeof(int32_t), s) != cudaSuccess) {
                 set_error("autotune: scratch allocation failed");
                 st = BBE_ERR_CUDA;
                 bbe_destroy_batch(sub);

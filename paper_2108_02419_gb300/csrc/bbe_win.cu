@@ -1,5 +1,9 @@
 // bbe_win.cu -- the win-count rollout kernels of the position law of responsiveness, and the
 // library's entry points to the win-count rollout kernels (kernel code: bbe_win.cuh).
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "bbe_win.cuh"
 
 namespace bbe {
@@ -26,8 +30,22 @@ cudaError_t launch_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStrea
 
 int rollout_resident_blocks(int dist, int slots_per_lane, int block)
 {
+    // the occupancy of a (device, distribution, layout, block size) does not change: asked once
+    static std::mutex mu;
+    static std::map<std::array<int, 4>, int> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    const std::array<int, 4> key{dev, dist, slots_per_lane, block};
+    {
+        std::lock_guard<std::mutex> g(mu);
+        const auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
     win::resident_time_law(dist, slots_per_lane, block);  // sets the time-law kernels' shared-memory limit too
-    return win::resident_position_law(dist, slots_per_lane, block);
+    const int nb = win::resident_position_law(dist, slots_per_lane, block);
+    std::lock_guard<std::mutex> g(mu);
+    known[key] = nb;
+    return nb;
 }
 
 }  // namespace bbe

@@ -2,6 +2,10 @@
 // rollout runs to the K-th finisher for bbe_place_counts, bbe_order_counts and
 // bbe_order_histogram (position law of responsiveness only); a translation unit of its own so
 // that the build compiles the three kernel families in parallel.
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "bbe_win.cuh"
 
 namespace bbe {
@@ -13,7 +17,21 @@ cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cud
 
 int place_resident_blocks(int dist, int slots_per_lane, int block, int place_cells)
 {
-    return win::resident_law<BBE_LAW_POSITION, 1>(dist, slots_per_lane, block, place_cells);
+    // asked once per (device, distribution, layout, block size, place table size)
+    static std::mutex mu;
+    static std::map<std::array<int, 5>, int> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    const std::array<int, 5> key{dev, dist, slots_per_lane, block, place_cells};
+    {
+        std::lock_guard<std::mutex> g(mu);
+        const auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
+    const int nb = win::resident_law<BBE_LAW_POSITION, 1>(dist, slots_per_lane, block, place_cells);
+    std::lock_guard<std::mutex> g(mu);
+    known[key] = nb;
+    return nb;
 }
 
 }  // namespace bbe
