@@ -193,7 +193,7 @@ struct bbe_batch {
     int64_t *g_steps = nullptr;
 
     // Streams that carried work reading this batch, each with an event recorded after its
-    // latest use.  The batch's device memory comes from the stream-ordered allocator and is
+    // latest use.  The batch's device memory comes from the library's stream-ordered pool and is
     // freed on `free_stream` behind those events, so replacing a buffer or destroying the batch
     // waits for this batch's own work only, never for the whole device.
     mutable std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
