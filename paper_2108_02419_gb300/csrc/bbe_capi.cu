@@ -334,12 +334,19 @@ cudaError_t enqueue_pass(const bbe_batch *b, int32_t *counts, int64_t *steps, cu
     return e;
 }
 
-bbe_status ensure_aux(bbe_batch *b)
+// The streams and events a pass needs, made on first need: the side stream and fork/join events
+// only for a pass of more than one layout group, the capture stream only for a captured graph.
+bbe_status ensure_aux(bbe_batch *b, bool capture = false)
 {
-    if (!b->capture_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
-    if (!b->side_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
-    if (!b->ev_fork) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-    if (!b->ev_join) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    int groups = 0;
+    for (int g = 0; g < kGroups; ++g) groups += b->n_items_v[g] > 0 ? 1 : 0;
+    if (capture && !b->capture_stream)
+        BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    if (groups > 1) {
+        if (!b->side_stream) BBE_CUDA_TRY(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
+        if (!b->ev_fork) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+        if (!b->ev_join) BBE_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    }
     return BBE_OK;
 }
 
@@ -347,7 +354,7 @@ bbe_status ensure_graph(bbe_batch *b, int32_t *counts, int64_t *steps)
 {
     if (b->gexec && b->g_counts == counts && b->g_steps == steps) return BBE_OK;
     free_graph(b);
-    bbe_status st = ensure_aux(b);
+    bbe_status st = ensure_aux(b, true);
     if (st) return st;
     BBE_CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_pass(b, counts, steps, b->capture_stream, b->side_stream);
