@@ -429,8 +429,10 @@ def run_surrogate(mode: str, dev, stream) -> dict:
             t_tr = timed(train)
             L = log.cpu().numpy()
             rows = float(gen.sizes().mean()) * B * nsteps
+            # the loss curve: the mean training loss over each tenth of the run
+            curve = [round(float(c.mean()), 5) for c in np.array_split(L, 10)]
             tr = {"train_steps": nsteps, "train_s": t_tr, "loss_first": float(L[:10].mean()),
-                  "loss_last": float(L[-10:].mean()), "train_states_per_s": nsteps * B / t_tr,
+                  "loss_last": float(L[-10:].mean()), "loss_curve_tenths": curve, "train_states_per_s": nsteps * B / t_tr,
                   "train_tflops": 3 * SURROGATE_FWD_FLOPS_PER_ROW * rows / t_tr / 1e12}
             if inputs == 14:
                 out.update(tr)
@@ -1114,7 +1116,8 @@ def surrogate_summary(sur):
     ref6 = sur.get("reference_1e6", {})
     five = sur.get("five_input", {})
     return {"train": {"states_per_s": r(sur.get("train_states_per_s")), "tflops": r(sur.get("train_tflops"), 3),
-                      "loss_last": r(sur.get("loss_last"), 3), "epochs": sur.get("epochs"), "states": sur.get("train_states")},
+                      "loss_last": r(sur.get("loss_last"), 3), "loss_curve_tenths": sur.get("loss_curve_tenths"),
+                      "epochs": sur.get("epochs"), "states": sur.get("train_states")},
             "gate": sur.get("gate", {}).get("chosen_14"),
             "network": dict(err(h.get("network", {})), vectors_per_s=r(sur.get("infer", {}).get("win_prob_vectors_per_s"))),
             "gated": dict(err(h.get("gated", {})), gated=h.get("gated", {}).get("gated"),
