@@ -569,6 +569,23 @@ def run_surrogate(mode: str, dev, stream) -> dict:
                                         "fallback_races": fr, "fallback_rollouts_mean": fro / max(fr, 1),
                                         "fallback_phase_s": {"stage": ft[0], "pilot": ft[1], "budget": ft[2],
                                                              "stage_topup": ft[3], "topup_and_finish": ft[4]}}
+        # the same queries with 3 % of them outside the training ranges (26 to 30 competitors
+        # against the trained 2 to 24), which the range check sends to Monte Carlo
+        n_oor = qrb.n_races * 3 // 100
+        oor = W.uneven_batch(seed=401, n_races=n_oor, n_lo=26, n_hi=30, rollouts=QUERY_ROLLOUTS)
+        mixed = W.concat([qrb.slice(0, qrb.n_races - n_oor), oor])
+        mb = bbe.Batch(mixed, stream=stream)
+        mp = torch.empty(mixed.n_total, dtype=torch.float32, device=dev)
+        mu8 = torch.empty(mixed.n_races, dtype=torch.uint8, device=dev)
+        bbe.bbe_surrogate_infer(s, mb.handle, mp, mu8, stream=stream)  # plans once per batch
+        t_m = timed(lambda: bbe.bbe_surrogate_infer(s, mb.handle, mp, mu8, stream=stream))
+        um = mu8.cpu().numpy()
+        out["infer_with_out_of_range"] = {"states": mixed.n_races, "planted_out_of_range": n_oor,
+                                          "out_of_range": int((um == 1).sum()),
+                                          "out_of_range_among_planted": int((um[-n_oor:] == 1).sum()),
+                                          "gated": int((um == 2).sum()), "s": t_m,
+                                          "win_prob_vectors_per_s": mixed.n_races / t_m}
+        mb.close()
         bbe.bbe_surrogate_set_fallback(s, 0)
         qb.close()
         # plain Monte Carlo at the query budget on a 20,000-query sample of the same stream
@@ -1129,6 +1146,9 @@ def surrogate_summary(sur):
             "mc_at_query_rollouts": dict(err(h.get("mc_at_query_rollouts", {})),
                                          vectors_per_s=r(sur.get("mc_at_query_rollouts", {}).get("win_prob_vectors_per_s"))),
             "gain_gated_two_stage_vs_mc": r(sur.get("gain_gated_two_stage_vs_mc_at_query_rollouts"), 3),
+            "with_3pct_out_of_range": {k: (r(v) if isinstance(v, float) else v) for k, v in
+                                       sur.get("infer_with_out_of_range", {}).items()
+                                       if k in ("out_of_range", "planted_out_of_range", "win_prob_vectors_per_s")},
             "vs_1e6_rollouts": {k: r(v.get("max_abs"), 3) for k, v in ref6.items() if isinstance(v, dict)},
             "five_input": {"network": err(five.get("network", {})), "answered": err(five.get("answered", {})),
                            "gate": five.get("gate"), "gated_share": r(five.get("gated_share"), 3)}}
