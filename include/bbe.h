@@ -218,9 +218,9 @@ BBE_API bbe_status bbe_order_table_size(const bbe_batch *batch, int32_t places, 
  * table holds a power of two of entries, at least twice min(R_r, n_r!/(n_r-K_r)!), so a free
  * entry is always found (were none found, the batch status would report BBE_ERR_RANGE).
  * Asynchronous on cuda_stream (a call with a new `places` uploads the layout first).  Cut-off
- * rollouts count for nobody and set BBE_ERR_STEP_LIMIT.  Position-law batches only.  Errors:
- * BBE_ERR_ARG, BBE_ERR_RANGE (a race whose keys exceed 64 bits, named in bbe_last_error),
- * BBE_ERR_UNSUPPORTED (time-law batch), BBE_ERR_CUDA. */
+ * rollouts count for nobody and set BBE_ERR_STEP_LIMIT.  Either law of responsiveness.
+ * Errors: BBE_ERR_ARG, BBE_ERR_RANGE (a race whose keys exceed 64 bits, named in
+ * bbe_last_error), BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_order_histogram(bbe_batch *batch, int32_t places, uint64_t *keys, int32_t *counts,
                                        int32_t *place_counts, int64_t *steps_total, void *cuda_stream);
 
@@ -322,7 +322,8 @@ BBE_API bbe_status bbe_bettor_predictions(const bbe_batch *src, int32_t race, co
  *   cuda_stream stream for the copies; the call synchronises it before returning.
  * bbe_rollout_batch, bbe_race_trajectory and bbe_snapshot_batch (whose snapshots carry
  * elapsed = t0 + the snapshot's step and the same horizon) follow the law.  Place and order
- * tallies and the surrogate take position-law batches only (BBE_ERR_UNSUPPORTED otherwise).  Errors: BBE_ERR_ARG (bad law, missing or invalid values),
+ * tallies and the order histogram follow it too; the surrogate takes position-law batches only
+ * (BBE_ERR_UNSUPPORTED otherwise).  Errors: BBE_ERR_ARG (bad law, missing or invalid values),
  * BBE_ERR_CUDA. */
 BBE_API bbe_status bbe_batch_set_law(bbe_batch *batch, bbe_law law, const float *elapsed, const float *horizon,
                                      void *cuda_stream);

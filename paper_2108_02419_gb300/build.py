@@ -30,6 +30,7 @@ UNITS = {
     "bbe_win.cu": ["--fmad=false"],
     "bbe_win_time.cu": ["--fmad=false"],
     "bbe_win_place.cu": ["--fmad=false"],
+    "bbe_win_place_time.cu": ["--fmad=false"],
     "bbe_noalloc.cu": ["--fmad=false"],
     "bbe_trajectory.cu": ["--fmad=false"],
     "bbe_surrogate.cu": [],

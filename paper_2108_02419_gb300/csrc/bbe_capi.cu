@@ -671,10 +671,6 @@ bbe_status run_place_mode(bbe_batch *b, int32_t places, int32_t *place_counts, i
                           int64_t *steps_total, cudaStream_t s, unsigned long long *hist_keys = nullptr,
                           int32_t *hist_counts = nullptr)
 {
-    if (b->dev.law != BBE_LAW_POSITION) {
-        set_error("place and order tallies take position-law batches only");
-        return BBE_ERR_UNSUPPORTED;
-    }
     if (place_counts)
         BBE_CUDA_TRY(cudaMemsetAsync(place_counts, 0, size_t(b->n_total) * size_t(places) * sizeof(int32_t), s));
     if (steps_total) BBE_CUDA_TRY(cudaMemsetAsync(steps_total, 0, size_t(b->n_races) * sizeof(int64_t), s));

@@ -1,7 +1,7 @@
 // bbe_win_place.cu -- the place-count rollout kernels (kernel code: bbe_win.cuh, MODE 1): every
 // rollout runs to the K-th finisher for bbe_place_counts, bbe_order_counts and
-// bbe_order_histogram (position law of responsiveness only); a translation unit of its own so
-// that the build compiles the three kernel families in parallel.
+// bbe_order_histogram; the position law's kernels here, the time law's in bbe_win_place_time.cu
+// (translation units of their own, so that the build compiles the kernel families in parallel).
 #include <array>
 #include <map>
 #include <mutex>
@@ -10,9 +10,15 @@
 
 namespace bbe {
 
+namespace win {
+cudaError_t launch_place_time_law(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream);
+int resident_place_time_law(int dist, int slots_per_lane, int block, int place_cells);
+}  // namespace win
+
 cudaError_t launch_place_rollout(const RolloutLaunch &l, int slots_per_lane, cudaStream_t stream)
 {
-    return win::launch_law<BBE_LAW_POSITION, 1>(l, slots_per_lane, stream);
+    return l.b.law == BBE_LAW_TIME ? win::launch_place_time_law(l, slots_per_lane, stream)
+                                   : win::launch_law<BBE_LAW_POSITION, 1>(l, slots_per_lane, stream);
 }
 
 int place_resident_blocks(int dist, int slots_per_lane, int block, int place_cells)
@@ -28,6 +34,7 @@ int place_resident_blocks(int dist, int slots_per_lane, int block, int place_cel
         const auto it = known.find(key);
         if (it != known.end()) return it->second;
     }
+    win::resident_place_time_law(dist, slots_per_lane, block, place_cells);  // sets its shared-memory limit too
     const int nb = win::resident_law<BBE_LAW_POSITION, 1>(dist, slots_per_lane, block, place_cells);
     std::lock_guard<std::mutex> g(mu);
     known[key] = nb;

@@ -128,13 +128,47 @@ def test_trajectories_and_snapshots(bbe):
         assert steps[rr] == wsteps
 
 
-def test_place_tallies_and_surrogate_refuse_the_time_law(bbe):
+@pytest.mark.parametrize("slots", [0, 1, 4])
+def test_places_orders_and_order_histogram_follow_the_time_law(bbe, slots):
+    # the place mode under the time law: place counts, dense ordered tallies and the full-order
+    # histogram of one pass each, against the oracle's dry-runs of the same law
+    rb = timed_batch(84, 24, n_lo=1, n_hi=9, rollouts=300, rem_lo=100.0, rem_hi=1500.0)
+    with bbe.Batch(rb) as b:
+        if slots:
+            b.set_cfg(slots_per_lane=slots)
+        pc, psteps = b.places(3)
+        orders, _, osteps = b.orders(2)
+        keys, hc, off, _, hsteps = b.order_histogram(32)
+        b.status()
+        pc, psteps, orders, osteps = (t.cpu().numpy() for t in (pc, psteps, orders, osteps))
+        keys, hc, hsteps = keys.cpu().numpy(), hc.cpu().numpy(), hsteps.cpu().numpy()
+    want_p, want_ps, st = oracle.batch_places(rb, 3)
+    assert st == 0 and np.array_equal(pc.ravel(), want_p.ravel()) and np.array_equal(psteps, want_ps)
+    want_o, want_os, st = oracle.batch_orders(rb, 2)
+    pos = 0
+    for r in range(rb.n_races):
+        n = int(rb.race_off[r + 1] - rb.race_off[r])
+        size = n ** min(2, n)
+        assert np.array_equal(orders[pos:pos + size], want_o[r]), r
+        pos += size
+    assert np.array_equal(osteps, want_os)
+    want_h, want_hs, st = oracle.batch_order_histograms(rb, 32)
+    assert st == 0 and np.array_equal(hsteps, want_hs)
+    for r in range(rb.n_races):
+        n = int(rb.race_off[r + 1] - rb.race_off[r])
+        k, c = keys[off[r]:off[r + 1]], hc[off[r]:off[r + 1]]
+        used = k != np.uint64(2 ** 64 - 1)
+        got = {tuple(int(x) for x in bbe.bbe_order_key_decode(n, 32, int(key))): int(v) for key, v in zip(k[used], c[used])}
+        assert got == dict(want_h[r]), r
+    # the law matters: the same batch under the position law places differently somewhere
+    pos_rb = W.uneven_batch(seed=84, n_races=24, n_lo=1, n_hi=9, rollouts=300, rem_lo=100.0, rem_hi=1500.0)
+    want_pos, _, _ = oracle.batch_places(pos_rb, 3)
+    assert not np.array_equal(want_pos.ravel(), want_p.ravel())
+
+
+def test_surrogate_refuses_the_time_law(bbe):
     rb = timed_batch(82, 8, rollouts=50)
     with bbe.Batch(rb) as b:
-        places = torch.empty((rb.n_total, 3), dtype=torch.int32, device="cuda")
-        with pytest.raises(bbe.BbeError) as ei:
-            bbe.bbe_place_counts(b.handle, 3, places)
-        assert ei.value.status == -2
         s = bbe.bbe_surrogate_create(0)
         try:
             out = torch.empty(rb.n_total, dtype=torch.float32, device="cuda")
