@@ -1,5 +1,6 @@
-// bbe_win.cuh -- the rollout kernel for win counts: the Section 3 dry-runs under Eq. 1, each
-// rollout run to its first finisher.
+// bbe_win.cuh -- the rollout kernel: the Section 3 dry-runs under Eq. 1, each rollout run to its
+// first finisher (win counts) or, in place mode, to its K-th (place counts, ordered tallies and
+// the finishing-order histogram).
 //
 // Layout.  A warp holds 32 V slots (V = 1..4 per lane; slot i = 32 v + lane, so the lanes of
 // one register hold consecutive slots).  A race of n competitors takes floor(32 V / n)
@@ -27,6 +28,13 @@
 // (within-step crossing time tau = (L - d) / S, slot) to its segment's minimum in shared
 // memory, which gives the least tau and, on equal tau, the lowest competitor index.  Wins are
 // tallied per competitor in shared memory and reach the global counts once per work item.
+// Place mode records each crossing with its key (sub-step, tau, slot) and places a block's
+// crossings at the block's end; a segment whose K-th place is filled ends its rollout, and its
+// places and order are tallied when it restarts.
+//
+// Loop bookkeeping.  After a block without a finish or a step-limit cut-off nothing can have
+// changed which slots run, so the warp's reduction of restart and liveness flags runs only after
+// blocks with one; a warp-uniform count-down rules out the step limit until a block could reach it.
 //
 // The arithmetic is the pinned binary32 round-to-nearest sequence of include/bbe.h (explicit
 // intrinsics, file compiled with --fmad=false), so the counts are bit-identical to any
