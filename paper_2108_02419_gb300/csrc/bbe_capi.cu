@@ -122,15 +122,37 @@ cudaError_t ensure_free_stream(bbe_batch *b)
     return b->free_stream ? cudaSuccess : cudaStreamCreateWithFlags(&b->free_stream, cudaStreamNonBlocking);
 }
 
-// Free `p` (stream-ordered allocation) on the batch's free stream once every recorded use of the
-// batch has completed; the host does not wait.
+// One stream per device on which the library releases batch memory (made once): each release
+// waits there for the events of its own batch's uses, so the host and the callers' streams never
+// wait, and no stream is made per batch.
+cudaError_t release_stream(cudaStream_t *out)
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = streams.find(dev);
+    if (it == streams.end()) {
+        cudaStream_t st = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        it = streams.emplace(dev, st).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
+}
+
+// Free `p` (stream-ordered allocation) once every recorded use of the batch has completed; the
+// host does not wait.
 cudaError_t free_behind_uses(bbe_batch *b, void *p)
 {
     if (!p) return cudaSuccess;
-    cudaError_t e = ensure_free_stream(b);
+    cudaStream_t rs = nullptr;
+    cudaError_t e = release_stream(&rs);
     for (auto &u : b->uses)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->free_stream, u.second, 0);
-    if (e == cudaSuccess) e = cudaFreeAsync(p, b->free_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, u.second, 0);
+    if (e == cudaSuccess) e = cudaFreeAsync(p, rs);
     return e;
 }
 
@@ -165,7 +187,7 @@ int slots_for(int n, int mode, const int8_t *by_n = nullptr, int dflt = 2)
     return n >= v ? v : std::min(n, 2);  // a layout wider than the race falls back
 }
 
-bbe_status build_items(bbe_batch *b)
+bbe_status build_items(bbe_batch *b, cudaStream_t upload = nullptr)
 {
     // Per race: full chunks of `chunk` rollouts (all of one cost) and a remainder.  The list puts
     // longer work first: full chunks race by race in descending cost per chunk, then the
@@ -257,14 +279,18 @@ bbe_status build_items(bbe_batch *b)
         b->n_items_v[g] = int32_t(sorted.size() - before);
     }
 
-    // the new list is in place before the call returns; the old one is freed behind this batch's
-    // work that may still read it
+    // the new list is in place before the call returns (uploaded on `upload`, the staging call's
+    // stream, else on the batch's free stream); the old one is freed behind this batch's work
+    // that may still read it
     bbe::WorkItem *fresh = nullptr;
-    BBE_CUDA_TRY(ensure_free_stream(b));
-    BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&fresh), std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), b->free_stream));
+    if (!upload) {
+        BBE_CUDA_TRY(ensure_free_stream(b));
+        upload = b->free_stream;
+    }
+    BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&fresh), std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), upload));
     BBE_CUDA_TRY(cudaMemcpyAsync(fresh, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice,
-                                 b->free_stream));
-    BBE_CUDA_TRY(cudaStreamSynchronize(b->free_stream));
+                                 upload));
+    BBE_CUDA_TRY(cudaStreamSynchronize(upload));
     free_graph(b);
     BBE_CUDA_TRY(free_behind_uses(b, b->d_items));
     b->d_items = fresh;
@@ -580,7 +606,7 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     b->cfg = bbe_launch_cfg{kDefaultWarpsPerBlock, kDefaultBlocksPerSm, kDefaultRolloutsPerLane, BBE_MAX_STEPS_DEFAULT, 0};
     for (int g = 0; g < kGroups; ++g)
         b->resident[g] = bbe::rollout_resident_blocks(b->dist, kSlots[g], 32 * kDefaultWarpsPerBlock);
-    if ((st = build_items(b))) return fail(st);
+    if ((st = build_items(b, s))) return fail(st);
     *out = b;
     return BBE_OK;
 }

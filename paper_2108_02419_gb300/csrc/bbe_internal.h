@@ -194,10 +194,10 @@ struct bbe_batch {
 
     // Streams that carried work reading this batch, each with an event recorded after its
     // latest use.  The batch's device memory comes from the library's stream-ordered pool and is
-    // freed on `free_stream` behind those events, so replacing a buffer or destroying the batch
-    // waits for this batch's own work only, never for the whole device.
+    // freed on the library's release stream behind those events, so replacing a buffer or
+    // destroying the batch waits for this batch's own work only, never for the whole device.
     mutable std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
-    cudaStream_t free_stream = nullptr;
+    cudaStream_t free_stream = nullptr;  // uploads of a rebuilt work list (made on first need)
 };
 
 
