@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libbbe.so")
+# BBE_LIB may name another build of the library (the checked build: build.build(checked=True))
+LIB_PATH = os.environ.get("BBE_LIB") or os.path.join(_HERE, "_lib", "libbbe.so")
 
 BBE_OK = 0
 STATUS_NAMES = {0: "BBE_OK", -1: "BBE_ERR_ARG", -2: "BBE_ERR_UNSUPPORTED", -3: "BBE_ERR_FINISHED",

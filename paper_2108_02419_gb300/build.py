@@ -4,6 +4,11 @@ Each translation unit is compiled in parallel and linked into
 ``paper_2108_02419_gb300/_lib/libbbe.so``.  The rollout translation units are compiled with
 ``--fmad=false``: the rollout arithmetic is pinned to explicit round-to-nearest
 intrinsics and nothing may be contracted behind its back.
+
+``build(checked=True)`` makes the checked build, ``_lib/checked/libbbe.so``: the same sources
+with ``BBE_CHECKED`` defined, so that the rollout kernels check their computed indices and record
+a failed check in the batch status instead of accessing out of range (the stand-in for a memory
+checker).  The binding loads it when ``BBE_LIB`` names it.
 """
 from __future__ import annotations
 
@@ -55,22 +60,26 @@ def _inputs_digest() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libbbe.so if any source changed. Returns the library path."""
-    os.makedirs(LIBDIR, exist_ok=True)
-    digest = _inputs_digest()
-    stamp = os.path.join(LIBDIR, "build.stamp")
-    if not force and os.path.exists(SO) and os.path.exists(stamp):
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link libbbe.so (or the checked build) if any source changed. Returns the
+    library path."""
+    libdir = os.path.join(LIBDIR, "checked") if checked else LIBDIR
+    so = os.path.join(libdir, "libbbe.so")
+    flags = ["-DBBE_CHECKED=1"] if checked else []
+    os.makedirs(libdir, exist_ok=True)
+    digest = _inputs_digest() + ("+checked" if checked else "")
+    stamp = os.path.join(libdir, "build.stamp")
+    if not force and os.path.exists(so) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
-                return SO
+                return so
     cc = nvcc()
     objs = []
 
     def compile_unit(item):
         name, extra = item
-        obj = os.path.join(LIBDIR, name.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, name), "-o", obj]
+        obj = os.path.join(libdir, name.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *COMMON, *flags, *extra, "-c", os.path.join(CSRC, name), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -82,18 +91,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS.items()))
-    tmp = SO + f".tmp{os.getpid()}"
+    tmp = so + f".tmp{os.getpid()}"
     res = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"],
                          capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, SO)
+    os.replace(tmp, so)
     with open(stamp, "w") as f:
         f.write(digest)
-    return SO
+    return so
 
 
 if __name__ == "__main__":
     import sys
 
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -1024,6 +1024,10 @@ bbe_status bbe_batch_status(bbe_batch *b, void *cuda_stream)
     int32_t flags = 0;
     BBE_CUDA_TRY(cudaMemcpyAsync(&flags, b->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     BBE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags & bbe::kStatusBadIndex) {
+        set_error("a device index check failed (checked build)");
+        return BBE_ERR_RANGE;
+    }
     if (flags & bbe::kStatusTableFull) {
         set_error("a finishing-order hash table had no free entry");
         return BBE_ERR_RANGE;

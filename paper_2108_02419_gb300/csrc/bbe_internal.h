@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -88,8 +89,31 @@ inline void fill_round_keys(RolloutLaunch &l)
 // Device status bits written by the kernels.
 constexpr int32_t kStatusStepLimit = 1;
 constexpr int32_t kStatusTableFull = 2;  // a finishing-order hash table had no free entry
+constexpr int32_t kStatusBadIndex = 4;   // checked build: a device index check failed
+
+// BBE_INDEX(i, n, status): the index i of an array of n entries.  The checked build (BBE_CHECKED
+// defined; build.build(checked=True)) tests 0 <= i < n, and on failure records kStatusBadIndex in
+// the status word and uses index 0 instead, so no access leaves its array; other builds use i
+// as it is, with no code added.
+#if defined(BBE_CHECKED) && BBE_CHECKED
+#define BBE_INDEX(i, n, status) ::bbe::checked_index((i), (n), (status))
+#else
+#define BBE_INDEX(i, n, status) (i)
+#endif
 
 #ifdef __CUDACC__
+template <typename I, typename N>
+__device__ __forceinline__ I checked_index(I i, N n, int32_t *status)
+{
+    bool bad = int64_t(i) >= int64_t(n);
+    if constexpr (std::is_signed<I>::value) bad = bad || i < I(0);
+    if (bad) {
+        atomicOr(status, kStatusBadIndex);
+        return I(0);
+    }
+    return i;
+}
+
 // One count for `key` in a hash table of `cap` entries (a power of two, at least twice the keys
 // it will hold, so a free entry is always found): MurmurHash3's 64-bit finaliser (Appleby)
 // picks the first entry, linear probing the next ones; an entry is claimed by compare-and-swap

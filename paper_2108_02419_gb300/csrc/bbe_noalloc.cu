@@ -283,6 +283,10 @@ extern "C" BBE_API bbe_status bbe_rollout_noalloc(int32_t n_races, int32_t n_com
     int32_t status = 0;
     NA_TRY(cudaMemcpyAsync(&status, &sc->h.status, sizeof(status), cudaMemcpyDeviceToHost, s));
     NA_TRY(cudaStreamSynchronize(s));
+    if (status & bbe::kStatusBadIndex) {
+        bbe::set_error("bbe_rollout_noalloc: a device index check failed (checked build)");
+        return BBE_ERR_RANGE;
+    }
     if (status & bbe::kStatusStepLimit) {
         bbe::set_error("bbe_rollout_noalloc: a rollout reached max_steps without a finisher");
         return BBE_ERR_STEP_LIMIT;

@@ -147,9 +147,10 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         it = __shfl_sync(kAll, it, 0);
         if (it >= l.n_items) break;
         const WorkItem w = l.items[it];
-        const int r = w.race;
+        const int r = BBE_INDEX(w.race, b.n_races, l.status);
         const int off = b.race_off[r];
-        const int n = b.race_off[r + 1] - off;
+        const int n = BBE_INDEX(b.race_off[r + 1] - off - 1, 32, l.status) + 1;  // 1..32
+        (void)BBE_INDEX(off + n - 1, b.n_total, l.status);
         const int nseg = l.seg_cap > 0 ? min(NS / n, l.seg_cap) : NS / n;  // segments of this warp
 
         // stage the race: lane j < n loads competitor j (coalesced) and ranks it by (d0, j)
@@ -172,7 +173,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
         }
         if (lane < n) {
             st.rank0[lane] = rank;
-            st.byrank0[rank] = lane;
+            st.byrank0[BBE_INDEX(rank, 32, l.status)] = lane;
         }
         for (int i = lane; i < NS; i += 32) {
             st.key[i] = kNoKey;
@@ -232,9 +233,9 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             d[v] = st.d0[c];
             pv[v] = st.prev0[c];
             const int r0 = st.rank0[c];
-            fo[v] = (used && r0 + 1 < n) ? (sb[v] + st.byrank0[r0 + 1]) * int(sizeof(float2)) : kSent;
+            fo[v] = (used && r0 + 1 < n) ? BBE_INDEX(sb[v] + st.byrank0[r0 + 1], NS, l.status) * int(sizeof(float2)) : kSent;
             if (alive[v]) {
-                st.order[sb[v] + r0] = slot;
+                st.order[BBE_INDEX(sb[v] + r0, NS, l.status)] = slot;
                 st.rnk[slot] = r0;
             }
         }
@@ -261,7 +262,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                         const bool lower = ((rk[v] ^ ph) & 1) == 0;
                         const int pr = lower ? rk[v] + 1 : rk[v] - 1;
                         if (alive[v] && pr >= 0 && pr < n) {
-                            const int ps = st.order[sb[v] + pr];
+                            const int ps = BBE_INDEX(st.order[BBE_INDEX(sb[v] + pr, NS, l.status)], NS, l.status);
                             const float pd = row[ps].x;
                             const bool inv = lower ? (d[v] > pd || (d[v] == pd && slot > ps))
                                                    : (pd > d[v] || (pd == d[v] && ps > slot));
@@ -275,7 +276,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         rk[v] = nr[v];
-                        if (alive[v]) st.order[sb[v] + nr[v]] = 32 * v + lane;
+                        if (alive[v]) st.order[BBE_INDEX(sb[v] + nr[v], NS, l.status)] = 32 * v + lane;
                     }
                     __syncwarp();
                 }
@@ -285,13 +286,15 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             for (int v = 0; v < V; ++v) {
                 if (!alive[v]) continue;
                 st.rnk[32 * v + lane] = rk[v];
-                fo[v] = rk[v] + 1 < n ? st.order[sb[v] + rk[v] + 1] * int(sizeof(float2)) : kSent;
+                fo[v] = rk[v] + 1 < n ? BBE_INDEX(st.order[BBE_INDEX(sb[v] + rk[v] + 1, NS, l.status)], NS, l.status) *
+                                            int(sizeof(float2))
+                                      : kSent;
                 float2 f = *reinterpret_cast<const float2 *>(pb + fo[v]);
                 if (!(f.x > d[v])) {
                     // level with the successor: the first later rank strictly in front, if any
                     f = make_float2(INFINITY, INFINITY);
                     for (int q = rk[v] + 2; q < n; ++q) {
-                        const float2 g = row[st.order[sb[v] + q]];
+                        const float2 g = row[BBE_INDEX(st.order[BBE_INDEX(sb[v] + q, NS, l.status)], NS, l.status)];
                         if (g.x > d[v]) {
                             f = g;
                             break;
@@ -315,7 +318,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             for (int v = 0; v < V; ++v) {
                 rk[v] = alive[v] ? st.rnk[32 * v + lane] : 0;
                 init[v] = alive[v] && fd[v] < d[v];
-                if (init[v]) st.flag[sb[v] + rk[v]] = 1;
+                if (init[v]) st.flag[BBE_INDEX(sb[v] + rk[v], NS, l.status)] = 1;
             }
             __syncwarp();
             bool ok[V];
@@ -329,7 +332,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                 st.flag[sb[v] + rk[v]] = 0;
                 if (ok[v]) {
                     const int slot = 32 * v + lane;
-                    const int f = st.order[sb[v] + rk[v] + 1];
+                    const int f = BBE_INDEX(st.order[BBE_INDEX(sb[v] + rk[v] + 1, NS, l.status)], NS, l.status);
                     st.order[sb[v] + rk[v]] = f;
                     st.order[sb[v] + rk[v] + 1] = slot;
                     st.rnk[f] = rk[v];
@@ -342,7 +345,8 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             for (int v = 0; v < V; ++v) {
                 if (!alive[v]) continue;
                 const int r1 = st.rnk[32 * v + lane] + 1;
-                fo[v] = r1 < n ? st.order[sb[v] + r1] * int(sizeof(float2)) : kSent;
+                fo[v] = r1 < n ? BBE_INDEX(st.order[BBE_INDEX(sb[v] + r1, NS, l.status)], NS, l.status) * int(sizeof(float2))
+                               : kSent;
                 const float2 f = *reinterpret_cast<const float2 *>(pb + fo[v]);
                 fd[v] = f.x;
                 fp[v] = f.y;
@@ -384,7 +388,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                     for (int v = 0; v < V; ++v) {
                         won[v] = fk[v] != kNoKey && st.key[sb[v]] == fk[v];
                         if (won[v]) {
-                            const int p = pl_n[sb[v]];
+                            const int p = BBE_INDEX(pl_n[sb[v]], n, l.status);
                             pl_ord[sb[v] + p] = 32 * v + lane - sb[v];
                             pl_n[sb[v]] = p + 1;
                             if (p == K - 1) pl_kj[sb[v]] = int(fk[v] >> 40);
@@ -430,7 +434,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             for (int v = 0; v < V; ++v) {
                 if (!pend[v] || pl_n[sb[v]] < K) continue;
                 const int c = 32 * v + lane - sb[v];  // this slot's competitor
-                if (c < K) atomicAdd(&pl_cnt[pl_ord[sb[v] + c] * K + c], 1);
+                if (c < K) atomicAdd(&pl_cnt[BBE_INDEX(pl_ord[sb[v] + c] * K + c, n * K, l.status)], 1);
                 if (c == 0 && (l.orders != nullptr || l.hist_keys != nullptr)) {
                     unsigned code = 0u, taken = 0u;
                     unsigned long long key = 0ull;
@@ -440,7 +444,13 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                         key = key * unsigned(n - j) + unsigned(__popc(((1u << cj) - 1u) & ~taken));
                         taken |= 1u << cj;
                     }
-                    if (l.orders != nullptr) atomicAdd(&l.orders[l.order_off[r] + code], 1);
+                    if (l.orders != nullptr) {
+#if defined(BBE_CHECKED) && BBE_CHECKED
+                        unsigned cells = 1u;  // n^K entries in the race's dense table
+                        for (int j = 0; j < K; ++j) cells *= unsigned(n);
+#endif
+                        atomicAdd(&l.orders[l.order_off[r] + BBE_INDEX(code, cells, l.status)], 1);
+                    }
                     if (l.hist_keys != nullptr) {
                         const int64_t h0 = l.hist_off[r];
                         hist_insert(l.hist_keys + h0, l.hist_counts + h0, l.hist_off[r + 1] - h0, key, l.status);
@@ -482,7 +492,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
             bool bad = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float2 f = *reinterpret_cast<const float2 *>(posb + BO + fo[v]);
+                const float2 f = *reinterpret_cast<const float2 *>(posb + BO + BBE_INDEX(fo[v], kSent + 1, l.status));
                 fd[v] = f.x;
                 fp[v] = f.y;
                 bad |= alive[v] && !(f.x > d[v]);
@@ -554,7 +564,7 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                         const unsigned long long kw = st.key[sb[v]];
                         if (kw != kNoKey) {
                             const int slot = 32 * v + lane;
-                            if (int(unsigned(kw)) == slot) atomicAdd(&st.wins[slot - sb[v]], 1);
+                            if (int(unsigned(kw)) == slot) atomicAdd(&st.wins[BBE_INDEX(slot - sb[v], 32, l.status)], 1);
                             alive[v] = false;
                             pend[v] = true;
                             if (slot == sb[v]) steps += (unsigned long long)(blk[v] * 4u + unsigned(J) + 1u);
