@@ -329,7 +329,9 @@ BBE_API bbe_status bbe_batch_set_law(bbe_batch *batch, bbe_law law, const float 
                                      void *cuda_stream);
 
 /* bbe_batch_status -- synchronise cuda_stream and return the batch's device status from
- * the last bbe_rollout_batch or bbe_place_counts: BBE_OK, BBE_ERR_STEP_LIMIT, or
+ * the last bbe_rollout_batch, bbe_place_counts, bbe_order_counts or bbe_order_histogram:
+ * BBE_OK, BBE_ERR_STEP_LIMIT, BBE_ERR_RANGE (an order hash table without a free entry, which
+ * its sizing rules out, or, in the checked build, a failed device index check), or
  * BBE_ERR_CUDA if the stream reported an error. */
 BBE_API bbe_status bbe_batch_status(bbe_batch *batch, void *cuda_stream);
 
