@@ -187,6 +187,29 @@ int slots_for(int n, int mode, const int8_t *by_n = nullptr, int dflt = 2)
     return n >= v ? v : std::min(n, 2);  // a layout wider than the race falls back
 }
 
+// A run of `count` work items of one race, each of `chunk` rollouts, the first from rollout
+// k0 on; `first` is the run's first index in the list.
+struct ItemRun {
+    int32_t race, k0, chunk, count, first, pad;
+};
+
+// items[i] for every list index i: the run holding i (the last whose first index is at most i,
+// by binary search over the runs in list order), then its item i - first.
+__global__ void expand_items(const ItemRun *__restrict__ runs, int32_t n_runs, int32_t total,
+                             bbe::WorkItem *__restrict__ items)
+{
+    const int32_t i = int32_t(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= total) return;
+    int32_t lo = 0, hi = n_runs - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (runs[mid].first <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const ItemRun r = runs[lo];
+    items[i] = bbe::WorkItem{r.race, r.k0 + (i - r.first) * r.chunk, r.chunk, 0};
+}
+
 bbe_status build_items(bbe_batch *b, cudaStream_t upload = nullptr)
 {
     // Per race: full chunks of `chunk` rollouts (all of one cost) and a remainder.  The list puts
@@ -263,33 +286,46 @@ bbe_status build_items(bbe_batch *b, cudaStream_t upload = nullptr)
         set_error("work list too long; raise rollouts_per_lane");
         return BBE_ERR_RANGE;
     }
-    std::vector<bbe::WorkItem> sorted;
-    sorted.reserve(total);
+    // the list as runs of equal items (a race's full chunks, then its remainder), expanded into
+    // items on the device: a few bytes per race cross the bus instead of 16 per item
+    std::vector<ItemRun> runs;
+    runs.reserve(size_t(2) * size_t(b->n_races));
+    int32_t listed = 0;
     for (int g = 0; g < kGroups; ++g) {
         std::vector<RacePlan> &pg = plans[g];
-        const size_t before = sorted.size();
+        const int32_t before = listed;
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_full > y.cost_full; });
-        for (const RacePlan &pl : pg)
-            for (int64_t i = 0; i < pl.full; ++i)
-                sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.k0 + i * pl.chunk), int32_t(pl.chunk), 0});
+        for (const RacePlan &pl : pg) {
+            if (pl.full == 0) continue;
+            runs.push_back(ItemRun{pl.race, int32_t(pl.k0), int32_t(pl.chunk), int32_t(pl.full), listed, 0});
+            listed += int32_t(pl.full);
+        }
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_rem > y.cost_rem; });
-        for (const RacePlan &pl : pg)
-            if (pl.rem > 0)
-                sorted.push_back(bbe::WorkItem{pl.race, int32_t(pl.k0 + pl.full * pl.chunk), int32_t(pl.rem), 0});
-        b->n_items_v[g] = int32_t(sorted.size() - before);
+        for (const RacePlan &pl : pg) {
+            if (pl.rem == 0) continue;
+            runs.push_back(ItemRun{pl.race, int32_t(pl.k0 + pl.full * pl.chunk), int32_t(pl.rem), 1, listed, 0});
+            listed += 1;
+        }
+        b->n_items_v[g] = listed - before;
     }
 
-    // the new list is in place before the call returns (uploaded on `upload`, the staging call's
+    // the new list is in place before the call returns (made on `upload`, the staging call's
     // stream, else on the batch's free stream); the old one is freed behind this batch's work
     // that may still read it
     bbe::WorkItem *fresh = nullptr;
+    ItemRun *d_runs = nullptr;
     if (!upload) {
         BBE_CUDA_TRY(ensure_free_stream(b));
         upload = b->free_stream;
     }
-    BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&fresh), std::max<size_t>(1, sorted.size()) * sizeof(bbe::WorkItem), upload));
-    BBE_CUDA_TRY(cudaMemcpyAsync(fresh, sorted.data(), sorted.size() * sizeof(bbe::WorkItem), cudaMemcpyHostToDevice,
-                                 upload));
+    BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&fresh), std::max<size_t>(1, size_t(listed)) * sizeof(bbe::WorkItem), upload));
+    if (!runs.empty()) {
+        BBE_CUDA_TRY(pool_alloc(reinterpret_cast<void **>(&d_runs), runs.size() * sizeof(ItemRun), upload));
+        BBE_CUDA_TRY(cudaMemcpyAsync(d_runs, runs.data(), runs.size() * sizeof(ItemRun), cudaMemcpyHostToDevice, upload));
+        expand_items<<<unsigned((listed + 255) / 256), 256, 0, upload>>>(d_runs, int32_t(runs.size()), listed, fresh);
+        BBE_CUDA_TRY(cudaGetLastError());
+        BBE_CUDA_TRY(cudaFreeAsync(d_runs, upload));
+    }
     BBE_CUDA_TRY(cudaStreamSynchronize(upload));
     free_graph(b);
     BBE_CUDA_TRY(free_behind_uses(b, b->d_items));
