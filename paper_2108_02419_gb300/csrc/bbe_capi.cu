@@ -80,6 +80,8 @@ bbe_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s, con
 // pool hands freed memory back at once, and mapping it again costs ~90 us per batch); it is
 // never the process's default pool, whose settings other libraries may rely on.
 constexpr uint64_t kPoolKeep = uint64_t(256) << 20;
+// Arenas up to this size are uploaded in one copy from a host image of the arena.
+constexpr size_t kOneCopyBytes = size_t(4) << 20;
 
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s)
 {
@@ -187,10 +189,10 @@ int slots_for(int n, int mode, const int8_t *by_n = nullptr, int dflt = 2)
     return n >= v ? v : std::min(n, 2);  // a layout wider than the race falls back
 }
 
-// A run of `count` work items of one race, each of `chunk` rollouts, the first from rollout
-// k0 on; `first` is the run's first index in the list.
+// A run of work items of one race, each of `chunk` rollouts, the first from rollout k0 on;
+// `first` is the run's first index in the list (the run ends where the next one starts).
 struct ItemRun {
-    int32_t race, k0, chunk, count, first, pad;
+    int32_t race, k0, chunk, first;
 };
 
 // items[i] for every list index i: the run holding i (the last whose first index is at most i,
@@ -287,7 +289,7 @@ bbe_status build_items(bbe_batch *b, cudaStream_t upload = nullptr)
         return BBE_ERR_RANGE;
     }
     // the list as runs of equal items (a race's full chunks, then its remainder), expanded into
-    // items on the device: a few bytes per race cross the bus instead of 16 per item
+    // items on the device: 16 bytes per run cross the bus instead of 16 per item
     std::vector<ItemRun> runs;
     runs.reserve(size_t(2) * size_t(b->n_races));
     int32_t listed = 0;
@@ -297,13 +299,13 @@ bbe_status build_items(bbe_batch *b, cudaStream_t upload = nullptr)
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_full > y.cost_full; });
         for (const RacePlan &pl : pg) {
             if (pl.full == 0) continue;
-            runs.push_back(ItemRun{pl.race, int32_t(pl.k0), int32_t(pl.chunk), int32_t(pl.full), listed, 0});
+            runs.push_back(ItemRun{pl.race, int32_t(pl.k0), int32_t(pl.chunk), listed});
             listed += int32_t(pl.full);
         }
         std::stable_sort(pg.begin(), pg.end(), [](const RacePlan &x, const RacePlan &y) { return x.cost_rem > y.cost_rem; });
         for (const RacePlan &pl : pg) {
             if (pl.rem == 0) continue;
-            runs.push_back(ItemRun{pl.race, int32_t(pl.k0 + pl.full * pl.chunk), int32_t(pl.rem), 1, listed, 0});
+            runs.push_back(ItemRun{pl.race, int32_t(pl.k0 + pl.full * pl.chunk), int32_t(pl.rem), listed});
             listed += 1;
         }
         b->n_items_v[g] = listed - before;
@@ -608,28 +610,34 @@ bbe_status bbe::stage_batch(bbe_batch **out, int32_t n_races, const int32_t *rac
     float *d_prev = carve<float>(p, nt);
     b->d_queue = carve<int32_t>(p, kGroups);
     b->d_status = carve<int32_t>(p, 1);
-    // the arena's contents are assembled on the host in its own layout and go up in one copy
-    // (one transfer instead of one per array; the queue heads and status are reset before use)
-    std::vector<char> img(bytes, 0);
-    auto put = [&](const void *dst, const void *src, size_t n) {
-        std::memcpy(img.data() + (static_cast<const char *>(dst) - static_cast<const char *>(b->arena)), src, n);
+    // A small batch's arena is assembled on the host in its own layout and goes up in one copy
+    // (one transfer's overhead instead of one per array); a large one goes up array by array,
+    // with no extra host pass over it.  The queue heads and status are reset before use.
+    struct Up {
+        void *dst;
+        const void *src;
+        size_t n;
     };
-    put(d_off, off.data(), off.size() * 4);
-    put(d_L, b->h_L.data(), size_t(n_races) * 4);
-    put(d_R, b->h_R.data(), size_t(n_races) * 8);
-    put(d_cr, comp_race.data(), size_t(nt) * 4);
-    put(d_d0, b->h_d0.data(), size_t(nt) * 4);
-    put(d_mu, b->h_mu.data(), size_t(nt) * 4);
-    put(d_sigma, h_sigma.data(), size_t(nt) * 4);
-    put(d_rho, h_rho.data(), size_t(nt) * 4);
-    put(d_P, h_P.data(), size_t(nt) * 4);
-    put(d_theta, h_theta.data(), size_t(nt) * 4);
-    if (prev_step) put(d_prev, h_prev.data(), size_t(nt) * 4);
-    if (race_ids) put(d_ids, b->h_race_ids.data(), size_t(n_races) * 4);
-    e = cudaMemcpyAsync(b->arena, img.data(), bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-        set_error(std::string("staging upload: ") + cudaGetErrorString(e));
-        return fail(BBE_ERR_CUDA);
+    std::vector<Up> ups = {{d_off, off.data(), off.size() * 4},       {d_L, b->h_L.data(), size_t(n_races) * 4},
+                           {d_R, b->h_R.data(), size_t(n_races) * 8}, {d_cr, comp_race.data(), size_t(nt) * 4},
+                           {d_d0, b->h_d0.data(), size_t(nt) * 4},   {d_mu, b->h_mu.data(), size_t(nt) * 4},
+                           {d_sigma, h_sigma.data(), size_t(nt) * 4}, {d_rho, h_rho.data(), size_t(nt) * 4},
+                           {d_P, h_P.data(), size_t(nt) * 4},         {d_theta, h_theta.data(), size_t(nt) * 4}};
+    if (prev_step) ups.push_back({d_prev, h_prev.data(), size_t(nt) * 4});
+    if (race_ids) ups.push_back({d_ids, b->h_race_ids.data(), size_t(n_races) * 4});
+    std::vector<char> img;
+    if (bytes <= kOneCopyBytes) {
+        img.assign(bytes, 0);
+        for (const Up &u : ups)
+            std::memcpy(img.data() + (static_cast<const char *>(u.dst) - static_cast<const char *>(b->arena)), u.src, u.n);
+        ups.assign(1, Up{b->arena, img.data(), bytes});
+    }
+    for (const Up &u : ups) {
+        e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            set_error(std::string("staging upload: ") + cudaGetErrorString(e));
+            return fail(BBE_ERR_CUDA);
+        }
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
