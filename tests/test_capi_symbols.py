@@ -51,3 +51,15 @@ def test_binding_refuses_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(bbe, "_lib", None)
     with pytest.raises(ImportError):
         bbe.lib()
+
+
+def test_checked_build_compiles_and_exports_every_declared_symbol():
+    # the checked build (every device index of the rollout kernels tested) compiles here without
+    # a GPU and offers the same entry points; its GPU run is tests/test_gpu_checked_build.py
+    from paper_2108_02419_gb300 import build
+
+    so = build.build(checked=True)
+    assert os.path.dirname(so).endswith(os.path.join("_lib", "checked"))
+    lib = ctypes.CDLL(so)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
