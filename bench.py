@@ -782,6 +782,24 @@ def run_population(dev, stream, bettors: int = 1000, dry_runs: int = 50) -> dict
                                **{name: float((pr[:, i] == pooled.argmax(axis=1)).mean())
                                   for i, name in enumerate(("LW", "UD(3)", "LinEx(10)", "ZI"))}},
     })
+    # the live use (Section 6: every bettor re-evaluates at each step): one snapshot's bettors
+    # alone, the race's positions at the middle snapshot, `bettors` races of `dry_runs` rollouts on
+    # the bettors' own streams; device time of the rollouts and probabilities, and end to end
+    # from host buffers
+    s_mid = max(1, n_snap // 2)
+    snap = W.from_arrays([rb.n_total] * bettors, float(rb.L[0]), dry_runs, np.tile(P[s_mid * every - 1], bettors),
+                         np.tile(rb.mu, bettors), np.tile(rb.sigma, bettors), np.tile(rb.rho, bettors),
+                         P=np.tile(rb.P, bettors), theta=np.tile(rb.theta, bettors), seed=rb.seed)
+    snap.race_id0 = id0 + s_mid * bettors
+    sc = torch.empty(snap.n_total, dtype=torch.int32, device=dev)
+    ss = torch.empty(snap.n_races, dtype=torch.int64, device=dev)
+    sp = torch.empty(snap.n_total, dtype=torch.float32, device=dev)
+    so = torch.empty(snap.n_total, dtype=torch.float32, device=dev)
+    with bbe.Batch(snap, stream=stream) as sb:
+        times, _ = _device_passes(sb, snap, sc, ss, sp, stream, dev, passes=20, warmup=3)
+    e2e_s, _, _ = _e2e_calls(snap, sc, sp, so, stream, dev, calls=20)
+    out["one_snapshot"] = {"bettors": bettors, "dry_runs": dry_runs, "snapshot_step": s_mid * every,
+                           "device_ms_median": float(np.median(times)) * 1e3, "e2e_ms_median": e2e_s * 1e3}
     return out
 
 
@@ -1121,6 +1139,10 @@ def make_summary(line: dict) -> dict:
                         "rate_n": {str(x["n"]): r(x["competitor_steps_per_s"], 3) for x in rows if x["n"] in (2, 5, 10, 20, 24, 32)}}
     if co:
         out["oracle"] = {k: r(v["value"], 3) for k, v in co.items() if isinstance(v, dict)}
+    pop = (line.get("population") or {}).get("one_snapshot")
+    if pop:
+        out["one_snapshot_bettors"] = {"bettors": pop["bettors"], "dry_runs": pop["dry_runs"],
+                                       "device_ms": r(pop["device_ms_median"], 3), "e2e_ms": r(pop["e2e_ms_median"], 3)}
     return out
 
 
