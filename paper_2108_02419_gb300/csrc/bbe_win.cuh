@@ -71,7 +71,8 @@ struct WinStage {
     int flag[NS];                       // by segment base + rank: the slot there swaps with its successor
     unsigned segk[NS];                  // by segment base: rollout index handed to a restart
     unsigned long long key[NS];         // by segment base: least crossing key of the block (win mode)
-    unsigned long long fkey[NS];        // place mode: each slot's crossing key of the block, or none
+    unsigned long long fkey[NS];        // place mode: each slot's crossing (sub-step, slot) of the block, or none
+    float2 fcross[NS];                  // place mode: (d, S) of that crossing step
     unsigned next_k;                    // next rollout index of the work item
 };
 
@@ -373,6 +374,9 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
                     const int slot = 32 * v + lane;
                     fk[v] = st.fkey[slot];
                     if (fk[v] != kNoKey) {
+                        const float2 c = st.fcross[slot];
+                        const float tau = __fdiv_rn(__fsub_rn(L, c.x), c.y);
+                        fk[v] |= static_cast<unsigned long long>(__float_as_uint(tau)) << 8;
                         st.fkey[slot] = kNoKey;
                         more = true;
                     }
@@ -538,10 +542,9 @@ __global__ void __maxnreg__((WinRegs<V, MODE>::value)) win_rollout_kernel(Rollou
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         if (fv[v]) {
-                            const float tau = __fdiv_rn(__fsub_rn(L, d[v]), S[v]);
-                            st.fkey[32 * v + lane] = (static_cast<unsigned long long>(J) << 40) |
-                                                     (static_cast<unsigned long long>(__float_as_uint(tau)) << 8) |
-                                                     unsigned(32 * v + lane);
+                            // tau joins the key at the block's end (one division there, none here)
+                            st.fkey[32 * v + lane] = (static_cast<unsigned long long>(J) << 40) | unsigned(32 * v + lane);
+                            st.fcross[32 * v + lane] = make_float2(d[v], S[v]);
                         }
                     }
                 }
